@@ -1,0 +1,115 @@
+/*
+ * FP64 CPU oracle for the instanced-quad path tracer.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code with
+ * the CUDA path: its own scene structures, BVH, intersection routine
+ * (Moller-Trumbore instead of the watertight test), camera, sampling and
+ * Philox generator, all in double precision from FP32 inputs.
+ *
+ * What it follows:
+ *   - two-level instancing: a top-level structure over object instances, one
+ *     structure per object, rays moved into object space (Section 4.2,
+ *     "Geometry Types, Complexity, and Memory Consumption"; Section 3.2);
+ *   - quads as the primitive, each quad the pair of triangles it was merged
+ *     from (Section 4.2, "Quads");
+ *   - a path tracer with progressive 1-spp accumulation and a maximum path
+ *     depth (Section 4.4 "Shading"; Section 5 "Results": depth five).
+ * Choices the paper leaves open are fixed identically on both sides and are
+ * listed in the design notes ("readings").
+ *
+ * Parity status per function:
+ *   ora_philox            pinned: known-answer vector and an external
+ *                         Philox4x32-10 implementation (Triton interpreter).
+ *   ora_intersect_quad    pinned: closed-form plane intersections, edges,
+ *                         vertices, misses.
+ *   ora_trace_*           pinned: BVH == brute force (exact), instanced ==
+ *                         flattened world-space brute force.
+ *   ora_render            pinned: flat-plane closed form (env and sun),
+ *                         white furnace, value-set invariant.
+ *   ora_sample_cosine     pinned: moments E[cos]=2/3, E[cos^2]=1/2, ONB.
+ *   ora_render_grad       pinned: closed form on a flat plane, central
+ *                         finite differences of ora_render.
+ *   ora_camera_ray        pinned: centre and corner rays in closed form.
+ */
+#ifndef QRT_ORACLE_H
+#define QRT_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ora_scene ora_scene;
+
+typedef struct {
+    float eye[3], look[3], up[3];
+    float vfov_deg;
+    uint32_t w, h, spp;
+    uint64_t pixel_base;
+} ora_view;
+
+typedef struct {
+    uint32_t max_depth;
+    uint64_t seed;
+    float env[3];
+    float sun_dir[3];
+    float sun_E[3];
+} ora_params;
+
+/* Philox4x32-10: out = philox(ctr, key). */
+void ora_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Scene: n_mesh meshes (verts float3 packed, quads 4 x u32), n_inst instances
+ * with object->world float 3x4 row-major transforms.  Arrays are copied. */
+ora_scene* ora_scene_new(uint32_t n_mesh, const float* const* verts, const uint32_t* n_verts,
+                         const uint32_t* const* quads, const uint32_t* n_quads,
+                         uint64_t n_inst, const float* xforms, const uint32_t* mesh_ids);
+void ora_scene_free(ora_scene* s);
+uint64_t ora_scene_n_quads(const ora_scene* s);
+
+/* One ray against one quad (v: 4 x float3).  Returns 1 on hit with t in
+ * (tmin, tmax); writes t and quad-space (u, v). */
+int ora_intersect_quad(const double o[3], const double d[3], double tmin, double tmax,
+                       const double v[12], double* t, double* u, double* w);
+
+/* rays: n x 8 floats (o, tmin, d, tmax).  mode 0 = BVH, 1 = brute force over
+ * all instances and quads, 2 = brute force over world-space (flattened)
+ * vertices.  Miss: inst = prim = 0xFFFFFFFF, t = tmax. */
+void ora_trace_closest(const ora_scene* s, const float* rays, uint64_t n, int mode,
+                       double* t, uint32_t* inst, uint32_t* prim, double* u, double* v,
+                       int nthreads);
+void ora_trace_any(const ora_scene* s, const float* rays, uint64_t n, int mode,
+                   uint8_t* occluded, int nthreads);
+
+/* Camera ray of pixel (x, y) with jitter (xi1, xi2): writes o[3], d[3]. */
+void ora_camera_ray(const ora_view* v, uint32_t x, uint32_t y, double xi1, double xi2,
+                    double o[3], double d[3]);
+
+/* Cosine-weighted direction about unit normal n from (xi1, xi2). */
+void ora_sample_cosine(const double n[3], double xi1, double xi2, double out[3]);
+
+/* Render the given pixels (indices y*w+x into the view; NULL = all, in
+ * order).  rgb: n_pix x 3 doubles (mean over spp).  If log_inst/log_prim are
+ * non-NULL they receive, per path (pixel-major, then sample), max_depth
+ * entries of the hit instance / quad (0xFFFFFFFF = no hit); log_shadow gets
+ * per path 2 bits per vertex for the first 16 vertices: bit 2i = shadow ray
+ * traced at vertex i, bit 2i+1 = it was occluded.  max_depth is 1..256.  n_escaped/n_truncated (nullable) count paths
+ * that left the scene / ran out of depth on a surface. */
+int ora_render(const ora_scene* s, const ora_view* view, const float* albedo,
+               const ora_params* p, const int64_t* pixels, uint64_t n_pix,
+               double* rgb, uint32_t* log_inst, uint32_t* log_prim, uint32_t* log_shadow,
+               uint64_t* n_escaped, uint64_t* n_truncated, int nthreads);
+
+/* Gradient of sum_p sum_c dimage[p,c] * I[p,c] with respect to the per-quad
+ * albedo (n_quads x 3), accumulated into grad (doubles, zeroed by caller),
+ * by storing each path and differentiating its polynomial in the albedos.
+ * dimage is indexed like rgb above (n_pix x 3). */
+int ora_render_grad(const ora_scene* s, const ora_view* view, const float* albedo,
+                    const ora_params* p, const int64_t* pixels, uint64_t n_pix,
+                    const double* dimage, double* grad, int nthreads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,467 @@
+"""Seeded synthetic inputs: meshes, instances, albedo, cameras and light settings.
+
+This module only *produces inputs*.  It holds none of the path's arithmetic
+(no ray generation, no intersection, no BVH, no shading); both the CUDA path
+and the FP64 oracle consume what it returns.  Every array is a plain numpy
+array so the two sides can marshal it their own way.
+
+Workloads (all deterministic from integer seeds; geometry seed 1, instance
+seed 2, albedo seed 3, render seed 4):
+
+* ``tiny``  -- one 64x64-quad jittered grid, 256 randomly rotated, scaled and
+  translated instances in a 100^3 box, 256x256, 1 spp, depth 2, white
+  environment light only.
+* ``mid``   -- 64 prototypes (half displaced grids, half closed noisy blobs)
+  with log-uniform quad counts in [2^12, 2^16], a 2048x2048-quad heightfield
+  terrain, 100k random affine instances standing on the terrain,
+  1024x1024, 4 spp, depth 5, environment plus a directional sun.
+* ``batched`` -- 32 views of the mid scene with uneven resolution and spp.
+* ``adjoint`` -- the mid scene at 512x512, 8 spp, depth 4, plus a perturbed
+  target albedo.
+
+They stand in for the Moana Island Scene (Section 3: 39.3 M instances of
+prototypes ranging from a few dozen to millions of primitives, heavily
+overlapping), which is not available here.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SEED_GEOMETRY = 1
+SEED_INSTANCES = 2
+SEED_ALBEDO = 3
+SEED_RENDER = 4
+SEED_VIEWS = 5
+SEED_TARGET = 6
+
+
+@dataclass
+class Scene:
+    """Meshes (prototypes) plus instances.
+
+    meshes: list of (verts float32 [V,3], quads uint32 [Q,4]); quad vertices
+            are listed in order around the quad.
+    xforms: float32 [N,12] object->world, row-major 3x4 (last column = translation).
+    mesh_ids: uint32 [N].
+    """
+    meshes: list
+    xforms: np.ndarray
+    mesh_ids: np.ndarray
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_quads(self) -> int:
+        return int(sum(q.shape[0] for _, q in self.meshes))
+
+    @property
+    def quad_offsets(self) -> np.ndarray:
+        """First albedo row of each mesh (albedo is per unique quad)."""
+        counts = np.array([q.shape[0] for _, q in self.meshes], dtype=np.int64)
+        return np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.int64)
+
+
+@dataclass
+class View:
+    eye: tuple
+    look: tuple
+    up: tuple
+    vfov_deg: float
+    w: int
+    h: int
+    spp: int
+    pixel_base: int = 0
+
+
+@dataclass
+class Params:
+    max_depth: int
+    seed: int = SEED_RENDER
+    env: tuple = (1.0, 1.0, 1.0)
+    sun_dir: tuple = (0.0, 0.0, 1.0)
+    sun_E: tuple = (0.0, 0.0, 0.0)
+
+    @property
+    def sun_on(self) -> bool:
+        return any(e != 0.0 for e in self.sun_E)
+
+
+# --------------------------------------------------------------------------
+# mesh builders
+# --------------------------------------------------------------------------
+
+def grid_quads(nx: int, ny: int) -> np.ndarray:
+    """Quads of an (nx+1)x(ny+1) vertex lattice, counter-clockwise seen from +z."""
+    i, j = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    v00 = (j * (nx + 1) + i).ravel()
+    q = np.stack([v00, v00 + 1, v00 + nx + 2, v00 + nx + 1], axis=1)
+    return q.astype(np.uint32)
+
+
+def _value_noise(rng: np.random.Generator, octaves: int = 5, base: int = 4):
+    """Returns f(x, y) -> fbm value noise in about [-1, 1]; x, y in [0, 1]."""
+    tables = []
+    for o in range(octaves):
+        n = base * (2 ** o) + 1
+        tables.append(rng.uniform(-1.0, 1.0, size=(n, n)))
+
+    def f(x, y):
+        out = np.zeros_like(x, dtype=np.float64)
+        amp = 1.0
+        for tab in tables:
+            n = tab.shape[0] - 1
+            gx = np.clip(x, 0.0, 1.0) * n
+            gy = np.clip(y, 0.0, 1.0) * n
+            ix = np.minimum(gx.astype(np.int64), n - 1)
+            iy = np.minimum(gy.astype(np.int64), n - 1)
+            fx = gx - ix
+            fy = gy - iy
+            sx = fx * fx * (3 - 2 * fx)
+            sy = fy * fy * (3 - 2 * fy)
+            a = tab[iy, ix] * (1 - sx) + tab[iy, ix + 1] * sx
+            b = tab[iy + 1, ix] * (1 - sx) + tab[iy + 1, ix + 1] * sx
+            out += amp * (a * (1 - sy) + b * sy)
+            amp *= 0.5
+        return out / 1.9375
+
+    return f
+
+
+def tiny_mesh(seed: int = SEED_GEOMETRY):
+    """65x65 vertex grid over [-1,1]^2, z ~ U(-0.1, 0.1): 4096 quads."""
+    rng = np.random.default_rng(seed)
+    n = 64
+    xs = np.linspace(-1.0, 1.0, n + 1)
+    X, Y = np.meshgrid(xs, xs, indexing="xy")
+    Z = rng.uniform(-0.1, 0.1, size=X.shape)
+    verts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1).astype(np.float32)
+    return verts, grid_quads(n, n)
+
+
+def displaced_grid(rng: np.random.Generator, nq: int):
+    """Unit-size displaced grid in [-0.5,0.5]^2 with fbm height (a 'leaf' or 'frond')."""
+    nx = max(2, int(round(math.sqrt(nq))))
+    ny = max(2, int(round(nq / nx)))
+    xs = np.linspace(-0.5, 0.5, nx + 1)
+    ys = np.linspace(-0.5, 0.5, ny + 1)
+    X, Y = np.meshgrid(xs, ys, indexing="xy")
+    f = _value_noise(rng, octaves=4, base=3)
+    Z = 0.15 * f(X + 0.5, Y + 0.5)
+    verts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1).astype(np.float32)
+    return verts, grid_quads(nx, ny)
+
+
+def noisy_blob(rng: np.random.Generator, nq: int):
+    """Closed lat-long sphere of radius ~0.5 with radial noise.
+
+    Rows touching a pole use the single pole vertex twice, so those quads are
+    degenerate on one edge (a triangle), as real production meshes have.
+    """
+    nlon = max(4, int(round(math.sqrt(2 * nq))))
+    nlat = max(3, int(round(nq / nlon)))
+    theta = np.linspace(0.0, math.pi, nlat + 1)[1:-1]  # interior rings
+    phi = np.linspace(0.0, 2 * math.pi, nlon, endpoint=False)
+    T, P = np.meshgrid(theta, phi, indexing="ij")
+    f = _value_noise(rng, octaves=3, base=3)
+    r = 0.5 * (1.0 + 0.25 * f(T / math.pi, P / (2 * math.pi)))
+    ring = np.stack([r * np.sin(T) * np.cos(P), r * np.sin(T) * np.sin(P), r * np.cos(T)], axis=-1)
+    ring = ring.reshape(-1, 3)
+    north = np.array([[0.0, 0.0, 0.5]])
+    south = np.array([[0.0, 0.0, -0.5]])
+    verts = np.concatenate([ring, north, south]).astype(np.float32)
+    nr = nlat - 1  # number of interior rings
+    iN = nr * nlon
+    iS = iN + 1
+    quads = []
+    j = np.arange(nlon)
+    jn = (j + 1) % nlon
+    # north cap: pole, ring0[j], ring0[j+1] (pole repeated -> triangle)
+    quads.append(np.stack([np.full(nlon, iN), j, jn, np.full(nlon, iN)], axis=1))
+    for a in range(nr - 1):
+        r0 = a * nlon
+        r1 = (a + 1) * nlon
+        quads.append(np.stack([r0 + j, r1 + j, r1 + jn, r0 + jn], axis=1))
+    r0 = (nr - 1) * nlon
+    quads.append(np.stack([r0 + j, np.full(nlon, iS), np.full(nlon, iS), r0 + jn], axis=1))
+    return verts, np.concatenate(quads).astype(np.uint32)
+
+
+# --------------------------------------------------------------------------
+# transforms
+# --------------------------------------------------------------------------
+
+def random_rotations(rng: np.random.Generator, n: int) -> np.ndarray:
+    """Uniform rotations on SO(3) from normalised Gaussian quaternions, [n,3,3]."""
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, z = q.T
+    R = np.empty((n, 3, 3))
+    R[:, 0, 0] = 1 - 2 * (y * y + z * z)
+    R[:, 0, 1] = 2 * (x * y - z * w)
+    R[:, 0, 2] = 2 * (x * z + y * w)
+    R[:, 1, 0] = 2 * (x * y + z * w)
+    R[:, 1, 1] = 1 - 2 * (x * x + z * z)
+    R[:, 1, 2] = 2 * (y * z - x * w)
+    R[:, 2, 0] = 2 * (x * z - y * w)
+    R[:, 2, 1] = 2 * (y * z + x * w)
+    R[:, 2, 2] = 1 - 2 * (x * x + y * y)
+    return R
+
+
+def pack_xforms(L: np.ndarray, t: np.ndarray) -> np.ndarray:
+    """[n,3,3] linear part and [n,3] translation -> float32 [n,12] row-major 3x4."""
+    n = L.shape[0]
+    M = np.zeros((n, 3, 4))
+    M[:, :, :3] = L
+    M[:, :, 3] = t
+    return M.reshape(n, 12).astype(np.float32)
+
+
+IDENTITY_XFORM = np.array([1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0], dtype=np.float32)
+
+
+# --------------------------------------------------------------------------
+# workloads
+# --------------------------------------------------------------------------
+
+def tiny_scene(seed_geom: int = SEED_GEOMETRY, seed_inst: int = SEED_INSTANCES,
+               n_inst: int = 256) -> Scene:
+    verts, quads = tiny_mesh(seed_geom)
+    rng = np.random.default_rng(seed_inst)
+    R = random_rotations(rng, n_inst)
+    s = rng.uniform(0.5, 2.0, size=n_inst)
+    t = rng.uniform(0.0, 100.0, size=(n_inst, 3))
+    xf = pack_xforms(R * s[:, None, None], t)
+    return Scene([(verts, quads)], xf, np.zeros(n_inst, dtype=np.uint32), name="tiny")
+
+
+def tiny_view() -> View:
+    return View(eye=(50.0, -120.0, 50.0), look=(50.0, 50.0, 50.0), up=(0.0, 0.0, 1.0),
+                vfov_deg=40.0, w=256, h=256, spp=1)
+
+
+def tiny_params() -> Params:
+    return Params(max_depth=2, env=(1.0, 1.0, 1.0), sun_E=(0.0, 0.0, 0.0))
+
+
+def albedo(n_quads: int, seed: int = SEED_ALBEDO, lo: float = 0.2, hi: float = 0.8) -> np.ndarray:
+    """Per-unique-quad RGB albedo, float32 [n_quads, 3]."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(lo, hi, size=(n_quads, 3)).astype(np.float32)
+
+
+MID_TERRAIN_EXTENT = 4096.0
+MID_TERRAIN_QUADS = 2048
+MID_TERRAIN_AMPLITUDE = 150.0
+
+
+def terrain_heights(seed: int, nq: int = MID_TERRAIN_QUADS,
+                    amplitude: float = MID_TERRAIN_AMPLITUDE) -> np.ndarray:
+    rng = np.random.default_rng(seed + 1000)
+    f = _value_noise(rng, octaves=6, base=4)
+    u = np.linspace(0.0, 1.0, nq + 1)
+    U, V = np.meshgrid(u, u, indexing="xy")
+    return amplitude * f(U, V)
+
+
+def terrain_mesh(heights: np.ndarray, extent: float):
+    n = heights.shape[0] - 1
+    xs = np.linspace(0.0, extent, n + 1)
+    X, Y = np.meshgrid(xs, xs, indexing="xy")
+    verts = np.stack([X.ravel(), Y.ravel(), heights.ravel()], axis=1).astype(np.float32)
+    return verts, grid_quads(n, n)
+
+
+def _terrain_height_at(heights: np.ndarray, extent: float, x, y):
+    n = heights.shape[0] - 1
+    gx = np.clip(x / extent * n, 0, n - 1e-9)
+    gy = np.clip(y / extent * n, 0, n - 1e-9)
+    ix = gx.astype(np.int64)
+    iy = gy.astype(np.int64)
+    fx = gx - ix
+    fy = gy - iy
+    h = heights
+    return ((h[iy, ix] * (1 - fx) + h[iy, ix + 1] * fx) * (1 - fy)
+            + (h[iy + 1, ix] * (1 - fx) + h[iy + 1, ix + 1] * fx) * fy)
+
+
+def mid_scene(seed_geom: int = SEED_GEOMETRY, seed_inst: int = SEED_INSTANCES,
+              n_proto: int = 64, n_inst: int = 100_000,
+              terrain_quads: int = MID_TERRAIN_QUADS,
+              extent: float = MID_TERRAIN_EXTENT) -> Scene:
+    """64 prototypes + terrain, 100k instances + 1 terrain instance (identity)."""
+    rng = np.random.default_rng(seed_geom)
+    meshes = []
+    for p in range(n_proto):
+        nq = int(round(2.0 ** rng.uniform(12.0, 16.0)))
+        meshes.append(displaced_grid(rng, nq) if p % 2 == 0 else noisy_blob(rng, nq))
+    heights = terrain_heights(seed_geom, terrain_quads)
+    meshes.append(terrain_mesh(heights, extent))
+    terrain_id = len(meshes) - 1
+
+    rng = np.random.default_rng(seed_inst)
+    R = random_rotations(rng, n_inst)
+    s = rng.uniform(0.5, 2.0, size=(n_inst, 3))
+    base = np.exp(rng.uniform(math.log(4.0), math.log(40.0), size=n_inst))
+    L = R * (s * base[:, None])[:, None, :]          # R @ diag(s * base)
+    x = rng.uniform(0.0, extent, size=n_inst)
+    y = rng.uniform(0.0, extent, size=n_inst)
+    z = _terrain_height_at(heights, extent, x, y)
+    xf = pack_xforms(L, np.stack([x, y, z], axis=1))
+    ids = rng.integers(0, n_proto, size=n_inst).astype(np.uint32)
+    xf = np.concatenate([xf, IDENTITY_XFORM[None]], axis=0)
+    ids = np.concatenate([ids, np.array([terrain_id], dtype=np.uint32)])
+    return Scene(meshes, xf, ids, name="mid",
+                 meta={"n_proto": n_proto, "terrain_mesh": terrain_id})
+
+
+def mid_view(w: int = 1024, h: int = 1024, spp: int = 4) -> View:
+    return View(eye=(2048.0, -300.0, 450.0), look=(2048.0, 1800.0, 0.0), up=(0.0, 0.0, 1.0),
+                vfov_deg=50.0, w=w, h=h, spp=spp)
+
+
+def _normalize(v):
+    v = np.asarray(v, dtype=np.float64)
+    return tuple(float(c) for c in v / np.linalg.norm(v))
+
+
+MID_SUN_DIR = _normalize((0.4, 0.3, 1.0))
+
+
+def mid_params(max_depth: int = 5) -> Params:
+    return Params(max_depth=max_depth, env=(1.0, 1.0, 1.0), sun_dir=MID_SUN_DIR, sun_E=(3.0, 3.0, 3.0))
+
+
+def batched_views(n_views: int = 32, seed: int = SEED_VIEWS, min_log2: float = 8.0,
+                  max_log2: float = 11.0, max_spp: int = 16) -> list:
+    """Uneven views around the mid vista: side = 32*round(2^U(8,11)/32), spp ~ U{1..16}.
+
+    pixel_base is the running pixel count, so every (view, pixel) has a unique
+    global pixel index and therefore its own random stream.
+    """
+    rng = np.random.default_rng(seed)
+    views = []
+    base = 0
+    for _ in range(n_views):
+        side = int(32 * round(2.0 ** rng.uniform(min_log2, max_log2) / 32))
+        side = max(32, side)
+        spp = int(rng.integers(1, max_spp + 1))
+        ex = 2048.0 + rng.uniform(-1200.0, 1200.0)
+        ey = rng.uniform(-600.0, 600.0)
+        ez = rng.uniform(250.0, 700.0)
+        lx = ex + rng.uniform(-800.0, 800.0)
+        ly = ey + rng.uniform(1200.0, 2400.0)
+        views.append(View(eye=(ex, ey, ez), look=(lx, ly, 0.0), up=(0.0, 0.0, 1.0),
+                          vfov_deg=float(rng.uniform(35.0, 60.0)), w=side, h=side, spp=spp,
+                          pixel_base=base))
+        base += side * side
+    return views
+
+
+def adjoint_view() -> View:
+    return mid_view(512, 512, 8)
+
+
+def adjoint_params() -> Params:
+    return mid_params(max_depth=4)
+
+
+def perturbed_albedo(a: np.ndarray, seed: int = SEED_TARGET, sigma: float = 0.05) -> np.ndarray:
+    """Target albedo a* + N(0, sigma), clamped to [0.01, 0.99]."""
+    rng = np.random.default_rng(seed)
+    return np.clip(a + rng.normal(0.0, sigma, size=a.shape), 0.01, 0.99).astype(np.float32)
+
+
+# --------------------------------------------------------------------------
+# ray sets for the trace entry points (independent of any renderer)
+# --------------------------------------------------------------------------
+
+def ray_array(o: np.ndarray, d: np.ndarray, tmin: float = 0.0, tmax: float = np.inf) -> np.ndarray:
+    """Pack origins/directions into float32 [n,8] = (o, tmin, d, tmax)."""
+    n = o.shape[0]
+    r = np.empty((n, 8), dtype=np.float32)
+    r[:, 0:3] = o
+    r[:, 3] = tmin
+    r[:, 4:7] = d
+    r[:, 7] = tmax
+    return r
+
+
+def scene_box(scene: Scene) -> tuple:
+    """Loose world box from instance translations (inputs only, not a bound)."""
+    t = scene.xforms.reshape(-1, 3, 4)[:, :, 3].astype(np.float64)
+    return t.min(axis=0), t.max(axis=0)
+
+
+def rays_focused(n: int, eye, lo, hi, seed: int) -> np.ndarray:
+    """Coherent bundle: from one eye toward uniform points in [lo, hi]."""
+    rng = np.random.default_rng(seed)
+    tgt = rng.uniform(lo, hi, size=(n, 3))
+    o = np.broadcast_to(np.asarray(eye, dtype=np.float64), (n, 3))
+    d = tgt - o
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return ray_array(o, d)
+
+
+def rays_random(n: int, lo, hi, seed: int, tmax: float = np.inf) -> np.ndarray:
+    """Incoherent: uniform origins in [lo, hi], uniform directions on the sphere."""
+    rng = np.random.default_rng(seed)
+    o = rng.uniform(lo, hi, size=(n, 3))
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return ray_array(o, d, 0.0, tmax)
+
+
+def rays_parallel(n: int, lo, hi, direction, seed: int) -> np.ndarray:
+    """Shadow-like: uniform origins in [lo, hi], one shared direction."""
+    rng = np.random.default_rng(seed)
+    o = rng.uniform(lo, hi, size=(n, 3))
+    d = np.broadcast_to(np.asarray(direction, dtype=np.float64), (n, 3))
+    return ray_array(o, d)
+
+
+def rays_toward(n: int, lo, hi, targets: np.ndarray, jitter: float, seed: int) -> np.ndarray:
+    """Origins uniform in [lo, hi], each aimed at a random target point
+    (plus a uniform jitter of +-jitter per axis) -- a high hit-rate ray set."""
+    rng = np.random.default_rng(seed)
+    o = rng.uniform(lo, hi, size=(n, 3))
+    k = rng.integers(0, targets.shape[0], size=n)
+    tgt = targets[k] + rng.uniform(-jitter, jitter, size=(n, 3))
+    d = tgt - o
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return ray_array(o, d)
+
+
+def instance_origins(scene: Scene) -> np.ndarray:
+    """Translation column of each instance transform (where its object sits)."""
+    return scene.xforms.reshape(-1, 3, 4)[:, :, 3].astype(np.float64)
+
+
+def sphere_mesh(n_lat: int = 24, n_lon: int = 48, radius: float = 1.0):
+    """Noise-free lat-long sphere (a convex polyhedron), pole rows degenerate."""
+    theta = np.linspace(0.0, math.pi, n_lat + 1)[1:-1]
+    phi = np.linspace(0.0, 2 * math.pi, n_lon, endpoint=False)
+    T, P = np.meshgrid(theta, phi, indexing="ij")
+    ring = radius * np.stack([np.sin(T) * np.cos(P), np.sin(T) * np.sin(P), np.cos(T)], axis=-1)
+    verts = np.concatenate([ring.reshape(-1, 3), [[0, 0, radius]], [[0, 0, -radius]]]).astype(np.float32)
+    nr = n_lat - 1
+    iN, iS = nr * n_lon, nr * n_lon + 1
+    j = np.arange(n_lon)
+    jn = (j + 1) % n_lon
+    quads = [np.stack([np.full(n_lon, iN), j, jn, np.full(n_lon, iN)], axis=1)]
+    for a in range(nr - 1):
+        quads.append(np.stack([a * n_lon + j, (a + 1) * n_lon + j, (a + 1) * n_lon + jn, a * n_lon + jn], axis=1))
+    r0 = (nr - 1) * n_lon
+    quads.append(np.stack([r0 + j, np.full(n_lon, iS), np.full(n_lon, iS), r0 + jn], axis=1))
+    return verts, np.concatenate(quads).astype(np.uint32)
+
+
+def plane_mesh(n: int = 8):
+    """Flat n x n quad grid over [-1,1]^2 at z = 0."""
+    xs = np.linspace(-1.0, 1.0, n + 1)
+    X, Y = np.meshgrid(xs, xs, indexing="xy")
+    verts = np.stack([X.ravel(), Y.ravel(), np.zeros(X.size)], axis=1).astype(np.float32)
+    return verts, grid_quads(n, n)
