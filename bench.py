@@ -1,0 +1,275 @@
+"""Benchmark of the instanced-quad path tracer on one GB300 (or N replicas).
+
+A step is one qrt_render_spp of the mid workload: 64 prototypes + terrain
+(5.73 M unique quads), 100k instances, 1024x1024, 4 spp, path depth 5,
+environment + sun with shadow rays.  value = all rays traced per second
+(closest-hit + shadow), the accounting of the paper's Mray/s (Section 5).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank renders its own frame (weak scaling, no collective
+on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mrays/s closest-hit & path samples/s, batched vs plain launch; adjoint/primal"
+STAT_WORDS = 6  # rays, nodes, quads, instance entries, fp64 re-tests, shading vertices
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"qrt_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def mid_workload():
+    from paper_2001_02620_gb300 import inputs as I
+    sc = I.mid_scene()
+    return sc, I.mid_view(), I.mid_params(), I.albedo(sc.n_quads)
+
+
+def oracle_sample(sc, view, params, alb, budget_s: float, rank_pixels: int = 0):
+    """Times the FP64 oracle on a bounded pixel sample of the same workload."""
+    import oracle as O
+    t0 = time.time()
+    osc = O.OracleScene(sc)
+    build_s = time.time() - t0
+    rng = np.random.default_rng(99)
+    npix = view.w * view.h
+    n = 256
+    rays = 0
+    elapsed = 0.0
+    done = 0
+    while elapsed < budget_s and done < npix:
+        px = rng.choice(npix, size=n, replace=False)
+        t = time.time()
+        r = osc.render(view, alb, params, pixels=px, log=True)
+        dt = time.time() - t
+        hits = int((r["inst"] != 0xFFFFFFFF).sum())
+        sh = r["shadow"]
+        shadow = sum(int(((sh >> (2 * i)) & 1).sum()) for i in range(params.max_depth))
+        rays += hits + int(r["escaped"]) + shadow
+        elapsed += dt
+        done += n
+        n *= 2
+    cores = os.cpu_count() or 1
+    return {"value": rays / elapsed / 1e6, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} random pixels x {view.spp} spp of the 1024x1024 mid frame "
+                      f"({rays} rays, {elapsed:.1f} s FP64, oracle BVH build {build_s:.1f} s excluded)",
+            "paths_per_s": done * view.spp / elapsed}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sc, view, params, alb = mid_workload()
+    per = []
+    base = None
+    for k in range(args.warmup + args.steps):
+        r = oracle_sample(sc, view, params, alb, budget_s=8.0 if k >= args.warmup else 2.0)
+        if k >= args.warmup:
+            per.append(r["value"])
+            base = r
+    v = float(np.median(per))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mrays/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "mid: 64 prototypes + 2048^2-quad terrain, 100k instances, "
+                                   "1024x1024, 4 spp, depth 5, env + sun"},
+            "cpu_baseline": {"value": v, "unit": "Mrays/s", "cores": base["cores"], "kind": "oracle",
+                             "sample": base["sample"]},
+            "e2e": {"value": v, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "vs_baseline": None}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--extras", default="trace,batched,adjoint")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    from paper_2001_02620_gb300 import api, inputs as I
+    from paper_2001_02620_gb300 import build as B
+    B.build()
+    sc, view, params, alb = mid_workload()
+    view.pixel_base = rank * view.w * view.h  # each rank renders its own frame
+    t0 = time.time()
+    scene = api.Scene(sc)
+    build_s = time.time() - t0
+    dev = torch.device("cuda", local)
+    d_alb = torch.from_numpy(alb).to(dev)
+    img = torch.empty((view.h, view.w, 3), device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        scene.render([view], d_alb, params, outs=[img])
+
+    # counters of one render (same launch configuration, counters added)
+    stats = torch.zeros(STAT_WORDS, dtype=torch.int64, device=dev)
+    scene.render([view], d_alb, params, outs=[img], stats=stats)
+    scene.check()
+    st = stats.cpu().numpy()
+    rays, nodes, quads, insts, fallbacks, verts = [int(x) for x in st]
+    paths = view.w * view.h * view.spp
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    clk = clocks.stop()
+    scene.check()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the public API with host buffers
+    h_alb = torch.from_numpy(alb).pin_memory()
+    h_img = torch.empty((view.h, view.w, 3)).pin_memory()
+    for _ in range(2):
+        d_alb.copy_(h_alb, non_blocking=True)
+        scene.render([view], d_alb, params, outs=[img])
+        h_img.copy_(img, non_blocking=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        d_alb.copy_(h_alb, non_blocking=True)
+        scene.render([view], d_alb, params, outs=[img])
+        h_img.copy_(img, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+
+    hbm, peak_kind = peaks()
+    alg_bytes = 64 * nodes + 48 * quads + 64 * insts + (12 + 48 + 64) * verts + 12 * view.w * view.h
+    achieved = alg_bytes / (ms * 1e-3) / 1e9
+    value = world * rays / (ms * 1e-3) / 1e6
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "mid: 64 prototypes (log-uniform 2^12..2^16 quads) + 2048^2-quad "
+                               "terrain = 5.73M unique quads, 100k instances, 1024x1024, 4 spp, "
+                               "depth 5, env + sun shadow rays",
+                   "parallelism": f"replicas{world}", "l2": "working set 0.47 GB > L2 (no flush)"},
+        "path_samples_per_s": world * paths / (ms * 1e-3),
+        "rays_per_step": rays, "paths_per_step": paths,
+        "counters": {"nodes": nodes, "quads": quads, "instance_entries": insts,
+                     "fp64_retests": fallbacks, "vertices": verts},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "peak_kind": peak_kind + " hbm_gbs (of " + peak_kind + ")"},
+        "e2e": {"value": world * rays / (e2e_ms * 1e-3) / 1e6, "unit": "Mrays/s",
+                "h2d_bytes_per_step": int(alb.nbytes), "d2h_bytes_per_step": int(img.numel() * 4),
+                "ms_per_step": e2e_ms},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "scene_build_s": build_s,
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = oracle_sample(sc, view, params, alb, budget_s=12.0)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,263 @@
+/*
+ * qrt -- instanced-quad ray tracing and path tracing on one GB300 (sm_103a).
+ *
+ * C ABI of the hot path of an interactive production-scene path tracer: a
+ * two-level acceleration structure (a top-level BVH over object instances,
+ * one BVH per object; Section 3.2 "Beyond Statistics" and Section 4.2
+ * "Geometry Types, Complexity, and Memory Consumption"), quads as the
+ * primitive (Section 4.2, "Quads"), closest-hit and any-hit ray queries, and
+ * a diffuse path tracer with a maximum path depth and one sample per pixel
+ * per progressive frame (Section 4.4 "Shading"; Section 5 "Results").
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns an int status: QRT_OK (0) or a negative QRT_ERR_*
+ *    code; qrt_last_error() gives a message for the calling thread.
+ *  - Pointers named d_* are caller-owned DEVICE memory on the current CUDA
+ *    device; every other pointer is host memory.  The library never frees
+ *    caller memory and keeps no pointer to it after the call returns, except
+ *    where a graph (qrt_render_graph_create) records device pointers.
+ *  - Device work is enqueued on the caller's stream (qrt_stream is the same
+ *    type as cudaStream_t; NULL = legacy default stream) and the call returns
+ *    without waiting.  Problems found on the device (stack overflow, step
+ *    limit) set a per-scene error word that qrt_check() reads.
+ *  - n == 0 is a no-op that returns QRT_OK.
+ *  - A scene is immutable after creation and may be used from several
+ *    streams at once for tracing and rendering.
+ *
+ * Units and layouts: world space is right-handed, z up.  Transforms are
+ * object->world, row-major 3x4 (the last column is the translation).  A quad
+ * (v0,v1,v2,v3) is the pair of triangles (v0,v1,v2) and (v0,v2,v3); quads
+ * are double-sided.  A ray hits at t only when tmin < t < tmax.
+ */
+#ifndef QRT_H
+#define QRT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QRT_VERSION 1
+
+enum {
+    QRT_OK = 0,
+    QRT_ERR_INVALID_ARG = -1,    /* bad handle, NULL pointer, size or value */
+    QRT_ERR_ALIGN = -2,          /* a device pointer is not aligned as stated */
+    QRT_ERR_OOM = -3,            /* device or host allocation failed */
+    QRT_ERR_CUDA = -4,           /* a CUDA runtime call failed (no device, launch error) */
+    QRT_ERR_STACK_OVERFLOW = -5, /* a traversal stack overflowed on the device */
+    QRT_ERR_STEP_LIMIT = -6,     /* a ray exceeded the traversal step limit */
+    QRT_ERR_NOT_READY = -7       /* resource not available (e.g. no free work slot) */
+};
+
+typedef struct CUstream_st* qrt_stream; /* identical to cudaStream_t */
+typedef struct qrt_scene_s* qrt_scene;
+typedef struct qrt_graph_s* qrt_graph;
+
+/* One object (prototype): n_verts packed float3 vertices and n_quads quads of
+ * four vertex indices each.  Host memory, copied during qrt_scene_create. */
+typedef struct {
+    const float* verts;
+    uint32_t n_verts;
+    const uint32_t* quads;
+    uint32_t n_quads;
+} qrt_mesh;
+
+/* Ray: 32 bytes.  Ray arrays must be 16-byte aligned.  d need not be unit
+ * length; t is measured in units of |d|. */
+typedef struct {
+    float o[3];
+    float tmin;
+    float d[3];
+    float tmax;
+} qrt_ray;
+
+/* Closest hit: 16 bytes.  inst = instance index, prim = quad index within
+ * that instance's mesh, uv = quad-space (u, v) as two unorm16 (u in the low
+ * half).  Miss: inst = prim = 0xFFFFFFFF, t = tmax.  Among hits at exactly
+ * the same t the smallest (inst, prim) wins. */
+typedef struct {
+    float t;
+    uint32_t inst;
+    uint32_t prim;
+    uint32_t uv;
+} qrt_hit;
+
+/* Pinhole camera.  Pixel (x, y), y = 0 the top row, is sampled at
+ * (x + xi1, y + xi2); vfov is the vertical field of view in degrees.
+ * pixel_base gives the first global pixel index of this view: the random
+ * stream of a sample is keyed by (pixel_base + y*w + x, sample, bounce), so
+ * distinct views should use disjoint ranges.  out_rgb: DEVICE float [h*w*3],
+ * row-major, receives the mean radiance over spp samples (overwritten). */
+typedef struct {
+    float eye[3];
+    float look[3];
+    float up[3];
+    float vfov_deg;
+    uint32_t w, h, spp;
+    uint32_t reserved0;
+    uint64_t pixel_base;
+    float* out_rgb;
+} qrt_view;
+
+/* Launch tuning; 0 in any field selects the library default.
+ *   block          threads per block (64..1024, multiple of 32)
+ *   blocks_per_sm  resident blocks per SM for persistent kernels
+ *   batch          work items a warp claims per fetch, in units of 32
+ *   stack          traversal stack entries per ray (32 or 64)
+ *   fetch          node fetch width in bytes (16: 4x128-bit, 32: 2x256-bit loads)
+ *   adjoint_mode   0/1 = path replay (recompute the path twice), 2 = keep the
+ *                  current path's vertices in registers (one trace pass) */
+typedef struct {
+    uint32_t block;
+    uint32_t blocks_per_sm;
+    uint32_t batch;
+    uint32_t stack;
+    uint32_t fetch;
+    uint32_t adjoint_mode;
+    uint32_t reserved[2];
+} qrt_tuning;
+
+/* Path-tracing parameters.
+ *   max_depth   closest-hit rays per path, camera ray included (1..256)
+ *   seed        Philox key
+ *   env         radiance of the uniform environment, reached by rays that
+ *               leave the scene
+ *   sun_dir     direction toward a directional sun (normalised internally);
+ *   sun_E       its irradiance (RGB); all zero disables the sun and its
+ *               shadow rays
+ *   d_path_log  optional DEVICE buffer for diagnostics (NULL = off): per path
+ *               max_depth pairs (inst, prim) of the hits, 0xFFFFFFFF where the
+ *               path had no such ray, then one word of shadow bits (bit 2i: a
+ *               shadow ray was traced at vertex i, bit 2i+1: it was occluded;
+ *               first 16 vertices).  Path p of view v sits at
+ *               sum_{u<v}(w*h*spp)_u + (y*w + x)*spp + sample, each path taking
+ *               2*max_depth + 1 words.
+ *   max_steps   traversal step limit per ray (0 = 2^20); exceeding it stops
+ *               that ray and raises QRT_ERR_STEP_LIMIT.
+ *   tuning      launch tuning (zeros = defaults). */
+typedef struct {
+    uint32_t max_depth;
+    uint32_t flags;
+    uint64_t seed;
+    float env[3];
+    float sun_dir[3];
+    float sun_E[3];
+    uint32_t max_steps;
+    uint32_t* d_path_log;
+    qrt_tuning tuning;
+} qrt_params;
+
+/* BVH build options (NULL = defaults).
+ *   max_leaf   quads per BLAS leaf (1..8, default 4)
+ *   sah_bins   binned-SAH bins (4..64, default 16)
+ *   threads    host threads for the build (0 = all cores)
+ *   degenerate 1 = build a deliberately deep chain-shaped BLAS (test aid for
+ *              the stack-overflow path); 0 = normal SAH build */
+typedef struct {
+    uint32_t max_leaf;
+    uint32_t sah_bins;
+    uint32_t threads;
+    uint32_t degenerate;
+} qrt_build_opts;
+
+/* Scene statistics (host). */
+typedef struct {
+    uint64_t n_meshes, n_instances, n_quads;
+    uint64_t blas_nodes, tlas_nodes;
+    uint64_t device_bytes;
+    uint32_t max_blas_depth, tlas_depth;
+    double build_seconds;
+} qrt_scene_stats;
+
+const char* qrt_last_error(void);
+int qrt_version(void);
+
+/* Build the two-level structure on the host and upload it to the current
+ * device (Section 4.2: objects are instanced, quads are the primitive).
+ * meshes: n_mesh host descriptors; xforms: host float [n_inst*12]; mesh_ids:
+ * host uint32 [n_inst].  Quad albedo rows are numbered mesh by mesh in order
+ * (mesh m's quad q is row sum_{k<m} n_quads_k + q).  On success *out owns all
+ * device memory of the scene.  Errors: INVALID_ARG (NULL/zero counts, index
+ * out of range, non-invertible transform), OOM, CUDA. */
+int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xforms,
+                     const uint32_t* mesh_ids, uint64_t n_inst, const qrt_build_opts* opts,
+                     qrt_scene* out);
+int qrt_scene_destroy(qrt_scene scene);
+int qrt_scene_stats_get(qrt_scene scene, qrt_scene_stats* out);
+
+/* Closest hit for n rays (Section 5: traversal and intersection dominate the
+ * frame).  d_rays: n qrt_ray, d_hits: n qrt_hit, both 16-byte aligned.
+ * tuning may be NULL. */
+int qrt_trace_closest(qrt_scene scene, const qrt_ray* d_rays, uint64_t n, qrt_hit* d_hits,
+                      const qrt_tuning* tuning, qrt_stream stream);
+
+/* Any hit (occlusion) for n rays: bit (i % 32) of d_occ_bits[i / 32] is set
+ * when ray i hits anything in (tmin, tmax).  d_occ_bits: ceil(n/32) uint32,
+ * overwritten. */
+int qrt_trace_any(qrt_scene scene, const qrt_ray* d_rays, uint64_t n, uint32_t* d_occ_bits,
+                  const qrt_tuning* tuning, qrt_stream stream);
+
+/* Path-trace n_views views (Section 4.4, progressive path tracing; one
+ * launch covers every (view, pixel) and all of each pixel's spp samples).
+ * d_albedo: DEVICE float [n_quads*3], per unique quad RGB albedo.  Each
+ * view's out_rgb receives the mean over its spp samples; results do not
+ * depend on n_views, on the tuning or on other views in the same call. */
+int qrt_render_spp(qrt_scene scene, const qrt_view* views, uint32_t n_views,
+                   const float* d_albedo, const qrt_params* params, qrt_stream stream);
+
+/* Adjoint of qrt_render_spp with respect to the albedo: adds
+ * sum_v sum_pixel sum_c d_dimage[v][pixel*3+c] * dI_v[pixel,c]/d albedo[q,c]
+ * into d_grad_albedo (DEVICE float [n_quads*3], accumulated, not cleared).
+ * Paths are recomputed from their random streams instead of being stored
+ * (path replay); contributions are added with FP32 atomics.  d_dimage: host
+ * array of n_views DEVICE pointers, each float [h*w*3]. */
+int qrt_render_adjoint(qrt_scene scene, const qrt_view* views, uint32_t n_views,
+                       const float* d_albedo, const float* const* d_dimage,
+                       float* d_grad_albedo, const qrt_params* params, qrt_stream stream);
+
+/* Mean-squared image loss and its gradient on the device:
+ * *d_loss = sum_i (img_i - target_i)^2 / n and d_dimage_i = 2 (img_i - target_i) / n
+ * (d_loss: one double; d_dimage may alias nothing).  n counts floats. */
+int qrt_l2_loss(const float* d_img, const float* d_target, uint64_t n, double* d_loss,
+                float* d_dimage, qrt_stream stream);
+
+/* Capture qrt_render_spp(views...) once into a CUDA graph (with its own work
+ * counter) and replay it with qrt_graph_launch.  The graph keeps the device
+ * pointers given here (albedo, out_rgb, path log); views and params are
+ * copied. */
+int qrt_render_graph_create(qrt_scene scene, const qrt_view* views, uint32_t n_views,
+                            const float* d_albedo, const qrt_params* params, qrt_graph* out);
+int qrt_graph_launch(qrt_graph graph, qrt_stream stream);
+int qrt_graph_destroy(qrt_graph graph);
+
+/* Diagnostics: as qrt_render_spp / qrt_trace_closest (any = 0) /
+ * qrt_trace_any (any = 1), and additionally add the traversal counters of the
+ * launch into d_stats (DEVICE uint64 [6], 8-byte aligned, accumulated):
+ * rays traced, inner nodes visited, quads tested, instances entered, quad
+ * tests re-done in FP64, path vertices shaded.  These counts give the algorithmic bytes of a
+ * launch (64 B per node, 48 B per quad, 64 B per instance entry). */
+int qrt_render_spp_stats(qrt_scene scene, const qrt_view* views, uint32_t n_views,
+                         const float* d_albedo, const qrt_params* params,
+                         unsigned long long* d_stats, qrt_stream stream);
+int qrt_trace_stats(qrt_scene scene, int any, const qrt_ray* d_rays, uint64_t n, void* d_out,
+                    const qrt_tuning* tuning, unsigned long long* d_stats, qrt_stream stream);
+
+/* Wait for the stream, then read and clear the scene's device error word.
+ * Returns QRT_OK, QRT_ERR_STACK_OVERFLOW, QRT_ERR_STEP_LIMIT or QRT_ERR_CUDA. */
+int qrt_check(qrt_scene scene, qrt_stream stream);
+
+/* Host only (no GPU needed): build one mesh's BLAS as qrt_scene_create would,
+ * verify its invariants (every quad referenced exactly once, every quantised
+ * child box contains the exact child box, child boxes inside the parent's)
+ * and report node count and depth.  Returns QRT_OK or INVALID_ARG with a
+ * message naming the broken invariant. */
+int qrt_blas_build_check(const qrt_mesh* mesh, const qrt_build_opts* opts, uint64_t* n_nodes,
+                         uint32_t* depth);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QRT_H */

@@ -1,0 +1,242 @@
+"""Python front end of the qrt C ABI.  PyTorch supplies device memory and
+streams; every step of the path runs in libqrt.so's kernels."""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _native as N
+from .inputs import Params, View
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def make_tuning(tuning: dict | None) -> N.qrt_tuning:
+    t = N.qrt_tuning()
+    for k, v in (tuning or {}).items():
+        setattr(t, k, int(v))
+    return t
+
+
+def make_params(p: Params, tuning: dict | None = None, path_log: torch.Tensor | None = None,
+                max_steps: int = 0) -> N.qrt_params:
+    cp = N.qrt_params()
+    cp.max_depth = int(p.max_depth)
+    cp.seed = int(p.seed)
+    cp.env[:] = [float(x) for x in p.env]
+    cp.sun_dir[:] = [float(x) for x in p.sun_dir]
+    cp.sun_E[:] = [float(x) for x in p.sun_E]
+    cp.max_steps = int(max_steps)
+    cp.d_path_log = _ptr(path_log)
+    cp.tuning = make_tuning(tuning)
+    return cp
+
+
+def make_views(views, outs) -> C.Array:
+    arr = (N.qrt_view * len(views))()
+    for k, (v, o) in enumerate(zip(views, outs)):
+        cv = arr[k]
+        cv.eye[:] = [float(x) for x in v.eye]
+        cv.look[:] = [float(x) for x in v.look]
+        cv.up[:] = [float(x) for x in v.up]
+        cv.vfov_deg = float(v.vfov_deg)
+        cv.w, cv.h, cv.spp = int(v.w), int(v.h), int(v.spp)
+        cv.pixel_base = int(v.pixel_base)
+        cv.out_rgb = _ptr(o)
+    return arr
+
+
+def path_log_words(views, max_depth: int) -> int:
+    return sum(int(v.w) * int(v.h) * int(v.spp) for v in views) * (2 * int(max_depth) + 1)
+
+
+class Scene:
+    """A scene uploaded to the current CUDA device (owns its device memory)."""
+
+    def __init__(self, scene, build_opts: dict | None = None):
+        L = N.lib()
+        meshes = scene.meshes
+        self._host = []
+        arr = (N.qrt_mesh * len(meshes))()
+        for k, (v, q) in enumerate(meshes):
+            v = np.ascontiguousarray(v, dtype=np.float32)
+            q = np.ascontiguousarray(q, dtype=np.uint32)
+            self._host += [v, q]
+            arr[k].verts = v.ctypes.data_as(C.POINTER(C.c_float))
+            arr[k].n_verts = v.shape[0]
+            arr[k].quads = q.ctypes.data_as(C.POINTER(C.c_uint32))
+            arr[k].n_quads = q.shape[0]
+        xf = np.ascontiguousarray(scene.xforms, dtype=np.float32).reshape(-1)
+        ids = np.ascontiguousarray(scene.mesh_ids, dtype=np.uint32)
+        opts = None
+        if build_opts:
+            opts = N.qrt_build_opts()
+            for k, v in build_opts.items():
+                setattr(opts, k, int(v))
+        h = C.c_void_p()
+        N.check(L.qrt_scene_create(arr, len(meshes), xf.ctypes.data_as(C.POINTER(C.c_float)),
+                                   ids.ctypes.data_as(C.POINTER(C.c_uint32)), ids.shape[0],
+                                   C.byref(opts) if opts is not None else None, C.byref(h)))
+        self._host = None
+        self.handle = h
+        st = N.qrt_scene_stats()
+        N.check(L.qrt_scene_stats_get(h, C.byref(st)))
+        self.stats = {f: getattr(st, f) for f, _ in N.qrt_scene_stats._fields_}
+        self.n_quads = int(st.n_quads)
+        self.n_instances = int(st.n_instances)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            N.lib().qrt_scene_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- ray queries ---------------------------------------------------------
+    def trace_closest(self, rays: torch.Tensor, hits: torch.Tensor | None = None,
+                      tuning: dict | None = None, stream=None) -> torch.Tensor:
+        """rays: float32 [n, 8] on the GPU -> hits int32 [n, 4] (t bits, inst, prim, uv)."""
+        n = rays.shape[0]
+        if hits is None:
+            hits = torch.empty((n, 4), dtype=torch.int32, device=rays.device)
+        t = make_tuning(tuning)
+        N.check(N.lib().qrt_trace_closest(self.handle, _ptr(rays), n, _ptr(hits), C.byref(t),
+                                          _stream(stream)))
+        return hits
+
+    def trace_any(self, rays: torch.Tensor, bits: torch.Tensor | None = None,
+                  tuning: dict | None = None, stream=None) -> torch.Tensor:
+        """rays: float32 [n, 8] -> int32 [ceil(n/32)] occlusion bit words."""
+        n = rays.shape[0]
+        if bits is None:
+            bits = torch.empty(((n + 31) // 32,), dtype=torch.int32, device=rays.device)
+        t = make_tuning(tuning)
+        N.check(N.lib().qrt_trace_any(self.handle, _ptr(rays), n, _ptr(bits), C.byref(t),
+                                      _stream(stream)))
+        return bits
+
+    def trace_stats(self, rays: torch.Tensor, any_hit: bool, out: torch.Tensor,
+                    stats: torch.Tensor, tuning: dict | None = None, stream=None):
+        t = make_tuning(tuning)
+        N.check(N.lib().qrt_trace_stats(self.handle, 1 if any_hit else 0, _ptr(rays), rays.shape[0],
+                                        _ptr(out), C.byref(t), _ptr(stats), _stream(stream)))
+
+    # -- rendering -----------------------------------------------------------
+    def render(self, views, albedo: torch.Tensor, params: Params, outs=None,
+               tuning: dict | None = None, path_log: torch.Tensor | None = None,
+               max_steps: int = 0, stats: torch.Tensor | None = None, stream=None):
+        """Renders views (list of inputs.View) into float32 [h, w, 3] tensors."""
+        if isinstance(views, View):
+            views = [views]
+        if outs is None:
+            outs = [torch.empty((v.h, v.w, 3), dtype=torch.float32, device=albedo.device)
+                    for v in views]
+        cv = make_views(views, outs)
+        cp = make_params(params, tuning, path_log, max_steps)
+        L = N.lib()
+        if stats is None:
+            N.check(L.qrt_render_spp(self.handle, cv, len(views), _ptr(albedo), C.byref(cp),
+                                     _stream(stream)))
+        else:
+            N.check(L.qrt_render_spp_stats(self.handle, cv, len(views), _ptr(albedo), C.byref(cp),
+                                           _ptr(stats), _stream(stream)))
+        return outs
+
+    def adjoint(self, views, albedo: torch.Tensor, dimages, grad: torch.Tensor, params: Params,
+                tuning: dict | None = None, stream=None) -> torch.Tensor:
+        """Adds the albedo gradient of sum(dimage * image) into grad [n_quads, 3]."""
+        if isinstance(views, View):
+            views = [views]
+        cv = make_views(views, [None] * len(views))
+        cp = make_params(params, tuning)
+        dptr = (C.c_void_p * len(views))(*[_ptr(d) for d in dimages])
+        N.check(N.lib().qrt_render_adjoint(self.handle, cv, len(views), _ptr(albedo), dptr,
+                                           _ptr(grad), C.byref(cp), _stream(stream)))
+        return grad
+
+    def check(self, stream=None) -> None:
+        """Raises QrtError if a kernel flagged a stack overflow or step limit."""
+        N.check(N.lib().qrt_check(self.handle, _stream(stream)))
+
+
+class RenderGraph:
+    """One render of fixed views captured as a CUDA graph; launch() replays it."""
+
+    def __init__(self, scene: Scene, views, albedo: torch.Tensor, params: Params, outs=None,
+                 tuning: dict | None = None):
+        if isinstance(views, View):
+            views = [views]
+        if outs is None:
+            outs = [torch.empty((v.h, v.w, 3), dtype=torch.float32, device=albedo.device)
+                    for v in views]
+        self.outs = outs
+        self._keep = (scene, albedo)
+        cv = make_views(views, outs)
+        cp = make_params(params, tuning)
+        h = C.c_void_p()
+        N.check(N.lib().qrt_render_graph_create(scene.handle, cv, len(views), _ptr(albedo),
+                                                C.byref(cp), C.byref(h)))
+        self.handle = h
+
+    def launch(self, stream=None):
+        N.check(N.lib().qrt_graph_launch(self.handle, _stream(stream)))
+        return self.outs
+
+    def close(self):
+        if getattr(self, "handle", None):
+            N.lib().qrt_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def l2_loss(img: torch.Tensor, target: torch.Tensor, dimage: torch.Tensor | None = None,
+            stream=None):
+    """Mean squared error (FP64 scalar tensor) and, if given, its gradient into dimage."""
+    loss = torch.empty((), dtype=torch.float64, device=img.device)
+    N.check(N.lib().qrt_l2_loss(_ptr(img), _ptr(target), img.numel(), _ptr(loss), _ptr(dimage),
+                                _stream(stream)))
+    return loss
+
+
+class RenderFn(torch.autograd.Function):
+    """image = render(albedo); backward runs the path-replay adjoint kernel."""
+
+    @staticmethod
+    def forward(ctx, albedo: torch.Tensor, scene: Scene, view: View, params: Params,
+                tuning: dict | None = None):
+        albedo = albedo.contiguous()
+        (img,) = scene.render([view], albedo, params, tuning=tuning)
+        ctx.scene, ctx.view, ctx.params, ctx.tuning = scene, view, params, tuning
+        ctx.save_for_backward(albedo)
+        return img
+
+    @staticmethod
+    def backward(ctx, grad_img: torch.Tensor):
+        (albedo,) = ctx.saved_tensors
+        grad = torch.zeros_like(albedo)
+        ctx.scene.adjoint([ctx.view], albedo, [grad_img.contiguous()], grad, ctx.params,
+                          tuning=ctx.tuning)
+        return grad, None, None, None, None
+
+
+def render_differentiable(albedo, scene, view, params, tuning=None):
+    return RenderFn.apply(albedo, scene, view, params, tuning)

@@ -1,0 +1,83 @@
+"""Builds libqrt.so in-tree for sm_103a (nvcc for the kernels, the host C++
+compiler for the C ABI and the BVH builder), compiling translation units in
+parallel and skipping the build when nothing changed."""
+from __future__ import annotations
+
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(BUILD, "libqrt.so")
+
+CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+CU_SOURCES = ["trace.cu", "render.cu"]
+CPP_SOURCES = ["capi.cpp", "bvh_build.cpp"]
+HEADERS = ["qrt_layout.h", "launch.h", "traverse.cuh", "bvh_build.h"]
+
+
+def _inputs():
+    files = [os.path.join(CSRC, f) for f in CU_SOURCES + CPP_SOURCES + HEADERS]
+    files.append(os.path.join(INCLUDE, "qrt.h"))
+    files.append(os.path.abspath(__file__))
+    return files
+
+
+def _up_to_date() -> bool:
+    if not os.path.exists(LIB):
+        return False
+    t = os.path.getmtime(LIB)
+    return all(os.path.getmtime(f) <= t for f in _inputs())
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every translation unit and link libqrt.so; returns its path."""
+    if not force and _up_to_date():
+        return LIB
+    os.makedirs(BUILD, exist_ok=True)
+    inc = ["-I", INCLUDE, "-I", CSRC]
+    jobs = []
+    objs = []
+    for f in CU_SOURCES:
+        obj = os.path.join(BUILD, f + ".o")
+        cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+               *inc, "-c", os.path.join(CSRC, f), "-o", obj]
+        jobs.append(cmd)
+        objs.append(obj)
+    for f in CPP_SOURCES:
+        obj = os.path.join(BUILD, f + ".o")
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-pthread",
+               *inc, "-I", os.path.join(CUDA_HOME, "include"), "-c", os.path.join(CSRC, f), "-o", obj]
+        jobs.append(cmd)
+        objs.append(obj)
+    procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
+             for c in jobs]
+    failed = []
+    for c, p in zip(jobs, procs):
+        out, _ = p.communicate()
+        if p.returncode != 0:
+            failed.append((c, out))
+        elif verbose and out:
+            sys.stderr.write(out)
+    if failed:
+        msg = "\n".join(" ".join(c) + "\n" + o for c, o in failed)
+        raise RuntimeError("libqrt build failed:\n" + msg)
+    tmp = LIB + f".tmp{os.getpid()}"
+    link = [NVCC, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
+            "-Xcompiler", "-pthread"]
+    r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("libqrt link failed:\n" + " ".join(link) + "\n" + r.stdout)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose=True))

@@ -1,0 +1,543 @@
+// Host BVH builder (see bvh_build.h).  Binned SAH on item centroids, leaves of
+// up to max_leaf items, collapsed greedily to four children per node (the
+// child with the largest surface area is opened first), child boxes quantised
+// to 8 bits per plane against a power-of-two grid anchored at the node's lower
+// corner and widened until the dequantised box contains the exact one.
+#include "bvh_build.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+
+namespace qrt {
+namespace {
+
+const float kFInf = std::numeric_limits<float>::infinity();
+
+void box_empty(FBox& b) {
+    for (int a = 0; a < 3; ++a) {
+        b.lo[a] = kFInf;
+        b.hi[a] = -kFInf;
+    }
+}
+void box_grow(FBox& b, const FBox& c) {
+    for (int a = 0; a < 3; ++a) {
+        b.lo[a] = std::min(b.lo[a], c.lo[a]);
+        b.hi[a] = std::max(b.hi[a], c.hi[a]);
+    }
+}
+double box_area(const FBox& b) {
+    if (b.lo[0] > b.hi[0]) return 0.0;
+    double dx = (double)b.hi[0] - b.lo[0], dy = (double)b.hi[1] - b.lo[1],
+           dz = (double)b.hi[2] - b.lo[2];
+    return 2.0 * (dx * dy + dy * dz + dz * dx);
+}
+
+struct BinNode {
+    FBox box;
+    int32_t left = -1, right = -1;
+    uint32_t first = 0, count = 0;  // leaf when left < 0
+};
+
+struct Centroid {
+    float c[3];
+};
+
+// Binned-SAH binary build over items [0, n); ids receives the leaf order.
+void build_binary(const std::vector<FBox>& boxes, std::vector<uint32_t>& ids, uint32_t max_leaf,
+                  uint32_t bins, std::vector<BinNode>& nodes) {
+    const uint32_t n = (uint32_t)boxes.size();
+    ids.resize(n);
+    std::vector<Centroid> cen(n);
+    for (uint32_t i = 0; i < n; ++i) {
+        ids[i] = i;
+        for (int a = 0; a < 3; ++a) cen[i].c[a] = 0.5f * boxes[i].lo[a] + 0.5f * boxes[i].hi[a];
+    }
+    nodes.clear();
+    nodes.reserve(2 * (size_t)n / std::max(1u, max_leaf) + 8);
+    nodes.emplace_back();
+    struct Task {
+        int32_t node;
+        uint32_t first, count;
+    };
+    std::vector<Task> work;
+    work.push_back(Task{0, 0, n});
+    std::vector<uint32_t> bcnt(bins);
+    std::vector<FBox> bbox(bins);
+    std::vector<double> right_area(bins);
+    std::vector<uint32_t> right_cnt(bins);
+    while (!work.empty()) {
+        Task tk = work.back();
+        work.pop_back();
+        FBox b, cb;
+        box_empty(b);
+        box_empty(cb);
+        for (uint32_t k = tk.first; k < tk.first + tk.count; ++k) {
+            box_grow(b, boxes[ids[k]]);
+            const Centroid& c = cen[ids[k]];
+            FBox p{{c.c[0], c.c[1], c.c[2]}, {c.c[0], c.c[1], c.c[2]}};
+            box_grow(cb, p);
+        }
+        nodes[tk.node].box = b;
+        if (tk.count <= max_leaf) {
+            nodes[tk.node].first = tk.first;
+            nodes[tk.node].count = tk.count;
+            continue;
+        }
+        int best_axis = -1;
+        uint32_t best_split = 0;
+        double best_cost = std::numeric_limits<double>::infinity();
+        for (int a = 0; a < 3; ++a) {
+            double ext = (double)cb.hi[a] - cb.lo[a];
+            if (!(ext > 0.0)) continue;
+            double scale = (double)bins / ext;
+            std::fill(bcnt.begin(), bcnt.end(), 0u);
+            for (auto& x : bbox) box_empty(x);
+            for (uint32_t k = tk.first; k < tk.first + tk.count; ++k) {
+                uint32_t i = ids[k];
+                int bi = (int)(((double)cen[i].c[a] - cb.lo[a]) * scale);
+                bi = std::min(std::max(bi, 0), (int)bins - 1);
+                bcnt[bi]++;
+                box_grow(bbox[bi], boxes[i]);
+            }
+            FBox acc;
+            box_empty(acc);
+            uint32_t cnt = 0;
+            for (int bi = (int)bins - 1; bi >= 1; --bi) {
+                box_grow(acc, bbox[bi]);
+                cnt += bcnt[bi];
+                right_area[bi] = box_area(acc);
+                right_cnt[bi] = cnt;
+            }
+            box_empty(acc);
+            cnt = 0;
+            for (uint32_t s = 0; s + 1 < bins; ++s) {  // left = bins [0, s]
+                box_grow(acc, bbox[s]);
+                cnt += bcnt[s];
+                uint32_t rc = right_cnt[s + 1];
+                if (cnt == 0 || rc == 0) continue;
+                double cost = box_area(acc) * cnt + right_area[s + 1] * rc;
+                if (cost < best_cost) {
+                    best_cost = cost;
+                    best_axis = a;
+                    best_split = s;
+                }
+            }
+        }
+        uint32_t mid;
+        if (best_axis < 0) {
+            mid = tk.first + tk.count / 2;  // all centroids coincide: split by count
+        } else {
+            double ext = (double)cb.hi[best_axis] - cb.lo[best_axis];
+            double scale = (double)bins / ext;
+            float lo = cb.lo[best_axis];
+            auto it = std::partition(ids.begin() + tk.first, ids.begin() + tk.first + tk.count,
+                                     [&](uint32_t i) {
+                                         int bi = (int)(((double)cen[i].c[best_axis] - lo) * scale);
+                                         bi = std::min(std::max(bi, 0), (int)bins - 1);
+                                         return (uint32_t)bi <= best_split;
+                                     });
+            mid = (uint32_t)(it - ids.begin());
+            if (mid == tk.first || mid == tk.first + tk.count) mid = tk.first + tk.count / 2;
+        }
+        int32_t l = (int32_t)nodes.size();
+        nodes.emplace_back();
+        nodes.emplace_back();
+        nodes[tk.node].left = l;
+        nodes[tk.node].right = l + 1;
+        work.push_back(Task{l + 1, mid, tk.first + tk.count - mid});
+        work.push_back(Task{l, tk.first, mid - tk.first});
+    }
+}
+
+// Chain-shaped binary tree (test aid): every inner node has one leaf of one
+// item and the rest of the chain; after collapsing, each wide node holds the
+// chain continuation in slot 0 and three single-item leaves after it.
+void build_chain(const std::vector<FBox>& boxes, std::vector<uint32_t>& ids,
+                 std::vector<BinNode>& nodes) {
+    const uint32_t n = (uint32_t)boxes.size();
+    ids.resize(n);
+    for (uint32_t i = 0; i < n; ++i) ids[i] = i;
+    nodes.clear();
+    // node for suffix [k, n): inner(leaf k, suffix k+1) until one item remains
+    std::vector<FBox> suffix(n);
+    FBox acc;
+    box_empty(acc);
+    for (int64_t k = (int64_t)n - 1; k >= 0; --k) {
+        box_grow(acc, boxes[k]);
+        suffix[k] = acc;
+    }
+    nodes.emplace_back();
+    int32_t cur = 0;
+    for (uint32_t k = 0; k < n; ++k) {
+        nodes[cur].box = suffix[k];
+        if (k + 1 == n) {
+            nodes[cur].first = k;
+            nodes[cur].count = 1;
+            break;
+        }
+        int32_t rest = (int32_t)nodes.size();
+        nodes.emplace_back();
+        int32_t leaf = (int32_t)nodes.size();
+        nodes.emplace_back();
+        nodes[leaf].box = boxes[k];
+        nodes[leaf].first = k;
+        nodes[leaf].count = 1;
+        nodes[cur].left = rest;  // continuation first, so it sorts first on ties
+        nodes[cur].right = leaf;
+        cur = rest;
+    }
+}
+
+bool quantize(QNode& q, const FBox* cb, int nc) {
+    FBox u;
+    box_empty(u);
+    for (int i = 0; i < nc; ++i) box_grow(u, cb[i]);
+    float origin[3] = {u.lo[0], u.lo[1], u.lo[2]};
+    int8_t ex[3];
+    for (int a = 0; a < 3; ++a) {
+        double ext = (double)u.hi[a] - (double)origin[a];
+        int e = -126;
+        if (ext > 0.0) e = (int)std::ceil(std::log2(ext / 254.0));
+        e = std::max(-126, std::min(127, e));
+        for (;; ++e) {
+            if (e > 127) return false;
+            bool ok = true;
+            const double s = std::ldexp(1.0, e);
+            for (int i = 0; i < nc && ok; ++i) {
+                double fl = std::floor(((double)cb[i].lo[a] - origin[a]) / s);
+                int ql = (int)std::max(0.0, std::min(255.0, fl));
+                while (ql > 0 && dequant((uint8_t)ql, (int8_t)e, origin[a]) > cb[i].lo[a]) --ql;
+                if (dequant((uint8_t)ql, (int8_t)e, origin[a]) > cb[i].lo[a]) {
+                    ok = false;
+                    break;
+                }
+                double ch = std::ceil(((double)cb[i].hi[a] - origin[a]) / s);
+                if (ch > 255.0) {
+                    ok = false;
+                    break;
+                }
+                int qh = (int)std::max(0.0, ch);
+                while (qh <= 255 && dequant((uint8_t)qh, (int8_t)e, origin[a]) < cb[i].hi[a]) ++qh;
+                if (qh > 255) {
+                    ok = false;
+                    break;
+                }
+                q.qlo[a][i] = (uint8_t)ql;
+                q.qhi[a][i] = (uint8_t)qh;
+            }
+            if (ok) break;
+        }
+        ex[a] = (int8_t)e;
+    }
+    q.ox = origin[0];
+    q.oy = origin[1];
+    q.oz = origin[2];
+    q.ex = ex[0];
+    q.ey = ex[1];
+    q.ez = ex[2];
+    return true;
+}
+
+struct Collapser {
+    const std::vector<BinNode>& bn;
+    const std::vector<uint32_t>& ids;
+    bool leaf_holds_id;  // TLAS: leaf child = instance id; BLAS: leaf child = slot
+    std::vector<QNode>& out;
+    uint32_t max_depth = 0;
+    std::string err;
+
+    // Emits the wide node for binary node b; returns its local index or -1.
+    int64_t emit(int32_t b, uint32_t depth) {
+        max_depth = std::max(max_depth, depth);
+        int64_t idx = (int64_t)out.size();
+        if (idx > (int64_t)kMaxLocalIndex) {
+            err = "too many nodes in one object (limit 2^27)";
+            return -1;
+        }
+        out.emplace_back();
+        int32_t ch[4];
+        int nc = 0;
+        if (bn[b].left < 0) {
+            ch[nc++] = b;
+        } else {
+            ch[nc++] = bn[b].left;
+            ch[nc++] = bn[b].right;
+            while (nc < 4) {
+                int pick = -1;
+                double best = -1.0;
+                for (int i = 0; i < nc; ++i) {
+                    if (bn[ch[i]].left < 0) continue;
+                    double a = box_area(bn[ch[i]].box);
+                    if (a > best) {
+                        best = a;
+                        pick = i;
+                    }
+                }
+                if (pick < 0) break;
+                int32_t c = ch[pick];
+                for (int i = nc; i > pick + 1; --i) ch[i] = ch[i - 1];
+                ch[pick] = bn[c].left;
+                ch[pick + 1] = bn[c].right;
+                ++nc;
+            }
+        }
+        QNode q;
+        std::memset(&q, 0, sizeof(q));
+        FBox cb[4];
+        uint32_t childv[4] = {0, 0, 0, 0};
+        uint8_t meta[4] = {0, 0, 0, 0};
+        for (int i = 0; i < nc; ++i) {
+            const BinNode& c = bn[ch[i]];
+            cb[i] = c.box;
+            if (c.left < 0) {
+                if (c.count == 0 || c.count > kMaxLeaf) {
+                    err = "leaf size out of range";
+                    return -1;
+                }
+                uint32_t first = leaf_holds_id ? ids[c.first] : c.first;
+                if (first > kMaxLocalIndex) {
+                    err = "item index beyond 2^27 within one object";
+                    return -1;
+                }
+                childv[i] = first;
+                meta[i] = (uint8_t)c.count;
+            } else {
+                int64_t k = emit(ch[i], depth + 1);
+                if (k < 0) return -1;
+                childv[i] = (uint32_t)k;
+                meta[i] = kMetaInner;
+            }
+        }
+        if (!quantize(q, cb, nc)) {
+            err = "box quantisation failed (coordinates out of range)";
+            return -1;
+        }
+        for (int i = 0; i < 4; ++i) {
+            q.child[i] = childv[i];
+            q.meta[i] = meta[i];
+        }
+        q.nchild = (uint8_t)nc;
+        out[idx] = q;
+        return idx;
+    }
+};
+
+bool finite_box(const FBox& b) {
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(b.lo[a]) || !std::isfinite(b.hi[a])) return false;
+    return true;
+}
+
+}  // namespace
+
+float dequant(uint8_t q, int8_t e, float origin) {
+    return std::fmaf((float)q, std::ldexp(1.0f, e), origin);
+}
+
+FBox transform_box(const FBox& b, const float* x) {
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int k = 0; k < 8; ++k) {
+        double p[3] = {(k & 1) ? b.hi[0] : b.lo[0], (k & 2) ? b.hi[1] : b.lo[1],
+                       (k & 4) ? b.hi[2] : b.lo[2]};
+        for (int r = 0; r < 3; ++r) {
+            double w = (double)x[4 * r] * p[0] + (double)x[4 * r + 1] * p[1] +
+                       (double)x[4 * r + 2] * p[2] + (double)x[4 * r + 3];
+            lo[r] = std::min(lo[r], w);
+            hi[r] = std::max(hi[r], w);
+        }
+    }
+    FBox out;
+    for (int r = 0; r < 3; ++r) {
+        // widen by a relative 1e-12 to cover the FP64 rounding above, then
+        // round outward to float
+        double pad = 1e-12 * (std::fabs(lo[r]) + std::fabs(hi[r]) + 1e-30);
+        double l = lo[r] - pad, h = hi[r] + pad;
+        float fl = (float)l, fh = (float)h;
+        if ((double)fl > l) fl = std::nextafter(fl, -kFInf);
+        if ((double)fh < h) fh = std::nextafter(fh, kFInf);
+        out.lo[r] = fl;
+        out.hi[r] = fh;
+    }
+    return out;
+}
+
+bool build_blas(const float* verts, uint32_t n_verts, const uint32_t* quads, uint32_t n_quads,
+                const BuildOpts& opts, BlasResult& out, std::string& err) {
+    if (n_quads == 0) {
+        err = "mesh has no quads";
+        return false;
+    }
+    if (n_quads > kMaxLocalIndex) {
+        err = "mesh has more than 2^27 quads";
+        return false;
+    }
+    std::vector<FBox> boxes(n_quads);
+    for (uint32_t q = 0; q < n_quads; ++q) {
+        FBox b;
+        box_empty(b);
+        for (int k = 0; k < 4; ++k) {
+            uint32_t vi = quads[4 * (size_t)q + k];
+            if (vi >= n_verts) {
+                err = "quad vertex index out of range";
+                return false;
+            }
+            const float* v = verts + 3 * (size_t)vi;
+            if (!std::isfinite(v[0]) || !std::isfinite(v[1]) || !std::isfinite(v[2])) {
+                err = "non-finite vertex";
+                return false;
+            }
+            FBox p{{v[0], v[1], v[2]}, {v[0], v[1], v[2]}};
+            box_grow(b, p);
+        }
+        if (!finite_box(b)) {
+            err = "non-finite vertex";
+            return false;
+        }
+        boxes[q] = b;
+    }
+    std::vector<BinNode> bn;
+    std::vector<uint32_t> ids;
+    if (opts.degenerate)
+        build_chain(boxes, ids, bn);
+    else
+        build_binary(boxes, ids, std::max(1u, std::min(opts.max_leaf, 8u)),
+                     std::max(4u, std::min(opts.sah_bins, 64u)), bn);
+    out.nodes.clear();
+    Collapser col{bn, ids, false, out.nodes};
+    if (col.emit(0, 1) < 0) {
+        err = col.err;
+        return false;
+    }
+    out.depth = col.max_depth;
+    out.quads.resize(n_quads);
+    out.prim.resize(n_quads);
+    for (uint32_t s = 0; s < n_quads; ++s) {
+        uint32_t q = ids[s];
+        out.prim[s] = q;
+        for (int k = 0; k < 4; ++k) {
+            const float* v = verts + 3 * (size_t)quads[4 * (size_t)q + k];
+            out.quads[s].v[3 * k] = v[0];
+            out.quads[s].v[3 * k + 1] = v[1];
+            out.quads[s].v[3 * k + 2] = v[2];
+        }
+    }
+    out.box = bn[0].box;
+    return true;
+}
+
+bool build_tlas(const std::vector<FBox>& inst_boxes, const BuildOpts& opts, TlasResult& out,
+                std::string& err) {
+    out.nodes.clear();
+    out.depth = 0;
+    if (inst_boxes.empty()) return true;
+    if (inst_boxes.size() > kMaxLocalIndex) {
+        err = "more than 2^27 instances";
+        return false;
+    }
+    for (const FBox& b : inst_boxes)
+        if (!finite_box(b)) {
+            err = "non-finite instance bounds";
+            return false;
+        }
+    std::vector<BinNode> bn;
+    std::vector<uint32_t> ids;
+    build_binary(inst_boxes, ids, 1, std::max(4u, std::min(opts.sah_bins, 64u)), bn);
+    Collapser col{bn, ids, true, out.nodes};
+    if (col.emit(0, 1) < 0) {
+        err = col.err;
+        return false;
+    }
+    out.depth = col.max_depth;
+    return true;
+}
+
+namespace {
+struct Checker {
+    const std::vector<QNode>& nodes;
+    const std::vector<FBox>& items;
+    std::vector<uint8_t> seen;
+    std::string err;
+    uint32_t depth = 0;
+
+    bool rec(uint32_t idx, uint32_t d, FBox& box) {
+        depth = std::max(depth, d);
+        if (idx >= nodes.size()) {
+            err = "child node index out of range";
+            return false;
+        }
+        const QNode& n = nodes[idx];
+        box_empty(box);
+        const float org[3] = {n.ox, n.oy, n.oz};
+        const int8_t ex[3] = {n.ex, n.ey, n.ez};
+        int valid = 0;
+        for (int i = 0; i < 4; ++i) {
+            if (n.meta[i] == 0) continue;
+            ++valid;
+            FBox cb;
+            if (n.meta[i] == kMetaInner) {
+                if (!rec(n.child[i], d + 1, cb)) return false;
+            } else {
+                if (n.meta[i] > kMaxLeaf) {
+                    err = "leaf count too large";
+                    return false;
+                }
+                box_empty(cb);
+                for (uint32_t k = 0; k < n.meta[i]; ++k) {
+                    uint32_t it = n.child[i] + k;
+                    if (it >= items.size()) {
+                        err = "leaf item out of range";
+                        return false;
+                    }
+                    if (seen[it]++) {
+                        err = "item referenced twice";
+                        return false;
+                    }
+                    box_grow(cb, items[it]);
+                }
+            }
+            for (int a = 0; a < 3; ++a) {
+                float lo = dequant(n.qlo[a][i], ex[a], org[a]);
+                float hi = dequant(n.qhi[a][i], ex[a], org[a]);
+                if (!(lo <= cb.lo[a] && hi >= cb.hi[a])) {
+                    err = "quantised child box does not contain its subtree";
+                    return false;
+                }
+            }
+            box_grow(box, cb);
+        }
+        if (valid == 0 || valid != n.nchild) {
+            err = "node child count inconsistent";
+            return false;
+        }
+        return true;
+    }
+};
+}  // namespace
+
+bool check_wide(const std::vector<QNode>& nodes, const std::vector<FBox>& item_boxes,
+                std::string& err, uint32_t* depth) {
+    if (nodes.empty()) {
+        if (!item_boxes.empty()) {
+            err = "no nodes for a non-empty item set";
+            return false;
+        }
+        return true;
+    }
+    Checker c{nodes, item_boxes, std::vector<uint8_t>(item_boxes.size(), 0), {}, 0};
+    FBox b;
+    if (!c.rec(0, 1, b)) {
+        err = c.err;
+        return false;
+    }
+    for (size_t i = 0; i < c.seen.size(); ++i)
+        if (c.seen[i] != 1) {
+            err = "item not referenced";
+            return false;
+        }
+    if (depth) *depth = c.depth;
+    return true;
+}
+
+}  // namespace qrt

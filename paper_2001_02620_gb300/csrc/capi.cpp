@@ -1,0 +1,740 @@
+// C ABI of the qrt library (include/qrt.h): argument checking, scene
+// construction and upload, work-counter slots, launch configuration, CUDA
+// graphs and the device error word.
+#include "qrt.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "bvh_build.h"
+#include "launch.h"
+
+using namespace qrt;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? QRT_ERR_OOM : QRT_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+constexpr int kCounterSlots = 64;
+constexpr size_t kSlotStride = 128;  // bytes between counters (own cache line)
+
+}  // namespace
+
+struct qrt_scene_s {
+    int device = -1;
+    int sm_count = 0;
+    DevScene S{};
+    void* d_nodes = nullptr;
+    void* d_quads = nullptr;
+    void* d_prim = nullptr;
+    void* d_inst = nullptr;
+    void* d_inst64 = nullptr;
+    uint32_t* d_err = nullptr;
+    char* d_counters = nullptr;  // kCounterSlots counters, kSlotStride apart
+    std::mutex mu;
+    std::unordered_map<cudaStream_t, int> slot_of;
+    int next_slot = 0;
+    qrt_scene_stats stats{};
+
+    // One work counter per stream: calls on one stream are ordered, so they
+    // may share it; different streams get different counters.
+    unsigned long long* counter_for(cudaStream_t s) {
+        std::lock_guard<std::mutex> g(mu);
+        auto it = slot_of.find(s);
+        int slot;
+        if (it != slot_of.end()) {
+            slot = it->second;
+        } else {
+            slot = next_slot % kCounterSlots;
+            next_slot++;
+            slot_of[s] = slot;
+        }
+        return reinterpret_cast<unsigned long long*>(d_counters + kSlotStride * slot);
+    }
+};
+
+struct qrt_graph_s {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long* d_counter = nullptr;
+    int device = -1;
+};
+
+namespace {
+
+void free_scene(qrt_scene_s* s) {
+    if (!s) return;
+    cudaFree(s->d_nodes);
+    cudaFree(s->d_quads);
+    cudaFree(s->d_prim);
+    cudaFree(s->d_inst);
+    cudaFree(s->d_inst64);
+    cudaFree(s->d_err);
+    cudaFree(s->d_counters);
+    delete s;
+}
+
+int check_device(const qrt_scene_s* s) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != s->device)
+        return fail(QRT_ERR_INVALID_ARG, "scene belongs to device " + std::to_string(s->device) +
+                                             " but device " + std::to_string(dev) + " is current");
+    return QRT_OK;
+}
+
+Tune resolve_tuning(const qrt_tuning* t) {
+    Tune r;
+    if (!t) return r;
+    if (t->block) r.block = (int)t->block;
+    if (t->blocks_per_sm) r.blocks_per_sm = (int)t->blocks_per_sm;
+    if (t->batch) r.batch = (int)t->batch;
+    if (t->stack) r.stack = (int)t->stack;
+    if (t->fetch) r.fetch = (int)t->fetch;
+    if (t->adjoint_mode) r.adjoint_mode = (int)t->adjoint_mode;
+    return r;
+}
+
+int validate_tuning(const Tune& t) {
+    if (t.block != 64 && t.block != 128 && t.block != 192 && t.block != 256)
+        return fail(QRT_ERR_INVALID_ARG, "tuning.block must be 64, 128, 192 or 256");
+    if (t.stack != 32 && t.stack != 64)
+        return fail(QRT_ERR_INVALID_ARG, "tuning.stack must be 32 or 64");
+    if (t.fetch != 16 && t.fetch != 32)
+        return fail(QRT_ERR_INVALID_ARG, "tuning.fetch must be 16 or 32");
+    if (t.batch < 1 || t.batch > 64) return fail(QRT_ERR_INVALID_ARG, "tuning.batch must be 1..64");
+    if (t.blocks_per_sm < 0 || t.blocks_per_sm > 32)
+        return fail(QRT_ERR_INVALID_ARG, "tuning.blocks_per_sm must be 0..32");
+    if (t.adjoint_mode < 1 || t.adjoint_mode > 2)
+        return fail(QRT_ERR_INVALID_ARG, "tuning.adjoint_mode must be 0, 1 or 2");
+    return QRT_OK;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// 3x3 inverse by the adjugate, FP64.  Returns false for singular input.
+bool inverse3(const double* m, double* r) {
+    double c00 = m[4] * m[8] - m[5] * m[7];
+    double c01 = m[5] * m[6] - m[3] * m[8];
+    double c02 = m[3] * m[7] - m[4] * m[6];
+    double det = m[0] * c00 + m[1] * c01 + m[2] * c02;
+    double scale = 0.0;
+    for (int k = 0; k < 9; ++k) scale = std::max(scale, std::fabs(m[k]));
+    if (!std::isfinite(det) || std::fabs(det) <= 1e-30 * scale * scale * scale || scale == 0.0)
+        return false;
+    double id = 1.0 / det;
+    r[0] = c00 * id;
+    r[1] = (m[2] * m[7] - m[1] * m[8]) * id;
+    r[2] = (m[1] * m[5] - m[2] * m[4]) * id;
+    r[3] = c01 * id;
+    r[4] = (m[0] * m[8] - m[2] * m[6]) * id;
+    r[5] = (m[2] * m[3] - m[0] * m[5]) * id;
+    r[6] = c02 * id;
+    r[7] = (m[1] * m[6] - m[0] * m[7]) * id;
+    r[8] = (m[0] * m[4] - m[1] * m[3]) * id;
+    return true;
+}
+
+BuildOpts resolve_build(const qrt_build_opts* o) {
+    BuildOpts b;
+    if (!o) return b;
+    if (o->max_leaf) b.max_leaf = o->max_leaf;
+    if (o->sah_bins) b.sah_bins = o->sah_bins;
+    b.threads = o->threads;
+    b.degenerate = o->degenerate;
+    return b;
+}
+
+template <class T>
+cudaError_t upload(void** dptr, const std::vector<T>& v) {
+    size_t bytes = std::max<size_t>(v.size() * sizeof(T), 64);
+    cudaError_t e = cudaMalloc(dptr, bytes);
+    if (e != cudaSuccess) return e;
+    if (!v.empty()) e = cudaMemcpy(*dptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* qrt_last_error(void) { return g_err.c_str(); }
+
+int qrt_version(void) { return QRT_VERSION; }
+
+int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xforms,
+                     const uint32_t* mesh_ids, uint64_t n_inst, const qrt_build_opts* opts,
+                     qrt_scene* out) {
+    if (!out) return fail(QRT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!meshes || n_mesh == 0) return fail(QRT_ERR_INVALID_ARG, "no meshes");
+    if (n_inst > 0 && (!xforms || !mesh_ids))
+        return fail(QRT_ERR_INVALID_ARG, "xforms or mesh_ids is NULL");
+    if (n_inst > (uint64_t)kMaxLocalIndex) return fail(QRT_ERR_INVALID_ARG, "too many instances");
+    for (uint32_t m = 0; m < n_mesh; ++m) {
+        if (!meshes[m].verts || !meshes[m].quads || meshes[m].n_quads == 0 || meshes[m].n_verts == 0)
+            return fail(QRT_ERR_INVALID_ARG, "mesh " + std::to_string(m) + " is empty or NULL");
+    }
+    for (uint64_t i = 0; i < n_inst; ++i)
+        if (mesh_ids[i] >= n_mesh)
+            return fail(QRT_ERR_INVALID_ARG, "instance " + std::to_string(i) + " names mesh " +
+                                                 std::to_string(mesh_ids[i]) + " out of range");
+    const BuildOpts bo = resolve_build(opts);
+    auto t0 = std::chrono::steady_clock::now();
+
+    // 1. one BLAS per mesh, largest first, on a pool of host threads
+    std::vector<BlasResult> blas(n_mesh);
+    std::vector<std::string> errs(n_mesh);
+    std::vector<uint32_t> order(n_mesh);
+    for (uint32_t m = 0; m < n_mesh; ++m) order[m] = m;
+    std::sort(order.begin(), order.end(),
+              [&](uint32_t a, uint32_t b) { return meshes[a].n_quads > meshes[b].n_quads; });
+    {
+        unsigned nt = bo.threads ? bo.threads : std::max(1u, std::thread::hardware_concurrency());
+        nt = std::min<unsigned>(nt, n_mesh);
+        std::atomic<uint32_t> next{0};
+        auto work = [&]() {
+            for (;;) {
+                uint32_t k = next.fetch_add(1);
+                if (k >= n_mesh) break;
+                uint32_t m = order[k];
+                build_blas(meshes[m].verts, meshes[m].n_verts, meshes[m].quads, meshes[m].n_quads,
+                           bo, blas[m], errs[m]);
+            }
+        };
+        std::vector<std::thread> th;
+        for (unsigned k = 1; k < nt; ++k) th.emplace_back(work);
+        work();
+        for (auto& t : th) t.join();
+    }
+    for (uint32_t m = 0; m < n_mesh; ++m)
+        if (!errs[m].empty()) return fail(QRT_ERR_INVALID_ARG, "mesh " + std::to_string(m) + ": " + errs[m]);
+    // Verify every BLAS before anything reaches the device: all child and
+    // item indices in range, each quad referenced once, boxes conservative.
+    {
+        std::atomic<uint32_t> next{0};
+        unsigned nt = bo.threads ? bo.threads : std::max(1u, std::thread::hardware_concurrency());
+        nt = std::min<unsigned>(nt, n_mesh);
+        auto work = [&]() {
+            for (;;) {
+                uint32_t m = next.fetch_add(1);
+                if (m >= n_mesh) break;
+                std::vector<FBox> items(blas[m].quads.size());
+                for (size_t k = 0; k < items.size(); ++k) {
+                    const float* v = blas[m].quads[k].v;
+                    for (int a = 0; a < 3; ++a) {
+                        items[k].lo[a] = std::min(std::min(v[a], v[3 + a]), std::min(v[6 + a], v[9 + a]));
+                        items[k].hi[a] = std::max(std::max(v[a], v[3 + a]), std::max(v[6 + a], v[9 + a]));
+                    }
+                }
+                uint32_t d = 0;
+                if (!check_wide(blas[m].nodes, items, errs[m], &d)) errs[m] = "BLAS check: " + errs[m];
+            }
+        };
+        std::vector<std::thread> th;
+        for (unsigned k = 1; k < nt; ++k) th.emplace_back(work);
+        work();
+        for (auto& t : th) t.join();
+    }
+    for (uint32_t m = 0; m < n_mesh; ++m)
+        if (!errs[m].empty()) return fail(QRT_ERR_INVALID_ARG, "mesh " + std::to_string(m) + ": " + errs[m]);
+
+    // 2. global layout: BLAS nodes mesh by mesh, then the TLAS
+    std::vector<uint64_t> node_base(n_mesh), quad_base(n_mesh);
+    uint64_t nn = 0, nq = 0;
+    uint32_t max_blas_depth = 0;
+    for (uint32_t m = 0; m < n_mesh; ++m) {
+        node_base[m] = nn;
+        quad_base[m] = nq;
+        nn += blas[m].nodes.size();
+        nq += blas[m].quads.size();
+        max_blas_depth = std::max(max_blas_depth, blas[m].depth);
+    }
+    if (nq > 0xFFFFFFFFull || nn > 0xFFFFFFFFull)
+        return fail(QRT_ERR_INVALID_ARG, "scene exceeds 2^32 quads or nodes");
+
+    // 3. instances: FP64 inverse, FP32 copy, world boxes
+    std::vector<InstDev> inst(n_inst);
+    std::vector<double> inst64(12 * n_inst);
+    std::vector<FBox> wbox(n_inst);
+    std::vector<float> meshR(n_mesh);
+    for (uint32_t m = 0; m < n_mesh; ++m) {
+        float r = 0.f;
+        for (int a = 0; a < 3; ++a)
+            r = std::max(r, std::max(std::fabs(blas[m].box.lo[a]), std::fabs(blas[m].box.hi[a])));
+        meshR[m] = r;
+    }
+    for (uint64_t i = 0; i < n_inst; ++i) {
+        const float* x = xforms + 12 * i;
+        double A[9], Ai[9];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) A[3 * r + c] = x[4 * r + c];
+        bool finite = true;
+        for (int k = 0; k < 12; ++k) finite = finite && std::isfinite(x[k]);
+        if (!finite || !inverse3(A, Ai))
+            return fail(QRT_ERR_INVALID_ARG,
+                        "instance " + std::to_string(i) + " has a non-finite or singular transform");
+        double* w = &inst64[12 * i];
+        for (int r = 0; r < 3; ++r) {
+            for (int c = 0; c < 3; ++c) w[4 * r + c] = Ai[3 * r + c];
+            w[4 * r + 3] = -(Ai[3 * r] * x[3] + Ai[3 * r + 1] * x[7] + Ai[3 * r + 2] * x[11]);
+        }
+        InstDev& I = inst[i];
+        for (int k = 0; k < 12; ++k) I.w2o[k] = (float)w[k];
+        const uint32_t m = mesh_ids[i];
+        I.node_base = (uint32_t)node_base[m];
+        I.quad_base = (uint32_t)quad_base[m];
+        I.R = meshR[m];
+        I.mesh_id = m;
+        wbox[i] = transform_box(blas[m].box, x);
+    }
+    TlasResult tlas;
+    std::string terr;
+    if (!build_tlas(wbox, bo, tlas, terr)) return fail(QRT_ERR_INVALID_ARG, "TLAS: " + terr);
+    {
+        uint32_t d = 0;
+        if (!check_wide(tlas.nodes, wbox, terr, &d)) return fail(QRT_ERR_INVALID_ARG, "TLAS check: " + terr);
+    }
+    const uint64_t tlas_base = nn;
+    if (nn + tlas.nodes.size() > 0xFFFFFFFFull) return fail(QRT_ERR_INVALID_ARG, "too many nodes");
+    float R_top = 0.f;
+    for (const FBox& b : wbox)
+        for (int a = 0; a < 3; ++a) R_top = std::max(R_top, std::max(std::fabs(b.lo[a]), std::fabs(b.hi[a])));
+
+    // 4. concatenate: inner node references stay local to their structure
+    std::vector<QNode> nodes;
+    nodes.reserve(nn + tlas.nodes.size());
+    std::vector<QuadDev> quads;
+    quads.reserve(nq);
+    std::vector<uint32_t> prim;
+    prim.reserve(nq);
+    for (uint32_t m = 0; m < n_mesh; ++m) {
+        nodes.insert(nodes.end(), blas[m].nodes.begin(), blas[m].nodes.end());
+        quads.insert(quads.end(), blas[m].quads.begin(), blas[m].quads.end());
+        prim.insert(prim.end(), blas[m].prim.begin(), blas[m].prim.end());
+        std::vector<QNode>().swap(blas[m].nodes);
+        std::vector<QuadDev>().swap(blas[m].quads);
+        std::vector<uint32_t>().swap(blas[m].prim);
+    }
+    nodes.insert(nodes.end(), tlas.nodes.begin(), tlas.nodes.end());
+    const double build_s =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+
+    // 5. upload
+    qrt_scene_s* s = new qrt_scene_s();
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e != cudaSuccess) {
+        delete s;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    e = cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device);
+    if (e == cudaSuccess) e = upload(&s->d_nodes, nodes);
+    if (e == cudaSuccess) e = upload(&s->d_quads, quads);
+    if (e == cudaSuccess) e = upload(&s->d_prim, prim);
+    if (e == cudaSuccess) e = upload(&s->d_inst, inst);
+    if (e == cudaSuccess) e = upload(&s->d_inst64, inst64);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_err, 2 * sizeof(uint32_t));
+    if (e == cudaSuccess) {
+        const uint32_t init[2] = {0u, 0xFFFFFFFFu};
+        e = cudaMemcpy(s->d_err, init, sizeof(init), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_counters, kCounterSlots * kSlotStride);
+    if (e == cudaSuccess) e = cudaMemset(s->d_counters, 0, kCounterSlots * kSlotStride);
+    if (e != cudaSuccess) {
+        free_scene(s);
+        return cuda_fail(e, "scene upload");
+    }
+    s->S.nodes = static_cast<const QNode*>(s->d_nodes);
+    s->S.quads = static_cast<const QuadDev*>(s->d_quads);
+    s->S.prim = static_cast<const uint32_t*>(s->d_prim);
+    s->S.inst = static_cast<const InstDev*>(s->d_inst);
+    s->S.inst64 = static_cast<const double*>(s->d_inst64);
+    s->S.tlas_base = (uint32_t)tlas_base;
+    s->S.n_inst = (uint32_t)n_inst;
+    s->S.R_top = R_top;
+    s->S.err = s->d_err;
+    s->stats.n_meshes = n_mesh;
+    s->stats.n_instances = n_inst;
+    s->stats.n_quads = nq;
+    s->stats.blas_nodes = nn;
+    s->stats.tlas_nodes = tlas.nodes.size();
+    s->stats.device_bytes = nodes.size() * sizeof(QNode) + quads.size() * sizeof(QuadDev) +
+                            prim.size() * 4 + inst.size() * sizeof(InstDev) + inst64.size() * 8;
+    s->stats.max_blas_depth = max_blas_depth;
+    s->stats.tlas_depth = tlas.depth;
+    s->stats.build_seconds = build_s;
+    *out = s;
+    return QRT_OK;
+}
+
+int qrt_scene_destroy(qrt_scene scene) {
+    if (!scene) return fail(QRT_ERR_INVALID_ARG, "scene is NULL");
+    free_scene(scene);
+    return QRT_OK;
+}
+
+int qrt_scene_stats_get(qrt_scene scene, qrt_scene_stats* out) {
+    if (!scene || !out) return fail(QRT_ERR_INVALID_ARG, "NULL argument");
+    *out = scene->stats;
+    return QRT_OK;
+}
+
+static int trace_common(bool any, qrt_scene scene, const qrt_ray* d_rays, uint64_t n, void* out,
+                        const qrt_tuning* tuning, qrt_stream stream) {
+    if (!scene) return fail(QRT_ERR_INVALID_ARG, "scene is NULL");
+    if (n == 0) return QRT_OK;
+    if (!d_rays || !out) return fail(QRT_ERR_INVALID_ARG, "NULL device pointer");
+    if (!aligned(d_rays, 16) || !aligned(out, any ? 4 : 16))
+        return fail(QRT_ERR_ALIGN, "rays/hits must be 16-byte aligned (occlusion bits 4-byte)");
+    Tune t = resolve_tuning(tuning);
+    int rc = validate_tuning(t);
+    if (rc) return rc;
+    rc = check_device(scene);
+    if (rc) return rc;
+    cudaError_t e = launch_trace(any, scene->S, d_rays, n, any ? nullptr : out,
+                                 any ? static_cast<uint32_t*>(out) : nullptr, 1u << 20, nullptr, t,
+                                 reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "trace launch");
+    return QRT_OK;
+}
+
+int qrt_trace_closest(qrt_scene scene, const qrt_ray* d_rays, uint64_t n, qrt_hit* d_hits,
+                      const qrt_tuning* tuning, qrt_stream stream) {
+    return trace_common(false, scene, d_rays, n, d_hits, tuning, stream);
+}
+
+int qrt_trace_any(qrt_scene scene, const qrt_ray* d_rays, uint64_t n, uint32_t* d_occ_bits,
+                  const qrt_tuning* tuning, qrt_stream stream) {
+    return trace_common(true, scene, d_rays, n, d_occ_bits, tuning, stream);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Builds the device view table for views[first, first+count).
+int make_views(const qrt_view* views, uint32_t first, uint32_t count, const float* const* d_dimage,
+               RenderArgs& A, uint64_t path_begin0) {
+    uint64_t items = 0, paths = path_begin0;
+    for (uint32_t k = 0; k < count; ++k) {
+        const qrt_view& v = views[first + k];
+        if (v.w == 0 || v.h == 0 || v.spp == 0)
+            return fail(QRT_ERR_INVALID_ARG, "view " + std::to_string(first + k) + " has zero size or spp");
+        if (!v.out_rgb && !d_dimage)
+            return fail(QRT_ERR_INVALID_ARG, "view " + std::to_string(first + k) + " has no out_rgb");
+        if (v.out_rgb && !aligned(v.out_rgb, 4)) return fail(QRT_ERR_ALIGN, "out_rgb must be 4-byte aligned");
+        double eye[3] = {v.eye[0], v.eye[1], v.eye[2]};
+        double f[3] = {v.look[0] - eye[0], v.look[1] - eye[1], v.look[2] - eye[2]};
+        double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+        if (!(fl > 0.0)) return fail(QRT_ERR_INVALID_ARG, "camera eye equals look");
+        for (double& c : f) c /= fl;
+        double up[3] = {v.up[0], v.up[1], v.up[2]};
+        double r[3] = {f[1] * up[2] - f[2] * up[1], f[2] * up[0] - f[0] * up[2], f[0] * up[1] - f[1] * up[0]};
+        double rl = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        if (!(rl > 0.0)) return fail(QRT_ERR_INVALID_ARG, "camera up is parallel to the view direction");
+        for (double& c : r) c /= rl;
+        double u[3] = {r[1] * f[2] - r[2] * f[1], r[2] * f[0] - r[0] * f[2], r[0] * f[1] - r[1] * f[0]};
+        if (!(v.vfov_deg > 0.f && v.vfov_deg < 180.f))
+            return fail(QRT_ERR_INVALID_ARG, "vfov_deg must be in (0, 180)");
+        const double th = std::tan(0.5 * (double)v.vfov_deg * 3.14159265358979323846 / 180.0);
+        const double aspect = (double)v.w / (double)v.h;
+        ViewDev& d = A.views[k];
+        for (int c = 0; c < 3; ++c) {
+            d.eye[c] = v.eye[c];
+            d.f[c] = (float)f[c];
+            d.r[c] = (float)r[c];
+            d.u[c] = (float)u[c];
+        }
+        d.sx0 = (float)(-th * aspect);
+        d.sxs = (float)(2.0 * th * aspect / v.w);
+        d.sy0 = (float)th;
+        d.sys = (float)(-2.0 * th / v.h);
+        d.w = v.w;
+        d.h = v.h;
+        d.spp = v.spp;
+        d.pad = 0;
+        d.pixel_base = v.pixel_base;
+        d.item_begin = items;
+        d.path_begin = paths;
+        d.out = v.out_rgb;
+        d.dimage = d_dimage ? d_dimage[first + k] : nullptr;
+        if (d_dimage && !d.dimage)
+            return fail(QRT_ERR_INVALID_ARG, "d_dimage[" + std::to_string(first + k) + "] is NULL");
+        items += (uint64_t)v.w * v.h;
+        paths += (uint64_t)v.w * v.h * v.spp;
+    }
+    A.n_items = items;
+    A.n_views = count;
+    return QRT_OK;
+}
+
+int make_params(const qrt_params* p, ParamsDev& P) {
+    if (!p) return fail(QRT_ERR_INVALID_ARG, "params is NULL");
+    if (p->max_depth < 1 || p->max_depth > 256)
+        return fail(QRT_ERR_INVALID_ARG, "max_depth must be 1..256");
+    P.max_depth = p->max_depth;
+    P.max_steps = p->max_steps ? p->max_steps : (1u << 20);
+    P.seed = p->seed;
+    for (int c = 0; c < 3; ++c) {
+        P.env[c] = p->env[c];
+        P.sun_E[c] = p->sun_E[c];
+    }
+    P.sun_on = (p->sun_E[0] != 0.f || p->sun_E[1] != 0.f || p->sun_E[2] != 0.f) ? 1u : 0u;
+    const double sl = std::sqrt((double)p->sun_dir[0] * p->sun_dir[0] + (double)p->sun_dir[1] * p->sun_dir[1] +
+                                (double)p->sun_dir[2] * p->sun_dir[2]);
+    if (P.sun_on && !(sl > 0.0)) return fail(QRT_ERR_INVALID_ARG, "sun_dir is zero");
+    for (int c = 0; c < 3; ++c) P.sun_l[c] = sl > 0.0 ? (float)(p->sun_dir[c] / sl) : 0.f;
+    P.path_log = p->d_path_log;
+    if (P.path_log && !aligned(P.path_log, 4)) return fail(QRT_ERR_ALIGN, "d_path_log must be 4-byte aligned");
+    return QRT_OK;
+}
+
+// Enqueues the render (or adjoint) of all views on stream s using counter.
+int render_enqueue(qrt_scene scene, const qrt_view* views, uint32_t n_views, const float* d_albedo,
+                   const float* const* d_dimage, float* d_grad, const qrt_params* params,
+                   unsigned long long* counter, unsigned long long* stats, cudaStream_t s) {
+    Tune t = resolve_tuning(params ? &params->tuning : nullptr);
+    int rc = validate_tuning(t);
+    if (rc) return rc;
+    static_assert(sizeof(RenderArgs) < 32000, "kernel parameter block too large");
+    RenderArgs* A = new RenderArgs();
+    std::memset(A, 0, sizeof(RenderArgs));
+    A->S = scene->S;
+    A->albedo = d_albedo;
+    A->grad = d_grad;
+    A->counter = counter;
+    A->stats = stats;
+    A->batch = (uint32_t)t.batch;
+    rc = make_params(params, A->P);
+    uint64_t paths = 0;
+    for (uint32_t first = 0; rc == QRT_OK && first < n_views; first += kMaxViewsPerLaunch) {
+        const uint32_t cnt = std::min<uint32_t>(kMaxViewsPerLaunch, n_views - first);
+        rc = make_views(views, first, cnt, d_dimage, *A, paths);
+        if (rc) break;
+        for (uint32_t k = 0; k < cnt; ++k)
+            paths += (uint64_t)views[first + k].w * views[first + k].h * views[first + k].spp;
+        cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+        if (e == cudaSuccess) e = launch_render(*A, t, scene->sm_count, s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "render launch");
+    }
+    delete A;
+    return rc;
+}
+
+int render_args_check(qrt_scene scene, const qrt_view* views, uint32_t n_views, const float* d_albedo) {
+    if (!scene) return fail(QRT_ERR_INVALID_ARG, "scene is NULL");
+    if (n_views > 0 && !views) return fail(QRT_ERR_INVALID_ARG, "views is NULL");
+    if (n_views > 0 && !d_albedo) return fail(QRT_ERR_INVALID_ARG, "d_albedo is NULL");
+    if (d_albedo && !aligned(d_albedo, 4)) return fail(QRT_ERR_ALIGN, "d_albedo must be 4-byte aligned");
+    return check_device(scene);
+}
+
+}  // namespace
+
+extern "C" {
+
+int qrt_render_spp(qrt_scene scene, const qrt_view* views, uint32_t n_views, const float* d_albedo,
+                   const qrt_params* params, qrt_stream stream) {
+    int rc = render_args_check(scene, views, n_views, d_albedo);
+    if (rc) return rc;
+    if (n_views == 0) return QRT_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return render_enqueue(scene, views, n_views, d_albedo, nullptr, nullptr, params,
+                          scene->counter_for(s), nullptr, s);
+}
+
+// Same as qrt_render_spp with traversal counters added into d_stats (device
+// uint64[5]: rays, inner nodes, quads tested, instances entered, FP64
+// re-tests).  Used to compute the algorithmic bytes of a render.
+int qrt_render_spp_stats(qrt_scene scene, const qrt_view* views, uint32_t n_views,
+                         const float* d_albedo, const qrt_params* params,
+                         unsigned long long* d_stats, qrt_stream stream) {
+    int rc = render_args_check(scene, views, n_views, d_albedo);
+    if (rc) return rc;
+    if (!d_stats || !aligned(d_stats, 8)) return fail(QRT_ERR_INVALID_ARG, "d_stats NULL or unaligned");
+    if (n_views == 0) return QRT_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return render_enqueue(scene, views, n_views, d_albedo, nullptr, nullptr, params,
+                          scene->counter_for(s), d_stats, s);
+}
+
+int qrt_trace_stats(qrt_scene scene, int any, const qrt_ray* d_rays, uint64_t n, void* d_out,
+                    const qrt_tuning* tuning, unsigned long long* d_stats, qrt_stream stream) {
+    if (!scene) return fail(QRT_ERR_INVALID_ARG, "scene is NULL");
+    if (n == 0) return QRT_OK;
+    if (!d_rays || !d_out || !d_stats) return fail(QRT_ERR_INVALID_ARG, "NULL device pointer");
+    if (!aligned(d_rays, 16) || !aligned(d_out, any ? 4 : 16) || !aligned(d_stats, 8))
+        return fail(QRT_ERR_ALIGN, "misaligned device pointer");
+    Tune t = resolve_tuning(tuning);
+    int rc = validate_tuning(t);
+    if (rc) return rc;
+    rc = check_device(scene);
+    if (rc) return rc;
+    cudaError_t e = launch_trace(any != 0, scene->S, d_rays, n, any ? nullptr : d_out,
+                                 any ? static_cast<uint32_t*>(d_out) : nullptr, 1u << 20, d_stats,
+                                 t, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "trace launch");
+    return QRT_OK;
+}
+
+int qrt_render_adjoint(qrt_scene scene, const qrt_view* views, uint32_t n_views,
+                       const float* d_albedo, const float* const* d_dimage, float* d_grad_albedo,
+                       const qrt_params* params, qrt_stream stream) {
+    int rc = render_args_check(scene, views, n_views, d_albedo);
+    if (rc) return rc;
+    if (n_views == 0) return QRT_OK;
+    if (!d_dimage) return fail(QRT_ERR_INVALID_ARG, "d_dimage is NULL");
+    if (!d_grad_albedo || !aligned(d_grad_albedo, 4))
+        return fail(QRT_ERR_INVALID_ARG, "d_grad_albedo is NULL or unaligned");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return render_enqueue(scene, views, n_views, d_albedo, d_dimage, d_grad_albedo, params,
+                          scene->counter_for(s), nullptr, s);
+}
+
+int qrt_l2_loss(const float* d_img, const float* d_target, uint64_t n, double* d_loss,
+                float* d_dimage, qrt_stream stream) {
+    if (!d_loss) return fail(QRT_ERR_INVALID_ARG, "d_loss is NULL");
+    if (n > 0 && (!d_img || !d_target)) return fail(QRT_ERR_INVALID_ARG, "NULL image pointer");
+    if (!aligned(d_loss, 8)) return fail(QRT_ERR_ALIGN, "d_loss must be 8-byte aligned");
+    cudaError_t e = launch_l2_loss(d_img, d_target, n, d_loss, d_dimage,
+                                   reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "loss launch");
+    return QRT_OK;
+}
+
+int qrt_render_graph_create(qrt_scene scene, const qrt_view* views, uint32_t n_views,
+                            const float* d_albedo, const qrt_params* params, qrt_graph* out) {
+    if (!out) return fail(QRT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int rc = render_args_check(scene, views, n_views, d_albedo);
+    if (rc) return rc;
+    if (n_views == 0) return fail(QRT_ERR_INVALID_ARG, "no views");
+    qrt_graph_s* g = new qrt_graph_s();
+    g->device = scene->device;
+    cudaError_t e = cudaMalloc((void**)&g->d_counter, kSlotStride);
+    if (e != cudaSuccess) {
+        delete g;
+        return cuda_fail(e, "graph counter");
+    }
+    cudaStream_t cs = nullptr;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        if (cs) cudaStreamDestroy(cs);
+        cudaFree(g->d_counter);
+        delete g;
+        return cuda_fail(e, "graph capture");
+    }
+    rc = render_enqueue(scene, views, n_views, d_albedo, nullptr, nullptr, params, g->d_counter,
+                        nullptr, cs);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    cudaStreamDestroy(cs);
+    if (rc == QRT_OK && e2 != cudaSuccess) rc = cuda_fail(e2, "graph capture");
+    if (rc == QRT_OK) {
+        g->graph = graph;
+        e = cudaGraphInstantiate(&g->exec, graph, 0);
+        if (e != cudaSuccess) rc = cuda_fail(e, "graph instantiate");
+    } else if (graph) {
+        cudaGraphDestroy(graph);
+    }
+    if (rc != QRT_OK) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        cudaFree(g->d_counter);
+        delete g;
+        return rc;
+    }
+    *out = g;
+    return QRT_OK;
+}
+
+int qrt_graph_launch(qrt_graph graph, qrt_stream stream) {
+    if (!graph) return fail(QRT_ERR_INVALID_ARG, "graph is NULL");
+    cudaError_t e = cudaGraphLaunch(graph->exec, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    return QRT_OK;
+}
+
+int qrt_graph_destroy(qrt_graph graph) {
+    if (!graph) return fail(QRT_ERR_INVALID_ARG, "graph is NULL");
+    if (graph->exec) cudaGraphExecDestroy(graph->exec);
+    if (graph->graph) cudaGraphDestroy(graph->graph);
+    cudaFree(graph->d_counter);
+    delete graph;
+    return QRT_OK;
+}
+
+int qrt_check(qrt_scene scene, qrt_stream stream) {
+    if (!scene) return fail(QRT_ERR_INVALID_ARG, "scene is NULL");
+    int rc = check_device(scene);
+    if (rc) return rc;
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    uint32_t w[2];
+    e = cudaMemcpy(w, scene->d_err, sizeof(w), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "error word read");
+    if (w[0] == 0) return QRT_OK;
+    const uint32_t init[2] = {0u, 0xFFFFFFFFu};
+    e = cudaMemcpy(scene->d_err, init, sizeof(init), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "error word reset");
+    if (w[0] & kErrStackOverflow)
+        return fail(QRT_ERR_STACK_OVERFLOW,
+                    "traversal stack overflow (first affected item " + std::to_string(w[1]) + ")");
+    return fail(QRT_ERR_STEP_LIMIT,
+                "traversal step limit exceeded (first affected item " + std::to_string(w[1]) + ")");
+}
+
+int qrt_blas_build_check(const qrt_mesh* mesh, const qrt_build_opts* opts, uint64_t* n_nodes,
+                         uint32_t* depth) {
+    if (!mesh || !mesh->verts || !mesh->quads)
+        return fail(QRT_ERR_INVALID_ARG, "mesh or its arrays are NULL");
+    BlasResult r;
+    std::string err;
+    if (!build_blas(mesh->verts, mesh->n_verts, mesh->quads, mesh->n_quads, resolve_build(opts), r, err))
+        return fail(QRT_ERR_INVALID_ARG, err);
+    std::vector<FBox> items(r.quads.size());
+    for (size_t s = 0; s < r.quads.size(); ++s) {
+        FBox b;
+        for (int a = 0; a < 3; ++a) {
+            b.lo[a] = std::min(std::min(r.quads[s].v[a], r.quads[s].v[3 + a]),
+                               std::min(r.quads[s].v[6 + a], r.quads[s].v[9 + a]));
+            b.hi[a] = std::max(std::max(r.quads[s].v[a], r.quads[s].v[3 + a]),
+                               std::max(r.quads[s].v[6 + a], r.quads[s].v[9 + a]));
+        }
+        items[s] = b;
+    }
+    // every original quad appears once in slot order
+    std::vector<uint8_t> seen(mesh->n_quads, 0);
+    for (uint32_t p : r.prim) {
+        if (p >= mesh->n_quads || seen[p]++) return fail(QRT_ERR_INVALID_ARG, "slot permutation broken");
+    }
+    uint32_t d = 0;
+    if (!check_wide(r.nodes, items, err, &d)) return fail(QRT_ERR_INVALID_ARG, err);
+    if (n_nodes) *n_nodes = r.nodes.size();
+    if (depth) *depth = d;
+    return QRT_OK;
+}
+
+}  // extern "C"

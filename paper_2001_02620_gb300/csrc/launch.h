@@ -1,0 +1,76 @@
+// Host-side launch interface between the C ABI (capi.cpp) and the CUDA
+// translation units (trace.cu, render.cu).  Plain C++ types only.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qrt_layout.h"
+
+namespace qrt {
+
+// Resolved launch configuration.
+struct Tune {
+    int block = 128;
+    int blocks_per_sm = 0;  // 0 = occupancy maximum
+    int batch = 1;          // 32-item groups a warp claims per fetch
+    int stack = 64;         // 32 or 64
+    int fetch = 16;         // 16 or 32
+    int adjoint_mode = 1;   // 1 = replay, 2 = register record
+};
+
+// A view with its camera basis precomputed on the host (FP64 -> FP32).
+struct ViewDev {
+    float eye[3];
+    float f[3], r[3], u[3];
+    float sx0, sxs, sy0, sys;  // sx = sx0 + px*sxs, sy = sy0 + py*sys
+    uint32_t w, h, spp, pad;
+    uint64_t pixel_base;
+    uint64_t item_begin;  // first work item (pixel) of this view in the launch
+    uint64_t path_begin;  // first path index of this view (for the path log)
+    float* out;           // float [h*w*3]
+    const float* dimage;  // adjoint input, float [h*w*3]
+};
+
+constexpr int kMaxViewsPerLaunch = 64;
+
+struct ParamsDev {
+    uint32_t max_depth;
+    uint32_t max_steps;
+    uint64_t seed;
+    float env[3];
+    float sun_l[3];  // unit vector toward the sun
+    float sun_E[3];
+    uint32_t sun_on;
+    uint32_t* path_log;
+};
+
+struct RenderArgs {
+    DevScene S;
+    const float* albedo;
+    float* grad;
+    ParamsDev P;
+    unsigned long long* counter;
+    unsigned long long* stats;  // optional: [rays, nodes, quads, instances, fp64 re-tests, vertices]
+    uint64_t n_items;
+    uint32_t n_views;
+    uint32_t batch;
+    ViewDev views[kMaxViewsPerLaunch];
+};
+
+cudaError_t launch_trace(bool any, const DevScene& S, const void* rays, uint64_t n, void* hits,
+                         uint32_t* occ_bits, uint32_t max_steps, unsigned long long* stats,
+                         const Tune& t, cudaStream_t s);
+
+constexpr int kStatsWords = 6;
+
+// Persistent render (grad == nullptr) or adjoint (grad != nullptr) launch;
+// A.counter must be zero when the kernel starts.
+cudaError_t launch_render(const RenderArgs& A, const Tune& t, int sm_count, cudaStream_t s);
+
+cudaError_t launch_l2_loss(const float* img, const float* target, uint64_t n, double* loss,
+                           float* dimage, cudaStream_t s);
+
+// Maximum resident blocks per SM for the render kernel variant.
+int render_occupancy(const Tune& t, bool adjoint);
+
+}  // namespace qrt

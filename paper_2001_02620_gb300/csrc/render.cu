@@ -1,0 +1,399 @@
+// Path tracer (qrt_render_spp), its adjoint by path replay
+// (qrt_render_adjoint) and the L2 image loss.
+//
+// One persistent kernel covers every (view, pixel) of a launch: each warp
+// claims 32*batch consecutive pixels at a time from a global counter, each
+// lane renders all spp samples of its pixel and writes the mean, so the
+// primal needs no atomics and a pixel's value does not depend on how views
+// are batched.  Random numbers: Philox4x32-10 keyed by the render seed with
+// counter (global pixel lo, global pixel hi, sample, bounce).
+//
+// Per path (Section 4.4, "Shading": a path tracer with progressive
+// one-sample-per-pixel refinement; Section 5: a maximum path depth):
+//   camera ray through (x + xi1, y + xi2);
+//   for i = 1..D: closest hit; on a miss add beta * env and stop; at a hit
+//   take the per-quad albedo a and the geometric normal faced against the
+//   ray, add the sun term beta * a/pi * E * (n.l) when the shadow ray toward
+//   the sun is unoccluded, set beta *= a, and continue along a cosine-
+//   distributed direction from an offset origin.
+#include <math_constants.h>
+
+#include "launch.h"
+#include "traverse.cuh"
+
+namespace qrt {
+
+// Philox4x32-10 (Salmon et al., SC 2011).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ float u01(uint32_t x) {
+    return __fmul_rn(__uint2float_rn(x >> 8), 5.9604644775390625e-08f);  // 2^-24
+}
+
+__device__ __forceinline__ uint4 draw(uint64_t seed, uint64_t pix, uint32_t sample, uint32_t bounce) {
+    return philox4x32_10(make_uint4((uint32_t)pix, (uint32_t)(pix >> 32), sample, bounce),
+                         (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+struct F3 {
+    float x, y, z;
+};
+__device__ __forceinline__ F3 f3(float x, float y, float z) { return F3{x, y, z}; }
+__device__ __forceinline__ float dot3(F3 a, F3 b) {
+    return __fmaf_rn(a.x, b.x, __fmaf_rn(a.y, b.y, __fmul_rn(a.z, b.z)));
+}
+__device__ __forceinline__ F3 normalize3(F3 a) {
+    const float inv = __frcp_rn(__fsqrt_rn(dot3(a, a)));
+    return f3(__fmul_rn(a.x, inv), __fmul_rn(a.y, inv), __fmul_rn(a.z, inv));
+}
+
+// Cosine-weighted direction about n: Malley's disk-to-hemisphere lift in the
+// orthonormal basis of Duff et al. (JCGT 2017).
+__device__ __forceinline__ F3 sample_cosine(F3 n, float xi1, float xi2) {
+    const float r = __fsqrt_rn(xi1);
+    float sp, cp;
+    sincospif(__fmul_rn(2.0f, xi2), &sp, &cp);
+    const float lx = __fmul_rn(r, cp), ly = __fmul_rn(r, sp);
+    const float lz = __fsqrt_rn(fmaxf(0.0f, __fsub_rn(1.0f, xi1)));
+    const float sign = copysignf(1.0f, n.z);
+    const float a = __fdiv_rn(-1.0f, __fadd_rn(sign, n.z));
+    const float b = __fmul_rn(__fmul_rn(n.x, n.y), a);
+    const F3 b1 = f3(__fadd_rn(1.0f, __fmul_rn(__fmul_rn(sign, __fmul_rn(n.x, n.x)), a)),
+                     __fmul_rn(sign, b), -__fmul_rn(sign, n.x));
+    const F3 b2 = f3(b, __fadd_rn(sign, __fmul_rn(__fmul_rn(n.y, n.y), a)), -n.y);
+    return f3(__fmaf_rn(lx, b1.x, __fmaf_rn(ly, b2.x, __fmul_rn(lz, n.x))),
+              __fmaf_rn(lx, b1.y, __fmaf_rn(ly, b2.y, __fmul_rn(lz, n.y))),
+              __fmaf_rn(lx, b1.z, __fmaf_rn(ly, b2.z, __fmul_rn(lz, n.z))));
+}
+
+// Add v (3 channels) into grad[3*row ..]; lanes of a warp that hit the same
+// row are summed first so only one of them issues the atomics.
+__device__ __forceinline__ void grad_add(float* grad, uint32_t row, float g0, float g1, float g2) {
+    const unsigned active = __activemask();
+    const unsigned peers = __match_any_sync(active, row);
+    const int lane = threadIdx.x & 31;
+    if (peers == (1u << lane)) {
+        atomicAdd(grad + 3 * (size_t)row, g0);
+        atomicAdd(grad + 3 * (size_t)row + 1, g1);
+        atomicAdd(grad + 3 * (size_t)row + 2, g2);
+        return;
+    }
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    unsigned m = peers;
+    while (m) {
+        const int j = __ffs(m) - 1;
+        m &= m - 1;
+        s0 += __shfl_sync(peers, g0, j);
+        s1 += __shfl_sync(peers, g1, j);
+        s2 += __shfl_sync(peers, g2, j);
+    }
+    if (lane == __ffs(peers) - 1) {
+        atomicAdd(grad + 3 * (size_t)row, s0);
+        atomicAdd(grad + 3 * (size_t)row + 1, s1);
+        atomicAdd(grad + 3 * (size_t)row + 2, s2);
+    }
+}
+
+// One path sample.  mode 0: returns its radiance in L.  mode 1 (replay):
+// recomputes the identical path and adds w * dL/da into A.grad, where the
+// radiance leaving vertex i is Ltot minus the sun terms gathered before i.
+// Every floating-point operation on the path is an explicitly rounded
+// intrinsic (nothing is left for the compiler to contract), so each inlined
+// copy -- primal, replay pass 1, replay pass 2 -- computes bit-identical paths.
+template <int STACK, int FETCH>
+__device__ __forceinline__ uint32_t path_sample(const RenderArgs& A, const ViewDev& V, uint32_t x,
+                                             uint32_t y, uint64_t gpix, uint32_t smp, int mode,
+                                             float* L, const float* Ltot, const float* w,
+                                             uint32_t* log, TraceStats* st) {
+    const ParamsDev& P = A.P;
+    const DevScene& S = A.S;
+    uint32_t err = 0;
+    TraceStats ls{0, 0, 0, 0, 0, 0};
+    uint4 xi = draw(P.seed, gpix, smp, 0);
+    const float px = __fadd_rn((float)x, u01(xi.x));
+    const float py = __fadd_rn((float)y, u01(xi.y));
+    const float sx = __fmaf_rn(px, V.sxs, V.sx0);
+    const float sy = __fmaf_rn(py, V.sys, V.sy0);
+    F3 d = normalize3(f3(__fmaf_rn(sx, V.r[0], __fmaf_rn(sy, V.u[0], V.f[0])),
+                         __fmaf_rn(sx, V.r[1], __fmaf_rn(sy, V.u[1], V.f[1])),
+                         __fmaf_rn(sx, V.r[2], __fmaf_rn(sy, V.u[2], V.f[2]))));
+    F3 o = f3(V.eye[0], V.eye[1], V.eye[2]);
+    float b0 = 1.f, b1 = 1.f, b2 = 1.f;     // throughput
+    float l0 = 0.f, l1 = 0.f, l2 = 0.f;     // radiance
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;     // sun terms so far (replay)
+    uint32_t shadow_bits = 0;
+    const uint32_t D = P.max_depth;
+    uint32_t i = 1;
+    for (; i <= D; ++i) {
+        Hit h;
+        err |= trace_ray<false, STACK, FETCH>(S, o.x, o.y, o.z, d.x, d.y, d.z, 0.0f, kInfF,
+                                               P.max_steps, h, ls);
+        if (log) {
+            log[2 * (i - 1)] = h.inst;
+            log[2 * (i - 1) + 1] = h.prim;
+        }
+        if (h.inst == 0xFFFFFFFFu) {
+            l0 = __fmaf_rn(b0, P.env[0], l0);
+            l1 = __fmaf_rn(b1, P.env[1], l1);
+            l2 = __fmaf_rn(b2, P.env[2], l2);
+            ++i;
+            break;
+        }
+        ++ls.verts;
+        // instance record: world->object rows and the quad base (= albedo base)
+        const InstDev* ip = S.inst + h.inst;
+        const float4* q4 = reinterpret_cast<const float4*>(ip);
+        const float4 m0 = __ldg(q4), m1 = __ldg(q4 + 1), m2 = __ldg(q4 + 2);
+        const uint32_t row = __ldg(reinterpret_cast<const uint32_t*>(ip) + 13) + h.prim;
+        const float a0 = __ldg(A.albedo + 3 * (size_t)row);
+        const float a1 = __ldg(A.albedo + 3 * (size_t)row + 1);
+        const float a2 = __ldg(A.albedo + 3 * (size_t)row + 2);
+        // geometric normal: cross of the diagonals, to world by the inverse transpose
+        const float4* qv = reinterpret_cast<const float4*>(S.quads + h.slot);
+        const float4 qa = __ldg(qv), qb = __ldg(qv + 1), qc = __ldg(qv + 2);
+        const F3 e1 = f3(__fsub_rn(qb.z, qa.x), __fsub_rn(qb.w, qa.y), __fsub_rn(qc.x, qa.z));  // v2 - v0
+        const F3 e2 = f3(__fsub_rn(qc.y, qa.w), __fsub_rn(qc.z, qb.x), __fsub_rn(qc.w, qb.y));  // v3 - v1
+        const F3 no = f3(__fsub_rn(__fmul_rn(e1.y, e2.z), __fmul_rn(e1.z, e2.y)),
+                         __fsub_rn(__fmul_rn(e1.z, e2.x), __fmul_rn(e1.x, e2.z)),
+                         __fsub_rn(__fmul_rn(e1.x, e2.y), __fmul_rn(e1.y, e2.x)));
+        F3 n = normalize3(f3(__fmaf_rn(m0.x, no.x, __fmaf_rn(m1.x, no.y, __fmul_rn(m2.x, no.z))),
+                             __fmaf_rn(m0.y, no.x, __fmaf_rn(m1.y, no.y, __fmul_rn(m2.y, no.z))),
+                             __fmaf_rn(m0.z, no.x, __fmaf_rn(m1.z, no.y, __fmul_rn(m2.z, no.z)))));
+        if (dot3(n, d) > 0.f) n = f3(-n.x, -n.y, -n.z);
+        const F3 hp = f3(__fmaf_rn(h.t, d.x, o.x), __fmaf_rn(h.t, d.y, o.y), __fmaf_rn(h.t, d.z, o.z));
+        const float off = __fmaf_rn(1e-5f, maxabs3(hp.x, hp.y, hp.z), 1e-4f);
+        const F3 sp = f3(__fmaf_rn(off, n.x, hp.x), __fmaf_rn(off, n.y, hp.y), __fmaf_rn(off, n.z, hp.z));
+        float n0 = 0.f, n1 = 0.f, n2 = 0.f;  // this vertex's sun term
+        if (P.sun_on) {
+            const float cl = dot3(n, f3(P.sun_l[0], P.sun_l[1], P.sun_l[2]));
+            if (cl > 0.f) {
+                if (i <= 16) shadow_bits |= 1u << (2 * (i - 1));
+                Hit hs;
+                err |= trace_ray<true, STACK, FETCH>(S, sp.x, sp.y, sp.z, P.sun_l[0], P.sun_l[1],
+                                                      P.sun_l[2], 0.0f, kInfF, P.max_steps, hs, ls);
+                if (hs.inst != 0xFFFFFFFFu) {
+                    if (i <= 16) shadow_bits |= 2u << (2 * (i - 1));
+                } else {
+                    const float k = __fmul_rn(cl, 0.318309886183790671538f);  // cos / pi
+                    n0 = __fmul_rn(__fmul_rn(b0, a0), __fmul_rn(P.sun_E[0], k));
+                    n1 = __fmul_rn(__fmul_rn(b1, a1), __fmul_rn(P.sun_E[1], k));
+                    n2 = __fmul_rn(__fmul_rn(b2, a2), __fmul_rn(P.sun_E[2], k));
+                }
+            }
+        }
+        if (mode == 1) {
+            // d L / d a_i = (radiance leaving vertex i) / a_i
+            const float g0 = a0 != 0.f ? __fdiv_rn(__fmul_rn(w[0], __fsub_rn(Ltot[0], s0)), a0) : 0.f;
+            const float g1 = a1 != 0.f ? __fdiv_rn(__fmul_rn(w[1], __fsub_rn(Ltot[1], s1)), a1) : 0.f;
+            const float g2 = a2 != 0.f ? __fdiv_rn(__fmul_rn(w[2], __fsub_rn(Ltot[2], s2)), a2) : 0.f;
+            grad_add(A.grad, row, g0, g1, g2);
+            s0 = __fadd_rn(s0, n0);
+            s1 = __fadd_rn(s1, n1);
+            s2 = __fadd_rn(s2, n2);
+        }
+        l0 = __fadd_rn(l0, n0);
+        l1 = __fadd_rn(l1, n1);
+        l2 = __fadd_rn(l2, n2);
+        b0 = __fmul_rn(b0, a0);
+        b1 = __fmul_rn(b1, a1);
+        b2 = __fmul_rn(b2, a2);
+        if (i == D) {
+            ++i;
+            break;
+        }
+        xi = draw(P.seed, gpix, smp, i);
+        d = sample_cosine(n, u01(xi.x), u01(xi.y));
+        o = sp;
+    }
+    if (log) {
+        for (uint32_t k = i - 1; k < D; ++k) {
+            log[2 * k] = 0xFFFFFFFFu;
+            log[2 * k + 1] = 0xFFFFFFFFu;
+        }
+        log[2 * D] = shadow_bits;
+    }
+    L[0] = l0;
+    L[1] = l1;
+    L[2] = l2;
+    st->rays += ls.rays;
+    st->nodes += ls.nodes;
+    st->quads += ls.quads;
+    st->insts += ls.insts;
+    st->fallbacks += ls.fallbacks;
+    st->verts += ls.verts;
+    return err;
+}
+
+__device__ __forceinline__ int find_view(const RenderArgs& A, uint64_t item) {
+    int lo = 0, hi = (int)A.n_views - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (A.views[mid].item_begin <= item)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int STACK, int FETCH, bool ADJ>
+__global__ void __launch_bounds__(256) render_kernel(const __grid_constant__ RenderArgs A) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t D = A.P.max_depth;
+    uint32_t err = 0;
+    uint64_t bad = ~0ull;
+    TraceStats st{0, 0, 0, 0, 0, 0};
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(A.counter, 32ull * A.batch);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (base >= A.n_items) break;
+        for (uint32_t k = 0; k < A.batch; ++k) {
+            const uint64_t item = base + 32ull * k + lane;
+            if (item >= A.n_items) break;
+            const ViewDev& V = A.views[find_view(A, item)];
+            const uint64_t pix = item - V.item_begin;
+            const uint32_t x = (uint32_t)(pix % V.w), y = (uint32_t)(pix / V.w);
+            const uint64_t gpix = V.pixel_base + pix;
+            const float inv_spp = __frcp_rn((float)V.spp);
+            if (!ADJ) {
+                float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
+                for (uint32_t s = 0; s < V.spp; ++s) {
+                    float L[3];
+                    uint32_t* log = A.P.path_log
+                                        ? A.P.path_log + (V.path_begin + pix * V.spp + s) * (2ull * D + 1)
+                                        : nullptr;
+                    const uint32_t e = path_sample<STACK, FETCH>(A, V, x, y, gpix, s, 0, L, nullptr,
+                                                                 nullptr, log, &st);
+                    if (e) {
+                        err |= e;
+                        bad = min(bad, item);
+                    }
+                    acc0 = __fadd_rn(acc0, L[0]);
+                    acc1 = __fadd_rn(acc1, L[1]);
+                    acc2 = __fadd_rn(acc2, L[2]);
+                }
+                float* out = V.out + 3 * pix;
+                out[0] = __fdiv_rn(acc0, (float)V.spp);
+                out[1] = __fdiv_rn(acc1, (float)V.spp);
+                out[2] = __fdiv_rn(acc2, (float)V.spp);
+            } else {
+                const float* di = V.dimage + 3 * pix;
+                const float w[3] = {__fmul_rn(__ldg(di), inv_spp), __fmul_rn(__ldg(di + 1), inv_spp),
+                                    __fmul_rn(__ldg(di + 2), inv_spp)};
+                if (w[0] == 0.f && w[1] == 0.f && w[2] == 0.f) continue;
+                for (uint32_t s = 0; s < V.spp; ++s) {
+                    float L[3], L2[3];
+                    uint32_t e = path_sample<STACK, FETCH>(A, V, x, y, gpix, s, 0, L, nullptr,
+                                                           nullptr, nullptr, &st);
+                    e |= path_sample<STACK, FETCH>(A, V, x, y, gpix, s, 1, L2, L, w, nullptr, &st);
+                    if (e) {
+                        err |= e;
+                        bad = min(bad, item);
+                    }
+                }
+            }
+        }
+    }
+    if (err) {
+        atomicOr(A.S.err, err);
+        atomicMin(A.S.err + 1, (uint32_t)min(bad, (uint64_t)0xFFFFFFFEu));
+    }
+    if (A.stats) add_stats(A.stats, st);
+}
+
+template <int STACK, int FETCH, bool ADJ>
+static int occupancy_of(int block) {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_kernel<STACK, FETCH, ADJ>, block, 0);
+    return n;
+}
+
+int render_occupancy(const Tune& t, bool adjoint) {
+    const bool s32 = t.stack <= 32, f32 = t.fetch == 32;
+    if (adjoint) {
+        if (s32) return f32 ? occupancy_of<32, 32, true>(t.block) : occupancy_of<32, 16, true>(t.block);
+        return f32 ? occupancy_of<64, 32, true>(t.block) : occupancy_of<64, 16, true>(t.block);
+    }
+    if (s32) return f32 ? occupancy_of<32, 32, false>(t.block) : occupancy_of<32, 16, false>(t.block);
+    return f32 ? occupancy_of<64, 32, false>(t.block) : occupancy_of<64, 16, false>(t.block);
+}
+
+cudaError_t launch_render(const RenderArgs& A, const Tune& t, int sm_count, cudaStream_t s) {
+    if (A.n_items == 0) return cudaSuccess;
+    const bool adj = A.grad != nullptr;
+    int per_sm = t.blocks_per_sm > 0 ? t.blocks_per_sm : render_occupancy(t, adj);
+    if (per_sm < 1) per_sm = 1;
+    uint64_t want = (A.n_items + (uint64_t)t.block - 1) / (uint64_t)t.block;
+    uint64_t grid = (uint64_t)sm_count * (uint64_t)per_sm;
+    if (want < grid) grid = want;
+    if (grid < 1) grid = 1;
+    const dim3 g((unsigned)grid), b((unsigned)t.block);
+    const bool s32 = t.stack <= 32, f32 = t.fetch == 32;
+    if (adj) {
+        if (s32) {
+            if (f32) render_kernel<32, 32, true><<<g, b, 0, s>>>(A);
+            else render_kernel<32, 16, true><<<g, b, 0, s>>>(A);
+        } else {
+            if (f32) render_kernel<64, 32, true><<<g, b, 0, s>>>(A);
+            else render_kernel<64, 16, true><<<g, b, 0, s>>>(A);
+        }
+    } else {
+        if (s32) {
+            if (f32) render_kernel<32, 32, false><<<g, b, 0, s>>>(A);
+            else render_kernel<32, 16, false><<<g, b, 0, s>>>(A);
+        } else {
+            if (f32) render_kernel<64, 32, false><<<g, b, 0, s>>>(A);
+            else render_kernel<64, 16, false><<<g, b, 0, s>>>(A);
+        }
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// L2 loss: loss = sum (img - target)^2 / n (FP64 reduction), dimage = 2 (img - target) / n
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) l2_loss_kernel(const float* __restrict__ img,
+                                                      const float* __restrict__ tgt, uint64_t n,
+                                                      double* loss, float* __restrict__ dimg) {
+    __shared__ double part[8];
+    double acc = 0.0;
+    const double inv_n = 1.0 / (double)n;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const float r = __fsub_rn(img[i], tgt[i]);
+        acc += (double)r * (double)r;
+        if (dimg) dimg[i] = (float)(2.0 * (double)r * inv_n);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += part[k];
+        atomicAdd(loss, s * inv_n);
+    }
+}
+
+cudaError_t launch_l2_loss(const float* img, const float* target, uint64_t n, double* loss,
+                           float* dimage, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    if (n == 0) return cudaSuccess;
+    uint64_t grid = (n + 255) / 256;
+    if (grid > 4096) grid = 4096;
+    l2_loss_kernel<<<(unsigned)grid, 256, 0, s>>>(img, target, n, loss, dimage);
+    return cudaGetLastError();
+}
+
+}  // namespace qrt

@@ -1,0 +1,511 @@
+// Device-side traversal of the two-level quad BVH (qrt_layout.h).
+//
+// Top level: four-wide TLAS over instance world boxes.  At a TLAS leaf the ray
+// is moved into the instance's object space with the FP32 world->object
+// matrix (the direction is not renormalised, so t is shared by both levels)
+// and the object's BLAS is traversed on the same stack; when the stack drains
+// back to the level where the instance was entered, the world ray is
+// restored.  Leaves of a BLAS hold up to 16 quads stored contiguously.
+//
+// Precision design.  Box tests are made conservative by widening every
+// dequantised box by delta, an absolute bound on the position error of the
+// FP32 ray in the current space (ray transform + slab arithmetic), so a node
+// is never culled that the exact ray enters.  The quad test is the watertight
+// test of Woop, Benthin and Wald (JCGT 2013) applied to both triangles of the
+// quad with the diagonal v0-v2 shared; an edge function whose magnitude is
+// within the same error bound of zero makes the decision uncertain, and only
+// then the quad is re-tested in FP64 from the world ray and the FP64 inverse
+// transform.  Hit/miss decisions therefore agree with exact arithmetic on the
+// given FP32 ray except when a hit lies within FP64 rounding of an edge.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qrt_layout.h"
+
+namespace qrt {
+
+constexpr float kInfF = __builtin_huge_valf();
+
+struct Hit {
+    float t;
+    uint32_t inst, prim;
+    float u, v;
+    uint32_t slot;  // global quad slot of the hit (for shading)
+};
+
+// Ray in the current space, with everything the node and quad tests reuse.
+struct RaySetup {
+    float ox, oy, oz;     // origin
+    float ix, iy, iz;     // reciprocal direction, |d| clamped away from 0
+    float oix, oiy, oiz;  // o * inv
+    float px, py, pz;     // box widening in t units (delta * |inv|)
+    uint32_t neg;         // bit a: direction negative along axis a
+    // watertight shear in affine form: X = V . rx - cx, Y = V . ry - cy, Z = V . rz - cz
+    float rx0, rx1, rx2, cx;
+    float ry0, ry1, ry2, cy;
+    float rz0, rz1, rz2, cz;
+    float delta;
+};
+
+__device__ __forceinline__ float clamp_dir(float d) {
+    return fabsf(d) > 1e-30f ? d : copysignf(1e-30f, d);
+}
+
+__device__ __forceinline__ void setup_boxes(RaySetup& r, float ox, float oy, float oz, float dx,
+                                            float dy, float dz, float delta) {
+    r.ox = ox;
+    r.oy = oy;
+    r.oz = oz;
+    r.ix = __frcp_rn(clamp_dir(dx));
+    r.iy = __frcp_rn(clamp_dir(dy));
+    r.iz = __frcp_rn(clamp_dir(dz));
+    r.oix = __fmul_rn(ox, r.ix);
+    r.oiy = __fmul_rn(oy, r.iy);
+    r.oiz = __fmul_rn(oz, r.iz);
+    r.px = __fmul_rn(delta, fabsf(r.ix));
+    r.py = __fmul_rn(delta, fabsf(r.iy));
+    r.pz = __fmul_rn(delta, fabsf(r.iz));
+    r.neg = (r.ix < 0.f ? 1u : 0u) | (r.iy < 0.f ? 2u : 0u) | (r.iz < 0.f ? 4u : 0u);
+    r.delta = delta;
+}
+
+__device__ __forceinline__ void setup_shear(RaySetup& r, float dx, float dy, float dz) {
+    const float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
+    // kz = dominant axis, (kx, ky) the next two in cyclic order; selects
+    // instead of indexed arrays keep everything in registers
+    const int kz = (ax > ay) ? ((ax > az) ? 0 : 2) : ((ay > az) ? 1 : 2);
+    const float dkx = kz == 0 ? dy : (kz == 1 ? dz : dx);
+    const float dky = kz == 0 ? dz : (kz == 1 ? dx : dy);
+    const float dkz = kz == 0 ? dx : (kz == 1 ? dy : dz);
+    const float okx = kz == 0 ? r.oy : (kz == 1 ? r.oz : r.ox);
+    const float oky = kz == 0 ? r.oz : (kz == 1 ? r.ox : r.oy);
+    const float okz = kz == 0 ? r.ox : (kz == 1 ? r.oy : r.oz);
+    const float Sx = __fdiv_rn(dkx, dkz), Sy = __fdiv_rn(dky, dkz), Sz = __frcp_rn(dkz);
+    // row X: +1 at kx, -Sx at kz; row Y: +1 at ky, -Sy at kz; row Z: Sz at kz
+    r.rx0 = kz == 0 ? -Sx : (kz == 2 ? 1.f : 0.f);
+    r.rx1 = kz == 1 ? -Sx : (kz == 0 ? 1.f : 0.f);
+    r.rx2 = kz == 2 ? -Sx : (kz == 1 ? 1.f : 0.f);
+    r.ry0 = kz == 0 ? -Sy : (kz == 1 ? 1.f : 0.f);
+    r.ry1 = kz == 1 ? -Sy : (kz == 2 ? 1.f : 0.f);
+    r.ry2 = kz == 2 ? -Sy : (kz == 0 ? 1.f : 0.f);
+    r.rz0 = kz == 0 ? Sz : 0.f;
+    r.rz1 = kz == 1 ? Sz : 0.f;
+    r.rz2 = kz == 2 ? Sz : 0.f;
+    r.cx = __fmaf_rn(-Sx, okz, okx);
+    r.cy = __fmaf_rn(-Sy, okz, oky);
+    r.cz = __fmul_rn(Sz, okz);
+}
+
+__device__ __forceinline__ float maxabs3(float a, float b, float c) {
+    return fmaxf(fabsf(a), fmaxf(fabsf(b), fabsf(c)));
+}
+
+// --------------------------------------------------------------------------
+// Node fetch: 64 bytes as four 128-bit or two 256-bit read-only loads.
+// --------------------------------------------------------------------------
+template <int FETCH>
+__device__ __forceinline__ void load_node(const QNode* n, uint4& a, uint4& b, uint4& c, uint4& d) {
+    if constexpr (FETCH == 32) {
+        asm volatile("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y),
+                       "=r"(b.z), "=r"(b.w)
+                     : "l"(n));
+        asm volatile("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(c.x), "=r"(c.y), "=r"(c.z), "=r"(c.w), "=r"(d.x), "=r"(d.y),
+                       "=r"(d.z), "=r"(d.w)
+                     : "l"(reinterpret_cast<const char*>(n) + 32));
+    } else {
+        const uint4* p = reinterpret_cast<const uint4*>(n);
+        a = __ldg(p);
+        b = __ldg(p + 1);
+        c = __ldg(p + 2);
+        d = __ldg(p + 3);
+    }
+}
+
+__device__ __forceinline__ float byte_f(uint32_t w, int i) {
+    return __uint2float_rn((w >> (8 * i)) & 0xFFu);
+}
+
+__device__ __forceinline__ float exp2i(int e) { return __int_as_float((e + 127) << 23); }
+
+// Tests the four children of a node; writes entry distances (inf = culled)
+// and references, sorted nearest first.  Returns the number of hits.
+template <int FETCH>
+__device__ __forceinline__ int node_children(const QNode* node, const RaySetup& r, float tmin,
+                                             float tmax, float t[4], uint32_t ref[4]) {
+    uint4 A, B, C, D;
+    load_node<FETCH>(node, A, B, C, D);
+    const float nox = __uint_as_float(A.x), noy = __uint_as_float(A.y), noz = __uint_as_float(A.z);
+    const int ex = (int)(int8_t)(A.w & 0xFF), ey = (int)(int8_t)((A.w >> 8) & 0xFF),
+              ez = (int)(int8_t)((A.w >> 16) & 0xFF);
+    const float ax = __fmul_rn(exp2i(ex), r.ix), ay = __fmul_rn(exp2i(ey), r.iy),
+                az = __fmul_rn(exp2i(ez), r.iz);
+    const float bx = __fmaf_rn(nox, r.ix, -r.oix), by = __fmaf_rn(noy, r.iy, -r.oiy),
+                bz = __fmaf_rn(noz, r.iz, -r.oiz);
+    const float bnx = bx - r.px, bfx = bx + r.px;
+    const float bny = by - r.py, bfy = by + r.py;
+    const float bnz = bz - r.pz, bfz = bz + r.pz;
+    // words: lo x,y,z = B.x, B.y, B.z ; hi x,y,z = B.w, C.x, C.y
+    const uint32_t nwx = (r.neg & 1u) ? B.w : B.x, fwx = (r.neg & 1u) ? B.x : B.w;
+    const uint32_t nwy = (r.neg & 2u) ? C.x : B.y, fwy = (r.neg & 2u) ? B.y : C.x;
+    const uint32_t nwz = (r.neg & 4u) ? C.y : B.z, fwz = (r.neg & 4u) ? B.z : C.y;
+    const uint32_t meta = D.z;
+    const uint32_t child[4] = {C.z, C.w, D.x, D.y};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float tnx = __fmaf_rn(byte_f(nwx, i), ax, bnx);
+        const float tfx = __fmaf_rn(byte_f(fwx, i), ax, bfx);
+        const float tny = __fmaf_rn(byte_f(nwy, i), ay, bny);
+        const float tfy = __fmaf_rn(byte_f(fwy, i), ay, bfy);
+        const float tnz = __fmaf_rn(byte_f(nwz, i), az, bnz);
+        const float tfz = __fmaf_rn(byte_f(fwz, i), az, bfz);
+        const float tn = fmaxf(fmaxf(tnx, tny), fmaxf(tnz, tmin));
+        const float tf = fminf(fminf(tfx, tfy), fminf(tfz, tmax));
+        const uint32_t m = (meta >> (8 * i)) & 0xFFu;
+        const bool hit = (m != 0u) && (tn <= tf);
+        t[i] = hit ? tn : kInfF;
+        ref[i] = (m == kMetaInner) ? child[i] : (kRefLeaf | ((m - 1u) << 27) | child[i]);
+    }
+    // sorting network on (t, ref); strict comparisons keep equal keys in order
+#define QRT_CSWAP(i, j)                             \
+    if (t[j] < t[i]) {                              \
+        float tt = t[i];                            \
+        t[i] = t[j];                                \
+        t[j] = tt;                                  \
+        uint32_t rr = ref[i];                       \
+        ref[i] = ref[j];                            \
+        ref[j] = rr;                                \
+    }
+    QRT_CSWAP(0, 1)
+    QRT_CSWAP(2, 3)
+    QRT_CSWAP(0, 2)
+    QRT_CSWAP(1, 3)
+    QRT_CSWAP(1, 2)
+#undef QRT_CSWAP
+    return (t[0] < kInfF) + (t[1] < kInfF) + (t[2] < kInfF) + (t[3] < kInfF);
+}
+
+// --------------------------------------------------------------------------
+// Quad test
+// --------------------------------------------------------------------------
+struct SV {
+    float X, Y, Z;
+};
+
+__device__ __forceinline__ SV shear(const RaySetup& r, float x, float y, float z) {
+    SV s;
+    s.X = __fmaf_rn(x, r.rx0, __fmaf_rn(y, r.rx1, __fmaf_rn(z, r.rx2, -r.cx)));
+    s.Y = __fmaf_rn(x, r.ry0, __fmaf_rn(y, r.ry1, __fmaf_rn(z, r.ry2, -r.cy)));
+    s.Z = __fmaf_rn(x, r.rz0, __fmaf_rn(y, r.rz1, __fmaf_rn(z, r.rz2, -r.cz)));
+    return s;
+}
+
+// 2D edge function; exactly antisymmetric: edge(P,Q) == -edge(Q,P).
+__device__ __forceinline__ float edge(const SV& P, const SV& Q) {
+    return __fsub_rn(__fmul_rn(P.X, Q.Y), __fmul_rn(P.Y, Q.X));
+}
+
+// 0 = certain miss, 1 = certain hit, 2 = uncertain.
+__device__ __forceinline__ int classify(float e0, float e1, float e2, float B) {
+    const bool p0 = e0 > B, p1 = e1 > B, p2 = e2 > B;
+    const bool n0 = e0 < -B, n1 = e1 < -B, n2 = e2 < -B;
+    if ((p0 || p1 || p2) && (n0 || n1 || n2)) return 0;
+    if ((p0 && p1 && p2) || (n0 && n1 && n2)) return 1;
+    return 2;
+}
+
+// Exact-enough re-test in FP64: object ray from the world ray and the FP64
+// world->object matrix, then the watertight test with FP64 arithmetic.
+// Returns 1 on a hit with t > tmin (t written, with quad-space u, v).
+static __device__ __noinline__ int quad_test64(const double* w2o, float wox, float woy, float woz,
+                                        float wdx, float wdy, float wdz, const float* v,
+                                        float tmin, double* t_out, float* u_out, float* v_out) {
+    double o[3], d[3];
+    const double wo[3] = {wox, woy, woz}, wd[3] = {wdx, wdy, wdz};
+    for (int r = 0; r < 3; ++r) {
+        o[r] = w2o[4 * r] * wo[0] + w2o[4 * r + 1] * wo[1] + w2o[4 * r + 2] * wo[2] + w2o[4 * r + 3];
+        d[r] = w2o[4 * r] * wd[0] + w2o[4 * r + 1] * wd[1] + w2o[4 * r + 2] * wd[2];
+    }
+    int kz = (fabs(d[0]) > fabs(d[1])) ? ((fabs(d[0]) > fabs(d[2])) ? 0 : 2)
+                                       : ((fabs(d[1]) > fabs(d[2])) ? 1 : 2);
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    const double Sx = d[kx] / d[kz], Sy = d[ky] / d[kz], Sz = 1.0 / d[kz];
+    double X[4], Y[4], Z[4];
+    for (int k = 0; k < 4; ++k) {
+        double P[3] = {(double)v[3 * k] - o[0], (double)v[3 * k + 1] - o[1],
+                       (double)v[3 * k + 2] - o[2]};
+        X[k] = P[kx] - Sx * P[kz];
+        Y[k] = P[ky] - Sy * P[kz];
+        Z[k] = Sz * P[kz];
+    }
+    auto E = [&](int p, int q) { return X[p] * Y[q] - Y[p] * X[q]; };
+    const double e21 = E(2, 1), e02 = E(0, 2), e10 = E(1, 0), e32 = E(3, 2), e03 = E(0, 3);
+    int hit = 0;
+    double best = INFINITY;
+    float bu = 0.f, bv = 0.f;
+    // triangle 0: (v0, v1, v2) with weights (e21, e02, e10)
+    {
+        const double U = e21, V = e02, W = e10;
+        if (((U >= 0 && V >= 0 && W >= 0) || (U <= 0 && V <= 0 && W <= 0))) {
+            const double det = U + V + W;
+            if (det != 0.0) {
+                const double tt = (U * Z[0] + V * Z[1] + W * Z[2]) / det;
+                if (tt > (double)tmin && tt < best) {
+                    best = tt;
+                    hit = 1;
+                    bu = (float)((V + W) / det);
+                    bv = (float)(W / det);
+                }
+            }
+        }
+    }
+    // triangle 1: (v0, v2, v3) with weights (e32, e03, -e02)
+    {
+        const double U = e32, V = e03, W = -e02;
+        if (((U >= 0 && V >= 0 && W >= 0) || (U <= 0 && V <= 0 && W <= 0))) {
+            const double det = U + V + W;
+            if (det != 0.0) {
+                const double tt = (U * Z[0] + V * Z[2] + W * Z[3]) / det;
+                if (tt > (double)tmin && tt < best) {
+                    best = tt;
+                    hit = 1;
+                    bu = (float)(V / det);
+                    bv = (float)((V + W) / det);
+                }
+            }
+        }
+    }
+    *t_out = best;
+    *u_out = bu;
+    *v_out = bv;
+    return hit;
+}
+
+// FP32 test of one quad; returns 1 on a hit with tmin < t (t, u, v written);
+// may defer to quad_test64.
+__device__ __forceinline__ int quad_test(const RaySetup& r, const QuadDev* q, const double* w2o64,
+                                         float wox, float woy, float woz, float wdx, float wdy,
+                                         float wdz, float tmin, float* t_out, float* u_out,
+                                         float* v_out, uint32_t* n_fallback) {
+    const float4* p = reinterpret_cast<const float4*>(q);
+    const float4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+    const SV s0 = shear(r, a.x, a.y, a.z);
+    const SV s1 = shear(r, a.w, b.x, b.y);
+    const SV s2 = shear(r, b.z, b.w, c.x);
+    const SV s3 = shear(r, c.y, c.z, c.w);
+    const float e21 = edge(s2, s1), e02 = edge(s0, s2), e10 = edge(s1, s0);
+    const float e32 = edge(s3, s2), e03 = edge(s0, s3);
+    // one error band for the whole quad: covers delta-perturbed vertices and
+    // the rounding of the edge products
+    const float M = fmaxf(fmaxf(fmaxf(fabsf(s0.X), fabsf(s0.Y)), fmaxf(fabsf(s1.X), fabsf(s1.Y))),
+                          fmaxf(fmaxf(fabsf(s2.X), fabsf(s2.Y)), fmaxf(fabsf(s3.X), fabsf(s3.Y))));
+    const float B = __fmaf_rn(4.0f * r.delta, M, 4.76837158e-07f * M * M);  // 2^-21 M^2
+    const int c0 = classify(e21, e02, e10, B);
+    const int c1 = classify(e32, e03, -e02, B);
+    if (c0 == 0 && c1 == 0) return 0;
+    if (c0 == 2 || c1 == 2) {
+        ++*n_fallback;
+        double t64;
+        float vv[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+        if (!quad_test64(w2o64, wox, woy, woz, wdx, wdy, wdz, vv, tmin, &t64, u_out, v_out))
+            return 0;
+        *t_out = (float)t64;
+        return 1;
+    }
+    float best = kInfF;
+    int hit = 0;
+    if (c0 == 1) {
+        const float det = e21 + e02 + e10;
+        const float T = __fmaf_rn(e21, s0.Z, __fmaf_rn(e02, s1.Z, __fmul_rn(e10, s2.Z)));
+        const float tt = __fdiv_rn(T, det);
+        if (tt > tmin) {
+            best = tt;
+            hit = 1;
+            *u_out = __fdiv_rn(e02 + e10, det);
+            *v_out = __fdiv_rn(e10, det);
+        }
+    }
+    if (c1 == 1) {
+        const float det = e32 + e03 - e02;
+        const float T = __fmaf_rn(e32, s0.Z, __fmaf_rn(e03, s2.Z, __fmul_rn(-e02, s3.Z)));
+        const float tt = __fdiv_rn(T, det);
+        if (tt > tmin && tt < best) {
+            best = tt;
+            hit = 1;
+            *u_out = __fdiv_rn(e03, det);
+            *v_out = __fdiv_rn(e03 - e02, det);
+        }
+    }
+    *t_out = best;
+    return hit;
+}
+
+// --------------------------------------------------------------------------
+// Two-level traversal
+// --------------------------------------------------------------------------
+struct TraceStats {
+    uint32_t nodes;      // inner nodes visited
+    uint32_t quads;      // quads tested
+    uint32_t insts;      // instances entered
+    uint32_t fallbacks;  // FP64 re-tests
+    uint32_t rays;       // rays traced
+    uint32_t verts;      // path vertices shaded (closest hits of the path tracer)
+};
+
+// Adds a thread's counters into stats[0..5] (rays, nodes, quads, instances,
+// FP64 re-tests, shaded vertices), one atomic per warp and counter.  Call
+// from converged code.
+__device__ __forceinline__ void add_stats(unsigned long long* stats, const TraceStats& st) {
+    uint32_t v[6] = {st.rays, st.nodes, st.quads, st.insts, st.fallbacks, st.verts};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        uint32_t x = v[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
+        if ((threadIdx.x & 31) == 0 && x) atomicAdd(stats + k, (unsigned long long)x);
+    }
+}
+
+// Closest hit (ANY = false) or any hit (ANY = true) of the world ray.
+// Returns device error bits (0 = fine).  For closest hit, h holds the best
+// hit found (inst = 0xFFFFFFFF if none).
+template <bool ANY, int STACK, int FETCH>
+__device__ __forceinline__ uint32_t trace_ray(const DevScene& S, float wox, float woy, float woz,
+                                              float wdx, float wdy, float wdz, float tmin,
+                                              float tmax, uint32_t max_steps, Hit& h,
+                                              TraceStats& st) {
+    h.t = tmax;
+    h.inst = 0xFFFFFFFFu;
+    h.prim = 0xFFFFFFFFu;
+    h.u = h.v = 0.f;
+    h.slot = 0;
+    ++st.rays;
+    if (S.n_inst == 0) return 0;
+    uint64_t stack[STACK];
+    int sp = 0;
+    int inst_sp = -1;
+    bool top = true;
+    uint32_t node_base = S.tlas_base;
+    uint32_t quad_base = 0;
+    uint32_t cur_inst = 0;
+    const double* w2o64 = nullptr;
+    RaySetup r;
+    const float delta_top = 9.5367431640625e-07f * (maxabs3(wox, woy, woz) + S.R_top);  // 2^-20
+    setup_boxes(r, wox, woy, woz, wdx, wdy, wdz, delta_top);
+    uint32_t cur = 0;  // TLAS root, an inner reference
+    bool have = true;
+    uint32_t steps = 0;
+    uint32_t err = 0;
+    for (;;) {
+        if (have) {
+            if (!(cur & kRefLeaf)) {
+                if (++steps > max_steps) {
+                    err |= kErrStepLimit;
+                    break;
+                }
+                ++st.nodes;
+                float t[4];
+                uint32_t ref[4];
+                const int nh = node_children<FETCH>(S.nodes + node_base + cur, r, tmin, h.t, t, ref);
+                if (nh == 0) {
+                    have = false;
+                } else {
+                    if (sp + nh - 1 > STACK) {
+                        err |= kErrStackOverflow;
+                        break;
+                    }
+#pragma unroll
+                    for (int k = 3; k >= 1; --k)
+                        if (k < nh)
+                            stack[sp++] = ((uint64_t)__float_as_uint(t[k]) << 32) | ref[k];
+                    cur = ref[0];
+                }
+                continue;
+            }
+            if (top) {
+                // enter instance cur_inst
+                cur_inst = cur & kRefIndexMask;
+                const InstDev* ip = S.inst + cur_inst;
+                const float4* q4 = reinterpret_cast<const float4*>(ip);
+                const float4 m0 = __ldg(q4), m1 = __ldg(q4 + 1), m2 = __ldg(q4 + 2);
+                const uint4 m3 = __ldg(reinterpret_cast<const uint4*>(ip) + 3);
+                const float ox = __fmaf_rn(m0.x, wox, __fmaf_rn(m0.y, woy, __fmaf_rn(m0.z, woz, m0.w)));
+                const float oy = __fmaf_rn(m1.x, wox, __fmaf_rn(m1.y, woy, __fmaf_rn(m1.z, woz, m1.w)));
+                const float oz = __fmaf_rn(m2.x, wox, __fmaf_rn(m2.y, woy, __fmaf_rn(m2.z, woz, m2.w)));
+                const float dx = __fmaf_rn(m0.x, wdx, __fmaf_rn(m0.y, wdy, __fmul_rn(m0.z, wdz)));
+                const float dy = __fmaf_rn(m1.x, wdx, __fmaf_rn(m1.y, wdy, __fmul_rn(m1.z, wdz)));
+                const float dz = __fmaf_rn(m2.x, wdx, __fmaf_rn(m2.y, wdy, __fmul_rn(m2.z, wdz)));
+                node_base = m3.x;
+                quad_base = m3.y;
+                const float R = __uint_as_float(m3.z);
+                const float delta = 3.814697265625e-06f * (maxabs3(ox, oy, oz) + R);  // 2^-18
+                setup_boxes(r, ox, oy, oz, dx, dy, dz, delta);
+                setup_shear(r, dx, dy, dz);
+                w2o64 = S.inst64 + 12 * (size_t)cur_inst;
+                inst_sp = sp;
+                top = false;
+                ++st.insts;
+                cur = 0;
+                continue;
+            }
+            // BLAS leaf: test its quads
+            {
+                const uint32_t first = cur & kRefIndexMask;
+                const uint32_t cnt = ((cur >> 27) & 0xFu) + 1u;
+                bool done = false;
+                for (uint32_t k = 0; k < cnt; ++k) {
+                    const uint32_t slot = quad_base + first + k;
+                    float tt, uu, vv;
+                    ++st.quads;
+                    if (!quad_test(r, S.quads + slot, w2o64, wox, woy, woz, wdx, wdy, wdz, tmin,
+                                   &tt, &uu, &vv, &st.fallbacks))
+                        continue;
+                    if (!(tt < tmax)) continue;
+                    if (ANY) {
+                        h.t = tt;
+                        h.inst = cur_inst;
+                        h.prim = __ldg(S.prim + slot);
+                        h.slot = slot;
+                        done = true;
+                        break;
+                    }
+                    if (tt < h.t) {
+                        h.t = tt;
+                        h.inst = cur_inst;
+                        h.prim = __ldg(S.prim + slot);
+                        h.u = uu;
+                        h.v = vv;
+                        h.slot = slot;
+                    } else if (tt == h.t) {
+                        const uint32_t pr = __ldg(S.prim + slot);
+                        if (cur_inst < h.inst || (cur_inst == h.inst && pr < h.prim)) {
+                            h.inst = cur_inst;
+                            h.prim = pr;
+                            h.u = uu;
+                            h.v = vv;
+                            h.slot = slot;
+                        }
+                    }
+                }
+                if (done) break;
+                have = false;
+            }
+        }
+        // pop
+        if (!top && sp == inst_sp) {
+            top = true;
+            node_base = S.tlas_base;
+            setup_boxes(r, wox, woy, woz, wdx, wdy, wdz, delta_top);
+        }
+        if (sp == 0) break;
+        const uint64_t e = stack[--sp];
+        if (__uint_as_float((uint32_t)(e >> 32)) > h.t) continue;
+        cur = (uint32_t)e;
+        have = true;
+    }
+    return err;
+}
+
+}  // namespace qrt

@@ -1,0 +1,295 @@
+"""GPU parity on the tiny instanced scene (one 64x64-quad mesh, 256
+instances): ray queries, path tracing, batching, graphs, the adjoint, and the
+device error paths, all through the C ABI against the FP64 oracle."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from paper_2001_02620_gb300 import inputs as I
+
+from parity import NONE, classify_closest, path_agreement
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2001_02620_gb300 import build as B
+    B.build()
+    from paper_2001_02620_gb300 import api as A
+    return A
+
+
+@pytest.fixture(scope="module")
+def tiny(api):
+    sc = I.tiny_scene()
+    return sc, api.Scene(sc), O.OracleScene(sc)
+
+
+def _rays(sc):
+    lo, hi = I.scene_box(sc)
+    tg = I.instance_origins(sc)
+    return np.concatenate([
+        I.rays_focused(65536, (50, -120, 50), lo, hi, seed=31),
+        I.rays_toward(131072, lo - 30, hi + 30, tg, 1.5, seed=32),
+        I.rays_random(65536, lo, hi, seed=33),
+    ])
+
+
+SETTINGS = [dict(), dict(stack=32), dict(fetch=32), dict(block=64), dict(block=256, fetch=32)]
+
+
+@pytest.mark.parametrize("tuning", SETTINGS)
+def test_trace_closest_matches_oracle(api, tiny, tuning):
+    sc, gs, osc = tiny
+    rays = _rays(sc)
+    d_rays = torch.from_numpy(rays).cuda()
+    hits = gs.trace_closest(d_rays, tuning=tuning)
+    gs.check()
+    h = hits.cpu().numpy().view(np.uint32)
+    o_t, o_i, o_p, _, _ = osc.trace_closest(rays)
+    n, acc, bad = classify_closest(sc, rays, h[:, 1], h[:, 2], o_t, o_i, o_p)
+    assert not bad, f"{len(bad)} unexplained mismatches, e.g. ray {bad[:5]}"
+    assert acc / len(rays) < 1e-5, f"{acc} near-tie mismatches of {len(rays)}"
+    hit = o_i != NONE
+    assert hit.mean() > 0.2
+    same = hit & (h[:, 1] == o_i) & (h[:, 2] == o_p)
+    gt = h[:, 0].view(np.float32).astype(np.float64)
+    np.testing.assert_allclose(gt[same], o_t[same], rtol=2e-5)
+    # misses report t = tmax
+    miss = (o_i == NONE) & (h[:, 1] == NONE)
+    assert np.all(gt[miss] == rays[miss, 7])
+
+
+@pytest.mark.parametrize("tuning", SETTINGS[:3])
+def test_trace_any_matches_oracle(api, tiny, tuning):
+    sc, gs, osc = tiny
+    rays = _rays(sc)
+    rays[::3, 7] = np.float32(40.0)   # finite tmax on a third of the rays
+    d_rays = torch.from_numpy(rays).cuda()
+    bits = gs.trace_any(d_rays, tuning=tuning).cpu().numpy().view(np.uint32)
+    gs.check()
+    occ = ((bits[np.arange(len(rays)) // 32] >> (np.arange(len(rays)) % 32)) & 1).astype(bool)
+    ref = osc.trace_any(rays)
+    mism = np.nonzero(occ != ref)[0]
+    # any mismatch must be a near-grazing ray; classify with closest hits
+    if len(mism):
+        o_t, o_i, o_p, _, _ = osc.trace_closest(rays[mism])
+        hits = gs.trace_closest(d_rays[torch.from_numpy(mism).cuda()]).cpu().numpy().view(np.uint32)
+        n, acc, bad = classify_closest(sc, rays[mism], hits[:, 1], hits[:, 2], o_t, o_i, o_p)
+        assert not bad
+    assert len(mism) / len(rays) < 1e-5
+
+
+def test_empty_and_ragged_ray_counts(api, tiny):
+    sc, gs, osc = tiny
+    rays = _rays(sc)
+    for n in (0, 1, 31, 33, 1000, 4097):
+        d = torch.from_numpy(rays[:n].copy()).cuda() if n else torch.empty((0, 8), device="cuda")
+        h = gs.trace_closest(d)
+        b = gs.trace_any(d)
+        assert h.shape == (n, 4) and b.shape == ((n + 31) // 32,)
+        if n:
+            o_t, o_i, o_p, _, _ = osc.trace_closest(rays[:n])
+            hh = h.cpu().numpy().view(np.uint32)
+            assert (hh[:, 1] == o_i).mean() > 0.999
+    gs.check()
+
+
+def _render_compare(api, gs, osc, view, alb, params):
+    D = params.max_depth
+    log = torch.zeros(api.path_log_words([view], D), dtype=torch.int32, device="cuda")
+    (img,) = gs.render([view], torch.from_numpy(alb).cuda(), params, path_log=log)
+    gs.check()
+    g = img.reshape(-1, 3).double().cpu().numpy()
+    ref = osc.render(view, alb, params, log=True)
+    agree = path_agreement(log.cpu().numpy().view(np.uint32), ref, D)
+    pix_ok = agree.reshape(-1, view.spp).all(1)
+    r = ref["rgb"][pix_ok]
+    err = np.abs(g[pix_ok] - r)
+    return pix_ok, err, r, g, ref
+
+
+def test_render_tiny_env_only(api, tiny):
+    sc, gs, osc = tiny
+    view, params = I.tiny_view(), I.tiny_params()
+    alb = I.albedo(sc.n_quads)
+    pix_ok, err, r, g, ref = _render_compare(api, gs, osc, view, alb, params)
+    assert pix_ok.mean() > 0.995, f"divergent pixels {1 - pix_ok.mean():.2e}"
+    assert (err <= 1e-4 * np.abs(r) + 1e-6).all(), err.max()
+
+
+def test_render_tiny_sun_and_depth(api, tiny):
+    sc, gs, osc = tiny
+    view = I.tiny_view()
+    view.spp = 3
+    view.w, view.h = 200, 120   # ragged: not a multiple of the warp batch
+    params = I.Params(max_depth=4, sun_dir=I.MID_SUN_DIR, sun_E=(3.0, 2.0, 1.0),
+                      env=(0.8, 1.0, 1.2))
+    alb = I.albedo(sc.n_quads)
+    pix_ok, err, r, g, ref = _render_compare(api, gs, osc, view, alb, params)
+    assert pix_ok.mean() > 0.99, f"divergent pixels {1 - pix_ok.mean():.2e}"
+    assert (err <= 1e-4 * np.abs(r) + 1e-6).all(), err.max()
+
+
+def test_white_furnace_gpu(api):
+    v, q = I.sphere_mesh(24, 48, 5.0)
+    sc = I.Scene([(v, q)], I.IDENTITY_XFORM[None].copy(), np.zeros(1, dtype=np.uint32))
+    gs = api.Scene(sc)
+    view = I.View(eye=(0.0, -30.0, 4.0), look=(0.0, 0.0, 0.0), up=(0, 0, 1), vfov_deg=30.0,
+                  w=96, h=64, spp=4)
+    ones = torch.ones((sc.n_quads, 3), device="cuda")
+    (img,) = gs.render([view], ones, I.Params(max_depth=256, env=(1.0, 1.0, 1.0)))
+    gs.check()
+    assert torch.all(img == 1.0)
+
+
+def test_batched_equals_plain_bit_exact(api, tiny):
+    sc, gs, osc = tiny
+    views = I.batched_views(n_views=7, min_log2=5.0, max_log2=8.0, max_spp=4)
+    for v in views:
+        v.eye = (50.0 + (v.eye[0] - 2048.0) / 40, -120.0, 50.0)
+        v.look = (50.0, 50.0, 50.0)
+    params = I.Params(max_depth=3, sun_dir=I.MID_SUN_DIR, sun_E=(3.0, 3.0, 3.0))
+    alb = torch.from_numpy(I.albedo(sc.n_quads)).cuda()
+    batched = gs.render(views, alb, params, tuning=dict(batch=2))
+    plain = [gs.render([v], alb, params)[0] for v in views]
+    graph = api.RenderGraph(gs, views, alb, params)
+    g1 = [x.clone() for x in graph.launch()]
+    g2 = graph.launch()
+    gs.check()
+    for b, p, x, y in zip(batched, plain, g1, g2):
+        assert torch.equal(b, p)
+        assert torch.equal(b, x)
+        assert torch.equal(b, y)
+
+
+def test_many_views_split_across_launches(api, tiny):
+    sc, gs, osc = tiny
+    views = []
+    for k in range(70):   # more views than one launch holds
+        views.append(I.View(eye=(50.0, -120.0 + k, 50.0), look=(50, 50, 50), up=(0, 0, 1),
+                            vfov_deg=40.0, w=16, h=8 + k % 3, spp=1, pixel_base=1000 * k))
+    params = I.tiny_params()
+    alb = torch.from_numpy(I.albedo(sc.n_quads)).cuda()
+    out = gs.render(views, alb, params)
+    gs.check()
+    for k in (0, 63, 64, 69):
+        (one,) = gs.render([views[k]], alb, params)
+        assert torch.equal(one, out[k])
+
+
+def test_adjoint_matches_oracle_gradient(api, tiny):
+    sc, gs, osc = tiny
+    view, params = I.tiny_view(), I.Params(max_depth=3, sun_dir=I.MID_SUN_DIR, sun_E=(3, 3, 3))
+    view.spp = 2
+    alb = I.albedo(sc.n_quads)
+    D = params.max_depth
+    dimg = np.random.default_rng(8).normal(size=(view.h, view.w, 3)).astype(np.float32)
+    d_alb = torch.from_numpy(alb).cuda()
+    grad = torch.zeros_like(d_alb)
+    gs.adjoint([view], d_alb, [torch.from_numpy(dimg).cuda()], grad, params)
+    log = torch.zeros(api.path_log_words([view], D), dtype=torch.int32, device="cuda")
+    gs.render([view], d_alb, params, path_log=log)
+    gs.check()
+    g = grad.double().cpu().numpy()
+    ref = osc.render(view, alb, params, log=True)
+    og = osc.grad(view, alb, params, dimg.reshape(-1, 3).astype(np.float64))
+    agree = path_agreement(log.cpu().numpy().view(np.uint32), ref, D)
+    # quads touched by a divergent path (either side) are excluded and counted
+    gl = log.cpu().numpy().view(np.uint32).reshape(-1, 2 * D + 1)
+    offs = sc.quad_offsets
+    touched = set()
+    for k in np.nonzero(~agree)[0]:
+        for inst, prim in list(zip(ref["inst"][k], ref["prim"][k])) + list(zip(gl[k, 0:2 * D:2], gl[k, 1:2 * D:2])):
+            if inst != NONE:
+                touched.add(int(offs[sc.mesh_ids[inst]] + prim))
+    mask = np.ones(sc.n_quads, dtype=bool)
+    mask[list(touched)] = False
+    big = np.abs(og).max()
+    sel = mask[:, None] & (np.abs(og) > 1e-6 * big)
+    assert sel.sum() > 1000
+    rel = np.abs(g[sel] - og[sel]) / np.abs(og[sel])
+    assert rel.max() < 1e-4, (rel.max(), len(touched))
+    assert (~agree).mean() < 0.01
+
+
+def test_l2_loss(api):
+    rng = np.random.default_rng(1)
+    a = rng.uniform(size=(37, 53, 3)).astype(np.float32)
+    b = rng.uniform(size=(37, 53, 3)).astype(np.float32)
+    da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    dimg = torch.empty_like(da)
+    loss = api.l2_loss(da, db, dimg)
+    ref = ((a.astype(np.float64) - b) ** 2).mean()
+    assert abs(float(loss) - ref) < 1e-12 * max(1.0, ref)
+    np.testing.assert_allclose(dimg.cpu().numpy(), 2 * (a.astype(np.float64) - b) / a.size, rtol=1e-6)
+
+
+def test_stack_overflow_is_reported(api):
+    """A chain-shaped BLAS over coincident quads needs about three stack
+    entries per level: a 32-entry stack overflows, the kernel stops that ray
+    and raises the error word; the context stays usable."""
+    vv = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0]], dtype=np.float32)
+    q = np.tile(np.array([[0, 1, 2, 3]], dtype=np.uint32), (300, 1))
+    sc = I.Scene([(vv, q)], I.IDENTITY_XFORM[None].copy(), np.zeros(1, dtype=np.uint32))
+    gs = api.Scene(sc, build_opts=dict(degenerate=1))
+    rays = torch.from_numpy(I.ray_array(np.array([[0.5, 0.5, 5.0]]), np.array([[0.0, 0.0, -1.0]]))).cuda()
+    gs.trace_closest(rays, tuning=dict(stack=32))
+    with pytest.raises(api.N.QrtError) as e:
+        gs.check()
+    assert e.value.code == api.N.QRT_ERR_STACK_OVERFLOW
+    gs.check()   # cleared after reading
+    # a normal scene still traces afterwards
+    sc2 = I.tiny_scene()
+    gs2 = api.Scene(sc2)
+    gs2.trace_closest(torch.from_numpy(_rays(sc2)[:1000]).cuda())
+    gs2.check()
+
+
+def test_step_limit_is_reported(api, tiny):
+    sc, gs, osc = tiny
+    view = I.tiny_view()
+    view.w = view.h = 32
+    alb = torch.from_numpy(I.albedo(sc.n_quads)).cuda()
+    gs.render([view], alb, I.tiny_params(), max_steps=2)
+    with pytest.raises(api.N.QrtError) as e:
+        gs.check()
+    assert e.value.code == api.N.QRT_ERR_STEP_LIMIT
+    gs.render([view], alb, I.tiny_params())
+    gs.check()
+
+
+def test_invalid_arguments_rejected(api, tiny):
+    sc, gs, osc = tiny
+    alb = torch.from_numpy(I.albedo(sc.n_quads)).cuda()
+    view = I.tiny_view()
+    with pytest.raises(api.N.QrtError):
+        gs.render([view], alb, I.Params(max_depth=0))
+    with pytest.raises(api.N.QrtError):
+        gs.render([view], alb, I.tiny_params(), tuning=dict(stack=48))
+    bad = I.View(eye=(0, 0, 0), look=(0, 0, 0), up=(0, 0, 1), vfov_deg=40, w=8, h=8, spp=1)
+    with pytest.raises(api.N.QrtError):
+        gs.render([bad], alb, I.tiny_params())
+    buf = torch.zeros(40 * 8 + 1, device="cuda")
+    with pytest.raises(api.N.QrtError) as e:
+        gs.trace_closest(buf[1:].view(40, 8))   # 4-byte offset: not 16-byte aligned
+    assert e.value.code == api.N.QRT_ERR_ALIGN
+
+
+def test_scene_without_instances(api):
+    v, q = I.plane_mesh(2)
+    sc = I.Scene([(v, q)], np.zeros((0, 12), dtype=np.float32), np.zeros(0, dtype=np.uint32))
+    gs = api.Scene(sc)
+    rays = torch.from_numpy(I.rays_random(100, [-1, -1, -1], [1, 1, 1], seed=1)).cuda()
+    h = gs.trace_closest(rays).cpu().numpy().view(np.uint32)
+    assert (h[:, 1] == NONE).all()
+    view = I.View(eye=(0, -5, 0), look=(0, 0, 0), up=(0, 0, 1), vfov_deg=40, w=8, h=8, spp=1)
+    (img,) = gs.render([view], torch.ones((sc.n_quads, 3), device="cuda"),
+                       I.Params(max_depth=2, env=(0.25, 0.5, 1.0)))
+    gs.check()
+    assert torch.all(img == torch.tensor([0.25, 0.5, 1.0], device="cuda"))

@@ -1,0 +1,138 @@
+"""CPU-only checks of the C ABI library: it loads, exports every symbol the
+header declares, rejects bad arguments on the host, and its BVH builder keeps
+its invariants.  No GPU call is made here."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2001_02620_gb300 import build as B
+from paper_2001_02620_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def native():
+    B.build()
+    from paper_2001_02620_gb300 import _native as N
+    return N
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "qrt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(qrt_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for f in ["qrt_scene_create", "qrt_scene_destroy", "qrt_trace_closest", "qrt_trace_any",
+              "qrt_render_spp", "qrt_render_adjoint", "qrt_check"]:
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol(native):
+    L = C.CDLL(native.LIB_PATH)
+    for name in _declared():
+        assert hasattr(L, name), name
+    # and the binding declares a signature for each of them
+    assert sorted(native.SIGNATURES) == _declared()
+
+
+def test_version_and_error_string(native):
+    L = native.lib()
+    assert L.qrt_version() == 1
+    assert isinstance(L.qrt_last_error(), bytes)
+
+
+def test_host_side_argument_errors(native):
+    L = native.lib()
+    # NULL scene handles are rejected before any CUDA call
+    assert L.qrt_trace_closest(None, None, 10, None, None, None) == native.QRT_ERR_INVALID_ARG
+    assert b"scene" in L.qrt_last_error()
+    assert L.qrt_trace_any(None, None, 0, None, None, None) == native.QRT_ERR_INVALID_ARG
+    assert L.qrt_render_spp(None, None, 0, None, None, None) == native.QRT_ERR_INVALID_ARG
+    assert L.qrt_check(None, None) == native.QRT_ERR_INVALID_ARG
+    assert L.qrt_scene_destroy(None) == native.QRT_ERR_INVALID_ARG
+    assert L.qrt_graph_launch(None, None) == native.QRT_ERR_INVALID_ARG
+    assert L.qrt_l2_loss(None, None, 0, None, None, None) == native.QRT_ERR_INVALID_ARG
+    out = C.c_void_p()
+    assert L.qrt_scene_create(None, 0, None, None, 0, None, C.byref(out)) == native.QRT_ERR_INVALID_ARG
+    # an instance naming a missing mesh is rejected before any device work
+    v, q = I.plane_mesh(2)
+    m = (native.qrt_mesh * 1)()
+    m[0].verts = v.ctypes.data_as(C.POINTER(C.c_float))
+    m[0].n_verts = v.shape[0]
+    m[0].quads = q.ctypes.data_as(C.POINTER(C.c_uint32))
+    m[0].n_quads = q.shape[0]
+    xf = np.tile(I.IDENTITY_XFORM, 2)
+    ids = np.array([0, 3], dtype=np.uint32)
+    rc = L.qrt_scene_create(m, 1, xf.ctypes.data_as(C.POINTER(C.c_float)),
+                            ids.ctypes.data_as(C.POINTER(C.c_uint32)), 2, None, C.byref(out))
+    assert rc == native.QRT_ERR_INVALID_ARG and b"out of range" in L.qrt_last_error()
+
+
+def _check_mesh(native, v, q, **opts):
+    L = native.lib()
+    m = native.qrt_mesh()
+    v = np.ascontiguousarray(v, dtype=np.float32)
+    q = np.ascontiguousarray(q, dtype=np.uint32)
+    m.verts = v.ctypes.data_as(C.POINTER(C.c_float))
+    m.n_verts = v.shape[0]
+    m.quads = q.ctypes.data_as(C.POINTER(C.c_uint32))
+    m.n_quads = q.shape[0]
+    o = native.qrt_build_opts()
+    for k, val in opts.items():
+        setattr(o, k, val)
+    n = C.c_uint64()
+    d = C.c_uint32()
+    rc = L.qrt_blas_build_check(C.byref(m), C.byref(o), C.byref(n), C.byref(d))
+    return rc, n.value, d.value, L.qrt_last_error().decode()
+
+
+@pytest.mark.parametrize("leaf", [1, 2, 4, 8])
+def test_blas_invariants_tiny_mesh(native, leaf):
+    v, q = I.tiny_mesh()
+    rc, n, d, msg = _check_mesh(native, v, q, max_leaf=leaf)
+    assert rc == 0, msg
+    assert n >= q.shape[0] / (leaf * 4)
+    assert d < 20
+
+
+def test_blas_invariants_varied_meshes(native):
+    rng = np.random.default_rng(3)
+    meshes = [I.displaced_grid(rng, 5000), I.noisy_blob(rng, 3000), I.sphere_mesh(10, 20),
+              I.plane_mesh(1), I.plane_mesh(3)]
+    # extreme coordinates: far from the origin and tiny extents
+    v, q = I.plane_mesh(16)
+    meshes.append((v * np.float32(1e-6) + np.float32(3e4), q))
+    meshes.append((v * np.float32(1e5), q))
+    # all quads coincident (zero centroid extent)
+    vv = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0]], dtype=np.float32)
+    meshes.append((vv, np.tile(np.array([[0, 1, 2, 3]], dtype=np.uint32), (50, 1))))
+    for v, q in meshes:
+        rc, n, d, msg = _check_mesh(native, v, q)
+        assert rc == 0, msg
+
+
+def test_blas_degenerate_chain_is_deep(native):
+    vv = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0]], dtype=np.float32)
+    q = np.tile(np.array([[0, 1, 2, 3]], dtype=np.uint32), (300, 1))
+    rc, n, d, msg = _check_mesh(native, vv, q, degenerate=1)
+    assert rc == 0, msg
+    assert d >= 90
+
+
+def test_blas_rejects_bad_meshes(native):
+    v, q = I.plane_mesh(2)
+    bad = q.copy()
+    bad[0, 0] = 999
+    rc, *_, msg = _check_mesh(native, v, bad)
+    assert rc == native.QRT_ERR_INVALID_ARG and "out of range" in msg
+    vn = v.copy()
+    vn[0, 0] = np.nan
+    rc, *_, msg = _check_mesh(native, vn, q)
+    assert rc == native.QRT_ERR_INVALID_ARG and "non-finite" in msg
