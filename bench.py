@@ -3,7 +3,7 @@
 A step is one qrt_render_spp of the mid workload: 64 prototypes + terrain
 (5.73 M unique quads), 100k instances, 1024x1024, 4 spp, path depth 5,
 environment + sun with shadow rays.  value = all rays traced per second
-(closest-hit + shadow), the accounting of the paper's Mray/s (Section 5).
+(closest-hit + shadow), the accounting of the paper's Mray/s (Section 6, "Results").
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun each rank renders its own frame (weak scaling, no collective
@@ -120,6 +120,99 @@ def oracle_sample(sc, view, params, alb, budget_s: float, rank_pixels: int = 0):
             "paths_per_s": done * view.spp / elapsed}
 
 
+def _time(fn, reps: int, warm: int = 2) -> float:
+    """Median seconds of fn() measured with CUDA events on the current stream."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) * 1e-3)
+    return float(np.median(ts))
+
+
+def bench_trace(scene, sc, dev):
+    """trace_closest / trace_any throughput on 4M-ray sets of the mid scene."""
+    import torch
+    from paper_2001_02620_gb300 import inputs as I
+    lo = np.array([0.0, 0.0, -150.0])
+    hi = np.array([4096.0, 4096.0, 250.0])
+    n = 1 << 22
+    sets = {
+        "primary": I.rays_focused(n, (2048.0, -300.0, 450.0), lo, hi, seed=51),
+        "incoherent": I.rays_random(n, lo, hi, seed=52),
+        "shadow": I.rays_parallel(n, lo, hi, I.MID_SUN_DIR, seed=53),
+    }
+    out = {}
+    hits = torch.empty((n, 4), dtype=torch.int32, device=dev)
+    bits = torch.empty(((n + 31) // 32,), dtype=torch.int32, device=dev)
+    for name, rays in sets.items():
+        d = torch.from_numpy(rays).to(dev)
+        tc = _time(lambda: scene.trace_closest(d, hits), 5)
+        ta = _time(lambda: scene.trace_any(d, bits), 5)
+        st = torch.zeros(STAT_WORDS, dtype=torch.int64, device=dev)
+        scene.trace_stats(d, False, hits, st)
+        s = st.cpu().numpy()
+        out[name] = {"closest_mrays_s": n / tc / 1e6, "any_mrays_s": n / ta / 1e6,
+                     "hit_rate": float((hits[:, 1] != -1).float().mean().item()),
+                     "nodes_per_ray": float(s[1]) / n, "quads_per_ray": float(s[2]) / n,
+                     "instances_per_ray": float(s[3]) / n}
+    scene.check()
+    return out
+
+
+def bench_batched(api, scene, d_alb, dev):
+    """32 uneven views of the mid scene: one graph-captured persistent launch
+    versus 32 plain launches on one stream; images must be bit-identical."""
+    import torch
+    from paper_2001_02620_gb300 import inputs as I
+    views = I.batched_views()
+    params = I.mid_params()
+    paths = sum(v.w * v.h * v.spp for v in views)
+    outs_b = [torch.empty((v.h, v.w, 3), device=dev) for v in views]
+    outs_p = [torch.empty((v.h, v.w, 3), device=dev) for v in views]
+    graph = api.RenderGraph(scene, views, d_alb, params, outs=outs_b)
+
+    def plain():
+        for v, o in zip(views, outs_p):
+            scene.render([v], d_alb, params, outs=[o])
+
+    tb = _time(graph.launch, 3, warm=1)
+    tp = _time(plain, 3, warm=1)
+    scene.check()
+    same = all(torch.equal(a, b) for a, b in zip(outs_b, outs_p))
+    return {"views": len(views), "paths": paths, "batched_paths_per_s": paths / tb,
+            "plain_paths_per_s": paths / tp, "speedup": tp / tb, "bit_identical": same,
+            "batched_ms": tb * 1e3, "plain_ms": tp * 1e3}
+
+
+def bench_adjoint(api, scene, sc, dev):
+    """Adjoint workload (512x512, 8 spp, depth 4): replay adjoint vs primal."""
+    import torch
+    from paper_2001_02620_gb300 import inputs as I
+    view, params = I.adjoint_view(), I.adjoint_params()
+    a0 = I.albedo(sc.n_quads)
+    alb = torch.from_numpy(a0).to(dev)
+    tgt_alb = torch.from_numpy(I.perturbed_albedo(a0)).to(dev)
+    (target,) = scene.render([view], tgt_alb, params)
+    img = torch.empty_like(target)
+    dimg = torch.empty_like(target)
+    grad = torch.zeros_like(alb)
+    tp = _time(lambda: scene.render([view], alb, params, outs=[img]), 5)
+    api.l2_loss(img, target, dimg)
+    ta = _time(lambda: scene.adjoint([view], alb, [dimg], grad, params), 5)
+    scene.check()
+    return {"primal_ms": tp * 1e3, "adjoint_ms": ta * 1e3, "ratio": ta / tp,
+            "paths": view.w * view.h * view.spp, "n_params": int(a0.size)}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -152,7 +245,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--extras", default="trace,batched,adjoint")
+    ap.add_argument("--extras", default="trace,batched,adjoint",
+                    help="comma list of sub-measurements to add (or 'none')")
+    ap.add_argument("--res", type=int, default=0,
+                    help="override the view side (small profiling captures only)")
+    ap.add_argument("--spp", type=int, default=0, help="override spp (profiling only)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -173,6 +270,10 @@ def main():
     from paper_2001_02620_gb300 import build as B
     B.build()
     sc, view, params, alb = mid_workload()
+    if args.res:
+        view.w = view.h = args.res
+    if args.spp:
+        view.spp = args.spp
     view.pixel_base = rank * view.w * view.h  # each rank renders its own frame
     t0 = time.time()
     scene = api.Scene(sc)
@@ -263,6 +364,13 @@ def main():
         "clocks": clk,
         "scene_build_s": build_s,
     }
+    extras = [] if args.extras == "none" else args.extras.split(",")
+    if "trace" in extras:
+        line["trace"] = bench_trace(scene, sc, dev)
+    if "batched" in extras:
+        line["batched_vs_plain"] = bench_batched(api, scene, d_alb, dev)
+    if "adjoint" in extras:
+        line["adjoint_vs_primal"] = bench_adjoint(api, scene, sc, dev)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = oracle_sample(sc, view, params, alb, budget_s=12.0)
     if rank == 0:

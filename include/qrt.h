@@ -3,11 +3,11 @@
  *
  * C ABI of the hot path of an interactive production-scene path tracer: a
  * two-level acceleration structure (a top-level BVH over object instances,
- * one BVH per object; Section 3.2 "Beyond Statistics" and Section 4.2
+ * one BVH per object; Section 4.2 "Beyond Statistics" and Section 5.2
  * "Geometry Types, Complexity, and Memory Consumption"), quads as the
- * primitive (Section 4.2, "Quads"), closest-hit and any-hit ray queries, and
+ * primitive (Section 5.2, "Quads"), closest-hit and any-hit ray queries, and
  * a diffuse path tracer with a maximum path depth and one sample per pixel
- * per progressive frame (Section 4.4 "Shading"; Section 5 "Results").
+ * per progressive frame (Section 5.4 "Shading"; Section 6 "Results").
  *
  * Conventions shared by every entry point:
  *  - Every function returns an int status: QRT_OK (0) or a negative QRT_ERR_*
@@ -176,7 +176,7 @@ const char* qrt_last_error(void);
 int qrt_version(void);
 
 /* Build the two-level structure on the host and upload it to the current
- * device (Section 4.2: objects are instanced, quads are the primitive).
+ * device (Section 5.2: objects are instanced, quads are the primitive).
  * meshes: n_mesh host descriptors; xforms: host float [n_inst*12]; mesh_ids:
  * host uint32 [n_inst].  Quad albedo rows are numbered mesh by mesh in order
  * (mesh m's quad q is row sum_{k<m} n_quads_k + q).  On success *out owns all
@@ -188,7 +188,7 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
 int qrt_scene_destroy(qrt_scene scene);
 int qrt_scene_stats_get(qrt_scene scene, qrt_scene_stats* out);
 
-/* Closest hit for n rays (Section 5: traversal and intersection dominate the
+/* Closest hit for n rays (Section 6, Table 1: traversal and intersection dominate the
  * frame).  d_rays: n qrt_ray, d_hits: n qrt_hit, both 16-byte aligned.
  * tuning may be NULL. */
 int qrt_trace_closest(qrt_scene scene, const qrt_ray* d_rays, uint64_t n, qrt_hit* d_hits,
@@ -200,7 +200,7 @@ int qrt_trace_closest(qrt_scene scene, const qrt_ray* d_rays, uint64_t n, qrt_hi
 int qrt_trace_any(qrt_scene scene, const qrt_ray* d_rays, uint64_t n, uint32_t* d_occ_bits,
                   const qrt_tuning* tuning, qrt_stream stream);
 
-/* Path-trace n_views views (Section 4.4, progressive path tracing; one
+/* Path-trace n_views views (Section 5.4, progressive path tracing; one
  * launch covers every (view, pixel) and all of each pixel's spp samples).
  * d_albedo: DEVICE float [n_quads*3], per unique quad RGB albedo.  Each
  * view's out_rgb receives the mean over its spp samples; results do not

@@ -9,12 +9,13 @@
  *
  * What it follows:
  *   - two-level instancing: a top-level structure over object instances, one
- *     structure per object, rays moved into object space (Section 4.2,
- *     "Geometry Types, Complexity, and Memory Consumption"; Section 3.2);
+ *     structure per object, rays moved into object space (Section 5.2,
+ *     "Geometry Types, Complexity, and Memory Consumption"; Section 4.2,
+ *     "Beyond Statistics");
  *   - quads as the primitive, each quad the pair of triangles it was merged
- *     from (Section 4.2, "Quads");
+ *     from (Section 5.2, paragraph "Quads");
  *   - a path tracer with progressive 1-spp accumulation and a maximum path
- *     depth (Section 4.4 "Shading"; Section 5 "Results": depth five).
+ *     depth (Section 5.4 "Shading"; Section 6 "Results": depth five).
  * Choices the paper leaves open are fixed identically on both sides and are
  * listed in the design notes ("readings").
  *

@@ -1,0 +1,124 @@
+"""Autotuner for the launch parameters of the render kernel.
+
+Searches traversal stack depth, node-fetch width, block size and the number of
+32-pixel groups a warp claims per fetch by timing renders of a proxy view
+(the target view at reduced resolution, same spp and depth) and keeps the
+fastest configuration that raised no device error.  Results are cached as
+JSON keyed by (GPU name, SM count, scene class), so later runs skip the
+search.  None of the parameters changes a rendered value: images are
+bit-identical under every candidate.
+"""
+from __future__ import annotations
+
+import dataclasses
+import itertools
+import json
+import os
+import time
+
+DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                             "autotune_cache", "qrt_tuning.json")
+
+SPACE = {
+    "block": [64, 128, 256],
+    "stack": [32, 64],
+    "fetch": [16, 32],
+    "batch": [1, 2, 4],
+}
+
+
+def candidates(space: dict | None = None) -> list[dict]:
+    space = space or SPACE
+    keys = sorted(space)
+    return [dict(zip(keys, vals)) for vals in itertools.product(*(space[k] for k in keys))]
+
+
+def scene_class(scene) -> str:
+    """Coarse key: scene name plus order of magnitude of quads and instances."""
+    import math
+    q = max(1, int(scene.n_quads))
+    i = max(1, int(getattr(scene, "n_instances", None) or len(scene.xforms)))
+    name = getattr(scene, "name", "") or "scene"
+    return f"{name}:q1e{int(math.log10(q))}:i1e{int(math.log10(i))}"
+
+
+def cache_key(gpu_name: str, sm_count: int, scene_cls: str, kind: str = "render") -> str:
+    return f"{gpu_name}|{sm_count}|{scene_cls}|{kind}"
+
+
+def load_cache(path: str = DEFAULT_CACHE) -> dict:
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def store_cache(entry_key: str, value: dict, path: str = DEFAULT_CACHE) -> None:
+    d = load_cache(path)
+    d[entry_key] = value
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def pick_best(timings: dict) -> tuple[str, float]:
+    """timings: candidate-json -> seconds (None = failed).  Returns the fastest."""
+    ok = {k: v for k, v in timings.items() if v is not None}
+    if not ok:
+        raise RuntimeError("no tuning candidate ran without error")
+    k = min(ok, key=lambda c: (ok[c], c))
+    return k, ok[k]
+
+
+def proxy_view(view, max_side: int = 256):
+    s = min(1.0, max_side / max(view.w, view.h))
+    return dataclasses.replace(view, w=max(32, int(view.w * s)), h=max(32, int(view.h * s)))
+
+
+def tune(scene, view, albedo, params, space: dict | None = None, reps: int = 3,
+         cache_path: str | None = DEFAULT_CACHE, scene_name: str | None = None,
+         force: bool = False, log=None) -> dict:
+    """Returns the best tuning dict for rendering `view` of `scene` (api.Scene)."""
+    import torch
+
+    from . import _native as N
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    cls = scene_class(type("S", (), {"n_quads": scene.n_quads, "n_instances": scene.n_instances,
+                                     "name": scene_name or ""})())
+    key = cache_key(props.name, props.multi_processor_count, cls)
+    if cache_path and not force:
+        hit = load_cache(cache_path).get(key)
+        if hit:
+            return hit["tuning"]
+    pv = proxy_view(view)
+    out = torch.empty((pv.h, pv.w, 3), device=albedo.device)
+    timings = {}
+    for cand in candidates(space):
+        ck = json.dumps(cand, sort_keys=True)
+        try:
+            scene.render([pv], albedo, params, outs=[out], tuning=cand)
+            scene.check()
+            ts = []
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                scene.render([pv], albedo, params, outs=[out], tuning=cand)
+                e1.record()
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1) * 1e-3)
+            scene.check()
+            timings[ck] = min(ts)
+        except N.QrtError:
+            timings[ck] = None
+        if log:
+            log(f"tune {ck}: {timings[ck]}")
+    best, t = pick_best(timings)
+    result = json.loads(best)
+    if cache_path:
+        store_cache(key, {"tuning": result, "seconds": t, "proxy": [pv.w, pv.h, pv.spp],
+                          "when": time.strftime("%Y-%m-%dT%H:%M:%S")}, cache_path)
+    return result

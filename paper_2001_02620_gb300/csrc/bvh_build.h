@@ -1,6 +1,6 @@
 // Host BVH builder: binned-SAH binary trees collapsed to four-wide nodes with
 // conservatively quantised child boxes (qrt_layout.h).  One BLAS per object,
-// one TLAS over instance world boxes (Section 4.2: objects instanced, quads as
+// one TLAS over instance world boxes (Section 5.2: objects instanced, quads as
 // the primitive).  Off the hot path: runs once in qrt_scene_create.
 #pragma once
 #include <stdint.h>

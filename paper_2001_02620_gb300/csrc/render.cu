@@ -8,8 +8,8 @@
 // are batched.  Random numbers: Philox4x32-10 keyed by the render seed with
 // counter (global pixel lo, global pixel hi, sample, bounce).
 //
-// Per path (Section 4.4, "Shading": a path tracer with progressive
-// one-sample-per-pixel refinement; Section 5: a maximum path depth):
+// Per path (Section 5.4, "Shading": a path tracer with progressive
+// one-sample-per-pixel refinement; Section 6: a maximum path depth):
 //   camera ray through (x + xi1, y + xi2);
 //   for i = 1..D: closest hit; on a miss add beta * env and stop; at a hit
 //   take the per-quad albedo a and the geometric normal faced against the
@@ -371,9 +371,9 @@ __global__ void __launch_bounds__(256) l2_loss_kernel(const float* __restrict__ 
     const double inv_n = 1.0 / (double)n;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        const float r = __fsub_rn(img[i], tgt[i]);
-        acc += (double)r * (double)r;
-        if (dimg) dimg[i] = (float)(2.0 * (double)r * inv_n);
+        const double r = (double)img[i] - (double)tgt[i];  // exact for float inputs
+        acc += r * r;
+        if (dimg) dimg[i] = (float)(2.0 * r * inv_n);
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
     if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;

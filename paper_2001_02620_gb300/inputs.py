@@ -19,7 +19,7 @@ seed 2, albedo seed 3, render seed 4):
 * ``adjoint`` -- the mid scene at 512x512, 8 spp, depth 4, plus a perturbed
   target albedo.
 
-They stand in for the Moana Island Scene (Section 3: 39.3 M instances of
+They stand in for the Moana Island Scene (Section 4: 39.3 M instances of
 prototypes ranging from a few dozen to millions of primitives, heavily
 overlapping), which is not available here.
 """

@@ -59,7 +59,8 @@ def test_trace_closest_matches_oracle(api, tiny, tuning):
     assert hit.mean() > 0.2
     same = hit & (h[:, 1] == o_i) & (h[:, 2] == o_p)
     gt = h[:, 0].view(np.float32).astype(np.float64)
-    np.testing.assert_allclose(gt[same], o_t[same], rtol=2e-5)
+    # FP32 t: relative error plus an absolute part from rounding of coordinates ~100
+    np.testing.assert_allclose(gt[same], o_t[same], rtol=2e-5, atol=1e-4)
     # misses report t = tmax
     miss = (o_i == NONE) & (h[:, 1] == NONE)
     assert np.all(gt[miss] == rays[miss, 7])
