@@ -105,11 +105,18 @@ typedef struct {
 /* Launch tuning; 0 in any field selects the library default.
  *   block          threads per block (64..1024, multiple of 32)
  *   blocks_per_sm  resident blocks per SM for persistent kernels
- *   batch          work items a warp claims per fetch, in units of 32
+ *   batch          single kernel: pixels a warp claims per fetch, in units
+ *                  of 32; wavefront: rays a lane claims per fetch
  *   stack          traversal stack entries per ray (32 or 64)
  *   fetch          node fetch width in bytes (16: 4x128-bit, 32: 2x256-bit loads)
- *   adjoint_mode   0/1 = path replay (recompute the path twice), 2 = keep the
- *                  current path's vertices in registers (one trace pass) */
+ *   adjoint_mode   reserved (0)
+ *   mode           renderer: 0 = default (wavefront), 1 = single persistent
+ *                  kernel (a lane renders whole pixels), 2 = wavefront (stages
+ *                  gen / trace / shade / shadow / accumulate over queues; a
+ *                  lane of a trace kernel takes a new ray as soon as its own
+ *                  is done).  Both give bit-identical images.
+ *   chunk_log2     wavefront: paths per chunk = 2^chunk_log2 (10..26,
+ *                  default 21); sets the size of the per-stream workspace */
 typedef struct {
     uint32_t block;
     uint32_t blocks_per_sm;
@@ -117,7 +124,8 @@ typedef struct {
     uint32_t stack;
     uint32_t fetch;
     uint32_t adjoint_mode;
-    uint32_t reserved[2];
+    uint32_t mode;
+    uint32_t chunk_log2;
 } qrt_tuning;
 
 /* Path-tracing parameters.

@@ -18,6 +18,7 @@
 
 #include "bvh_build.h"
 #include "launch.h"
+#include "wavefront.h"
 
 using namespace qrt;
 
@@ -40,6 +41,14 @@ constexpr size_t kSlotStride = 128;  // bytes between counters (own cache line)
 
 }  // namespace
 
+// Scratch of one stream: a work counter for the single-kernel renderer and
+// the wavefront workspace (grown on demand, outside stream capture).
+struct StreamSlot {
+    unsigned long long* counter = nullptr;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+};
+
 struct qrt_scene_s {
     int device = -1;
     int sm_count = 0;
@@ -48,28 +57,31 @@ struct qrt_scene_s {
     void* d_quads = nullptr;
     void* d_prim = nullptr;
     void* d_inst = nullptr;
-    void* d_inst64 = nullptr;
     uint32_t* d_err = nullptr;
     char* d_counters = nullptr;  // kCounterSlots counters, kSlotStride apart
     std::mutex mu;
     std::unordered_map<cudaStream_t, int> slot_of;
+    std::vector<StreamSlot> slots;
     int next_slot = 0;
     qrt_scene_stats stats{};
 
-    // One work counter per stream: calls on one stream are ordered, so they
-    // may share it; different streams get different counters.
-    unsigned long long* counter_for(cudaStream_t s) {
+    // Calls on one stream are ordered, so they may share scratch; different
+    // streams get different slots (up to kCounterSlots, then reused).
+    StreamSlot& slot_for(cudaStream_t s) {
         std::lock_guard<std::mutex> g(mu);
+        if (slots.empty()) slots.resize(kCounterSlots);
         auto it = slot_of.find(s);
-        int slot;
+        int k;
         if (it != slot_of.end()) {
-            slot = it->second;
+            k = it->second;
         } else {
-            slot = next_slot % kCounterSlots;
+            k = next_slot % kCounterSlots;
             next_slot++;
-            slot_of[s] = slot;
+            slot_of[s] = k;
         }
-        return reinterpret_cast<unsigned long long*>(d_counters + kSlotStride * slot);
+        StreamSlot& sl = slots[k];
+        sl.counter = reinterpret_cast<unsigned long long*>(d_counters + kSlotStride * k);
+        return sl;
     }
 };
 
@@ -77,6 +89,7 @@ struct qrt_graph_s {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     unsigned long long* d_counter = nullptr;
+    void* ws = nullptr;
     int device = -1;
 };
 
@@ -88,9 +101,9 @@ void free_scene(qrt_scene_s* s) {
     cudaFree(s->d_quads);
     cudaFree(s->d_prim);
     cudaFree(s->d_inst);
-    cudaFree(s->d_inst64);
     cudaFree(s->d_err);
     cudaFree(s->d_counters);
+    for (StreamSlot& sl : s->slots) cudaFree(sl.ws);
     delete s;
 }
 
@@ -113,6 +126,8 @@ Tune resolve_tuning(const qrt_tuning* t) {
     if (t->stack) r.stack = (int)t->stack;
     if (t->fetch) r.fetch = (int)t->fetch;
     if (t->adjoint_mode) r.adjoint_mode = (int)t->adjoint_mode;
+    if (t->mode) r.mode = (int)t->mode;
+    if (t->chunk_log2) r.chunk_log2 = (int)t->chunk_log2;
     return r;
 }
 
@@ -126,8 +141,10 @@ int validate_tuning(const Tune& t) {
     if (t.batch < 1 || t.batch > 64) return fail(QRT_ERR_INVALID_ARG, "tuning.batch must be 1..64");
     if (t.blocks_per_sm < 0 || t.blocks_per_sm > 32)
         return fail(QRT_ERR_INVALID_ARG, "tuning.blocks_per_sm must be 0..32");
-    if (t.adjoint_mode < 1 || t.adjoint_mode > 2)
-        return fail(QRT_ERR_INVALID_ARG, "tuning.adjoint_mode must be 0, 1 or 2");
+    if (t.adjoint_mode != 0) return fail(QRT_ERR_INVALID_ARG, "tuning.adjoint_mode must be 0");
+    if (t.mode < 1 || t.mode > 2) return fail(QRT_ERR_INVALID_ARG, "tuning.mode must be 0, 1 or 2");
+    if (t.chunk_log2 < 10 || t.chunk_log2 > 26)
+        return fail(QRT_ERR_INVALID_ARG, "tuning.chunk_log2 must be 10..26");
     return QRT_OK;
 }
 
@@ -274,9 +291,8 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
     if (nq > 0xFFFFFFFFull || nn > 0xFFFFFFFFull)
         return fail(QRT_ERR_INVALID_ARG, "scene exceeds 2^32 quads or nodes");
 
-    // 3. instances: FP64 inverse, FP32 copy, world boxes
+    // 3. instances: FP64 inverse, world boxes
     std::vector<InstDev> inst(n_inst);
-    std::vector<double> inst64(12 * n_inst);
     std::vector<FBox> wbox(n_inst);
     std::vector<float> meshR(n_mesh);
     for (uint32_t m = 0; m < n_mesh; ++m) {
@@ -295,13 +311,12 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
         if (!finite || !inverse3(A, Ai))
             return fail(QRT_ERR_INVALID_ARG,
                         "instance " + std::to_string(i) + " has a non-finite or singular transform");
-        double* w = &inst64[12 * i];
-        for (int r = 0; r < 3; ++r) {
-            for (int c = 0; c < 3; ++c) w[4 * r + c] = Ai[3 * r + c];
-            w[4 * r + 3] = -(Ai[3 * r] * x[3] + Ai[3 * r + 1] * x[7] + Ai[3 * r + 2] * x[11]);
-        }
         InstDev& I = inst[i];
-        for (int k = 0; k < 12; ++k) I.w2o[k] = (float)w[k];
+        std::memset(&I, 0, sizeof(I));
+        for (int k = 0; k < 9; ++k) I.w[k] = Ai[k];
+        I.c[0] = x[3];
+        I.c[1] = x[7];
+        I.c[2] = x[11];
         const uint32_t m = mesh_ids[i];
         I.node_base = (uint32_t)node_base[m];
         I.quad_base = (uint32_t)quad_base[m];
@@ -353,7 +368,6 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
     if (e == cudaSuccess) e = upload(&s->d_quads, quads);
     if (e == cudaSuccess) e = upload(&s->d_prim, prim);
     if (e == cudaSuccess) e = upload(&s->d_inst, inst);
-    if (e == cudaSuccess) e = upload(&s->d_inst64, inst64);
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_err, 2 * sizeof(uint32_t));
     if (e == cudaSuccess) {
         const uint32_t init[2] = {0u, 0xFFFFFFFFu};
@@ -369,7 +383,6 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
     s->S.quads = static_cast<const QuadDev*>(s->d_quads);
     s->S.prim = static_cast<const uint32_t*>(s->d_prim);
     s->S.inst = static_cast<const InstDev*>(s->d_inst);
-    s->S.inst64 = static_cast<const double*>(s->d_inst64);
     s->S.tlas_base = (uint32_t)tlas_base;
     s->S.n_inst = (uint32_t)n_inst;
     s->S.R_top = R_top;
@@ -380,7 +393,7 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
     s->stats.blas_nodes = nn;
     s->stats.tlas_nodes = tlas.nodes.size();
     s->stats.device_bytes = nodes.size() * sizeof(QNode) + quads.size() * sizeof(QuadDev) +
-                            prim.size() * 4 + inst.size() * sizeof(InstDev) + inst64.size() * 8;
+                            prim.size() * 4 + inst.size() * sizeof(InstDev);
     s->stats.max_blas_depth = max_blas_depth;
     s->stats.tlas_depth = tlas.depth;
     s->stats.build_seconds = build_s;
@@ -412,9 +425,10 @@ static int trace_common(bool any, qrt_scene scene, const qrt_ray* d_rays, uint64
     if (rc) return rc;
     rc = check_device(scene);
     if (rc) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = launch_trace(any, scene->S, d_rays, n, any ? nullptr : out,
-                                 any ? static_cast<uint32_t*>(out) : nullptr, 1u << 20, nullptr, t,
-                                 reinterpret_cast<cudaStream_t>(stream));
+                                 any ? static_cast<uint32_t*>(out) : nullptr, 1u << 20,
+                                 scene->slot_for(s).counter, nullptr, t, scene->sm_count, s);
     if (e != cudaSuccess) return cuda_fail(e, "trace launch");
     return QRT_OK;
 }
@@ -510,36 +524,117 @@ int make_params(const qrt_params* p, ParamsDev& P) {
     return QRT_OK;
 }
 
-// Enqueues the render (or adjoint) of all views on stream s using counter.
+// Ensures sl holds a wavefront workspace of at least `bytes`.  Allocation is
+// refused while the stream is being captured.
+int ensure_workspace(StreamSlot& sl, size_t bytes, cudaStream_t s) {
+    if (sl.ws_bytes >= bytes) return QRT_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
+    if (cs != cudaStreamCaptureStatusNone)
+        return fail(QRT_ERR_NOT_READY,
+                    "wavefront workspace must be allocated before capture: render once on this "
+                    "stream outside capture, or use qrt_render_graph_create");
+    // the old workspace may still be in use by queued work on this stream
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    cudaFree(sl.ws);
+    sl.ws = nullptr;
+    sl.ws_bytes = 0;
+    e = cudaMalloc(&sl.ws, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "wavefront workspace");
+    sl.ws_bytes = bytes;
+    return QRT_OK;
+}
+
+// Enqueues the render (or adjoint) of all views on stream s.  counter serves
+// the single-kernel renderer, workspace (bytes) the wavefront one.
 int render_enqueue(qrt_scene scene, const qrt_view* views, uint32_t n_views, const float* d_albedo,
                    const float* const* d_dimage, float* d_grad, const qrt_params* params,
-                   unsigned long long* counter, unsigned long long* stats, cudaStream_t s) {
+                   unsigned long long* counter, void* workspace, size_t ws_bytes,
+                   unsigned long long* stats, cudaStream_t s) {
     Tune t = resolve_tuning(params ? &params->tuning : nullptr);
     int rc = validate_tuning(t);
     if (rc) return rc;
-    static_assert(sizeof(RenderArgs) < 32000, "kernel parameter block too large");
-    RenderArgs* A = new RenderArgs();
-    std::memset(A, 0, sizeof(RenderArgs));
-    A->S = scene->S;
-    A->albedo = d_albedo;
-    A->grad = d_grad;
-    A->counter = counter;
-    A->stats = stats;
-    A->batch = (uint32_t)t.batch;
-    rc = make_params(params, A->P);
+    const bool adjoint = d_grad != nullptr;
+    if (t.mode == 1) {
+        static_assert(sizeof(RenderArgs) < 32000, "kernel parameter block too large");
+        RenderArgs* A = new RenderArgs();
+        std::memset(A, 0, sizeof(RenderArgs));
+        A->S = scene->S;
+        A->albedo = d_albedo;
+        A->grad = d_grad;
+        A->counter = counter;
+        A->stats = stats;
+        A->batch = (uint32_t)t.batch;
+        rc = make_params(params, A->P);
+        if (adjoint) A->P.path_log = nullptr;
+        uint64_t paths = 0;
+        for (uint32_t first = 0; rc == QRT_OK && first < n_views; first += kMaxViewsPerLaunch) {
+            const uint32_t cnt = std::min<uint32_t>(kMaxViewsPerLaunch, n_views - first);
+            rc = make_views(views, first, cnt, d_dimage, *A, paths);
+            if (rc) break;
+            for (uint32_t k = 0; k < cnt; ++k)
+                paths += (uint64_t)views[first + k].w * views[first + k].h * views[first + k].spp;
+            cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+            if (e == cudaSuccess) e = launch_render(*A, t, scene->sm_count, s);
+            if (e != cudaSuccess) rc = cuda_fail(e, "render launch");
+        }
+        delete A;
+        return rc;
+    }
+    static_assert(sizeof(WaveArgs) < 32000, "kernel parameter block too large");
+    const uint64_t cap = 1ull << t.chunk_log2;
+    if (wave_workspace_bytes(cap, adjoint) > ws_bytes)
+        return fail(QRT_ERR_INVALID_ARG, "wavefront workspace too small for chunk_log2");
+    WaveArgs* W = new WaveArgs();
+    std::memset(W, 0, sizeof(WaveArgs));
+    W->S = scene->S;
+    W->albedo = d_albedo;
+    W->grad = d_grad;
+    W->stats = stats;
+    W->capacity = cap;
+    W->batch = (uint32_t)t.batch;
+    wave_carve(workspace, cap, adjoint, W->B);
+    rc = make_params(params, W->P);
+    if (adjoint) W->P.path_log = nullptr;
+    // the view table is shared with the single-kernel renderer's layout
+    RenderArgs* R = new RenderArgs();
     uint64_t paths = 0;
     for (uint32_t first = 0; rc == QRT_OK && first < n_views; first += kMaxViewsPerLaunch) {
         const uint32_t cnt = std::min<uint32_t>(kMaxViewsPerLaunch, n_views - first);
-        rc = make_views(views, first, cnt, d_dimage, *A, paths);
+        rc = make_views(views, first, cnt, d_dimage, *R, paths);
         if (rc) break;
-        for (uint32_t k = 0; k < cnt; ++k)
+        for (uint32_t k = 0; k < cnt; ++k) {
+            W->views[k] = R->views[k];
             paths += (uint64_t)views[first + k].w * views[first + k].h * views[first + k].spp;
-        cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
-        if (e == cudaSuccess) e = launch_render(*A, t, scene->sm_count, s);
-        if (e != cudaSuccess) rc = cuda_fail(e, "render launch");
+        }
+        W->n_views = cnt;
+        cudaError_t e = launch_wave(*W, t, scene->sm_count, s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "wavefront launch");
     }
-    delete A;
+    delete R;
+    delete W;
     return rc;
+}
+
+// Scratch for a plain (non-graph) call on stream s.
+int stream_scratch(qrt_scene scene, const qrt_params* params, bool adjoint, cudaStream_t s,
+                   unsigned long long** counter, void** ws, size_t* ws_bytes) {
+    StreamSlot& sl = scene->slot_for(s);
+    *counter = sl.counter;
+    Tune t = resolve_tuning(params ? &params->tuning : nullptr);
+    int rc = validate_tuning(t);
+    if (rc) return rc;
+    if (t.mode == 2) {
+        // one workspace per stream, sized for the adjoint so both fit
+        rc = ensure_workspace(sl, wave_workspace_bytes(1ull << t.chunk_log2, true), s);
+        if (rc) return rc;
+    }
+    (void)adjoint;
+    *ws = sl.ws;
+    *ws_bytes = sl.ws_bytes;
+    return QRT_OK;
 }
 
 int render_args_check(qrt_scene scene, const qrt_view* views, uint32_t n_views, const float* d_albedo) {
@@ -560,8 +655,13 @@ int qrt_render_spp(qrt_scene scene, const qrt_view* views, uint32_t n_views, con
     if (rc) return rc;
     if (n_views == 0) return QRT_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    return render_enqueue(scene, views, n_views, d_albedo, nullptr, nullptr, params,
-                          scene->counter_for(s), nullptr, s);
+    unsigned long long* ctr;
+    void* ws;
+    size_t wsb;
+    rc = stream_scratch(scene, params, false, s, &ctr, &ws, &wsb);
+    if (rc) return rc;
+    return render_enqueue(scene, views, n_views, d_albedo, nullptr, nullptr, params, ctr, ws, wsb,
+                          nullptr, s);
 }
 
 // Same as qrt_render_spp with traversal counters added into d_stats (device
@@ -575,8 +675,13 @@ int qrt_render_spp_stats(qrt_scene scene, const qrt_view* views, uint32_t n_view
     if (!d_stats || !aligned(d_stats, 8)) return fail(QRT_ERR_INVALID_ARG, "d_stats NULL or unaligned");
     if (n_views == 0) return QRT_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    return render_enqueue(scene, views, n_views, d_albedo, nullptr, nullptr, params,
-                          scene->counter_for(s), d_stats, s);
+    unsigned long long* ctr;
+    void* ws;
+    size_t wsb;
+    rc = stream_scratch(scene, params, false, s, &ctr, &ws, &wsb);
+    if (rc) return rc;
+    return render_enqueue(scene, views, n_views, d_albedo, nullptr, nullptr, params, ctr, ws, wsb,
+                          d_stats, s);
 }
 
 int qrt_trace_stats(qrt_scene scene, int any, const qrt_ray* d_rays, uint64_t n, void* d_out,
@@ -591,9 +696,10 @@ int qrt_trace_stats(qrt_scene scene, int any, const qrt_ray* d_rays, uint64_t n,
     if (rc) return rc;
     rc = check_device(scene);
     if (rc) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = launch_trace(any != 0, scene->S, d_rays, n, any ? nullptr : d_out,
-                                 any ? static_cast<uint32_t*>(d_out) : nullptr, 1u << 20, d_stats,
-                                 t, reinterpret_cast<cudaStream_t>(stream));
+                                 any ? static_cast<uint32_t*>(d_out) : nullptr, 1u << 20,
+                                 scene->slot_for(s).counter, d_stats, t, scene->sm_count, s);
     if (e != cudaSuccess) return cuda_fail(e, "trace launch");
     return QRT_OK;
 }
@@ -608,8 +714,13 @@ int qrt_render_adjoint(qrt_scene scene, const qrt_view* views, uint32_t n_views,
     if (!d_grad_albedo || !aligned(d_grad_albedo, 4))
         return fail(QRT_ERR_INVALID_ARG, "d_grad_albedo is NULL or unaligned");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    return render_enqueue(scene, views, n_views, d_albedo, d_dimage, d_grad_albedo, params,
-                          scene->counter_for(s), nullptr, s);
+    unsigned long long* ctr;
+    void* ws;
+    size_t wsb;
+    rc = stream_scratch(scene, params, true, s, &ctr, &ws, &wsb);
+    if (rc) return rc;
+    return render_enqueue(scene, views, n_views, d_albedo, d_dimage, d_grad_albedo, params, ctr, ws,
+                          wsb, nullptr, s);
 }
 
 int qrt_l2_loss(const float* d_img, const float* d_target, uint64_t n, double* d_loss,
@@ -630,12 +741,19 @@ int qrt_render_graph_create(qrt_scene scene, const qrt_view* views, uint32_t n_v
     int rc = render_args_check(scene, views, n_views, d_albedo);
     if (rc) return rc;
     if (n_views == 0) return fail(QRT_ERR_INVALID_ARG, "no views");
+    Tune tg = resolve_tuning(params ? &params->tuning : nullptr);
+    rc = validate_tuning(tg);
+    if (rc) return rc;
     qrt_graph_s* g = new qrt_graph_s();
     g->device = scene->device;
+    const size_t wsb = tg.mode == 2 ? wave_workspace_bytes(1ull << tg.chunk_log2, false) : 0;
     cudaError_t e = cudaMalloc((void**)&g->d_counter, kSlotStride);
+    if (e == cudaSuccess && wsb) e = cudaMalloc(&g->ws, wsb);
     if (e != cudaSuccess) {
+        cudaFree(g->d_counter);
+        cudaFree(g->ws);
         delete g;
-        return cuda_fail(e, "graph counter");
+        return cuda_fail(e, "graph scratch");
     }
     cudaStream_t cs = nullptr;
     e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
@@ -643,11 +761,12 @@ int qrt_render_graph_create(qrt_scene scene, const qrt_view* views, uint32_t n_v
     if (e != cudaSuccess) {
         if (cs) cudaStreamDestroy(cs);
         cudaFree(g->d_counter);
+        cudaFree(g->ws);
         delete g;
         return cuda_fail(e, "graph capture");
     }
     rc = render_enqueue(scene, views, n_views, d_albedo, nullptr, nullptr, params, g->d_counter,
-                        nullptr, cs);
+                        g->ws, wsb, nullptr, cs);
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
     cudaStreamDestroy(cs);
@@ -663,6 +782,7 @@ int qrt_render_graph_create(qrt_scene scene, const qrt_view* views, uint32_t n_v
         if (g->exec) cudaGraphExecDestroy(g->exec);
         if (g->graph) cudaGraphDestroy(g->graph);
         cudaFree(g->d_counter);
+        cudaFree(g->ws);
         delete g;
         return rc;
     }
@@ -682,6 +802,7 @@ int qrt_graph_destroy(qrt_graph graph) {
     if (graph->exec) cudaGraphExecDestroy(graph->exec);
     if (graph->graph) cudaGraphDestroy(graph->graph);
     cudaFree(graph->d_counter);
+    cudaFree(graph->ws);
     delete graph;
     return QRT_OK;
 }

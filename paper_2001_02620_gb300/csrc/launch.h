@@ -15,7 +15,9 @@ struct Tune {
     int batch = 1;          // 32-item groups a warp claims per fetch
     int stack = 64;         // 32 or 64
     int fetch = 16;         // 16 or 32
-    int adjoint_mode = 1;   // 1 = replay, 2 = register record
+    int adjoint_mode = 0;   // reserved
+    int mode = 2;           // 1 = single persistent kernel, 2 = wavefront
+    int chunk_log2 = 21;    // wavefront paths per chunk = 2^chunk_log2
 };
 
 // A view with its camera basis precomputed on the host (FP64 -> FP32).
@@ -57,9 +59,10 @@ struct RenderArgs {
     ViewDev views[kMaxViewsPerLaunch];
 };
 
+// Persistent ray-query launch; cursor is a device counter the launch resets.
 cudaError_t launch_trace(bool any, const DevScene& S, const void* rays, uint64_t n, void* hits,
-                         uint32_t* occ_bits, uint32_t max_steps, unsigned long long* stats,
-                         const Tune& t, cudaStream_t s);
+                         uint32_t* occ_bits, uint32_t max_steps, unsigned long long* cursor,
+                         unsigned long long* stats, const Tune& t, int sm_count, cudaStream_t s);
 
 constexpr int kStatsWords = 6;
 

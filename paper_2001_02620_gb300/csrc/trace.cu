@@ -1,73 +1,115 @@
-// Ray-query kernels behind qrt_trace_closest / qrt_trace_any: one ray per
-// thread, 32 consecutive rays per warp so an any-hit warp writes its 32
-// occlusion bits with a single ballot and store.
+// Ray-query kernels behind qrt_trace_closest / qrt_trace_any.  Persistent:
+// a grid of SMs x resident blocks, each lane claiming `batch` rays at a time
+// from a global cursor and starting its next ray as soon as its own is done,
+// so no lane idles while the rest of its warp finishes slower rays.
 #include "launch.h"
 #include "traverse.cuh"
 
 namespace qrt {
 
 template <bool ANY, int STACK, int FETCH>
-__global__ void __launch_bounds__(256) trace_kernel(const DevScene S, const float4* __restrict__ rays,
-                                                    uint64_t n, uint4* __restrict__ hits,
-                                                    uint32_t* __restrict__ occ, uint32_t max_steps,
-                                                    unsigned long long* stats) {
-    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = i < n;
-    Hit h;
-    h.inst = 0xFFFFFFFFu;
-    uint32_t err = 0;
+__global__ void __launch_bounds__(256, 2) trace_kernel(const DevScene S, const float4* __restrict__ rays,
+                                                       uint64_t n, uint4* __restrict__ hits,
+                                                       uint32_t* __restrict__ occ, uint32_t max_steps,
+                                                       unsigned long long* cursor, uint32_t batch,
+                                                       unsigned long long* stats) {
     TraceStats st{0, 0, 0, 0, 0, 0};
-    if (valid) {
-        const float4 a = __ldg(rays + 2 * i), b = __ldg(rays + 2 * i + 1);
-        err = trace_ray<ANY, STACK, FETCH>(S, a.x, a.y, a.z, b.x, b.y, b.z, a.w, b.w, max_steps, h,
-                                           st);
-        if (!ANY) {
-            const uint32_t uq = (uint32_t)__float2uint_rn(__saturatef(h.u) * 65535.f);
-            const uint32_t vq = (uint32_t)__float2uint_rn(__saturatef(h.v) * 65535.f);
-            const uint32_t uv = h.inst == 0xFFFFFFFFu ? 0u : (uq | (vq << 16));
-            hits[i] = make_uint4(__float_as_uint(h.t), h.inst, h.prim, uv);
+    Traversal<ANY, STACK, FETCH> T;
+    uint64_t next = 0, end = 0, i = 0;
+    uint32_t err = 0;
+    uint64_t bad = ~0ull;
+    bool busy = false;
+    for (;;) {
+        if (!busy) {
+            if (next >= end) {
+                next = atomicAdd(cursor, (unsigned long long)batch);
+                end = min(next + batch, n);
+                if (next >= n) break;
+            }
+            i = next++;
+            const float4 a = __ldg(rays + 2 * i), b = __ldg(rays + 2 * i + 1);
+            T.init(S, a.x, a.y, a.z, b.x, b.y, b.z, a.w, b.w, max_steps, st);
+            busy = true;
         }
-    }
-    if (ANY) {
-        const unsigned bits = __ballot_sync(0xFFFFFFFFu, valid && h.inst != 0xFFFFFFFFu);
-        if ((threadIdx.x & 31) == 0 && (i < n)) occ[i >> 5] = bits;
+        busy = T.step(S, st);
+        if (!busy) {
+            if (T.err) {
+                err |= T.err;
+                bad = min(bad, i);
+            }
+            if (ANY) {
+                if (T.h.inst != 0xFFFFFFFFu) atomicOr(occ + (i >> 5), 1u << (i & 31));
+            } else {
+                const uint32_t uq = (uint32_t)__float2uint_rn(__saturatef(T.h.u) * 65535.f);
+                const uint32_t vq = (uint32_t)__float2uint_rn(__saturatef(T.h.v) * 65535.f);
+                const uint32_t uv = T.h.inst == 0xFFFFFFFFu ? 0u : (uq | (vq << 16));
+                hits[i] = make_uint4(__float_as_uint(T.h.t), T.h.inst, T.h.prim, uv);
+            }
+        }
     }
     if (err) {
         atomicOr(S.err, err);
-        atomicMin(S.err + 1, (uint32_t)min(i, (uint64_t)0xFFFFFFFEu));
+        atomicMin(S.err + 1, (uint32_t)min(bad, (uint64_t)0xFFFFFFFEu));
     }
-    if (stats) add_stats(stats, st);
+    if (stats) {
+        __syncwarp();
+        add_stats(stats, st);
+    }
+}
+
+template <bool ANY, int STACK, int FETCH>
+static int occupancy(int block) {
+    int k = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, trace_kernel<ANY, STACK, FETCH>, block, 0);
+    return k;
+}
+
+template <bool ANY, int STACK, int FETCH>
+static cudaError_t launch_variant(const DevScene& S, const float4* rays, uint64_t n, uint4* hits,
+                                  uint32_t* occ, uint32_t max_steps, unsigned long long* cursor,
+                                  unsigned long long* stats, const Tune& t, int sm_count,
+                                  cudaStream_t s) {
+    int per_sm = t.blocks_per_sm > 0 ? t.blocks_per_sm : occupancy<ANY, STACK, FETCH>(t.block);
+    if (per_sm < 1) per_sm = 1;
+    uint64_t grid = (uint64_t)sm_count * per_sm;
+    const uint64_t want = (n + (uint64_t)t.block - 1) / (uint64_t)t.block;
+    if (want < grid) grid = want;
+    trace_kernel<ANY, STACK, FETCH><<<(unsigned)grid, t.block, 0, s>>>(
+        S, rays, n, hits, occ, max_steps, cursor, (uint32_t)t.batch, stats);
+    return cudaGetLastError();
 }
 
 template <bool ANY>
 static cudaError_t launch_any_variant(const DevScene& S, const void* rays, uint64_t n, void* hits,
-                                      uint32_t* occ, uint32_t max_steps,
-                                      unsigned long long* stats, const Tune& t, cudaStream_t s) {
-    const int block = t.block;
-    const uint64_t grid = (n + block - 1) / block;
-    if (grid > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+                                      uint32_t* occ, uint32_t max_steps, unsigned long long* cursor,
+                                      unsigned long long* stats, const Tune& t, int sm_count,
+                                      cudaStream_t s) {
     const float4* r = static_cast<const float4*>(rays);
     uint4* hp = static_cast<uint4*>(hits);
     if (t.stack <= 32) {
         if (t.fetch == 32)
-            trace_kernel<ANY, 32, 32><<<(unsigned)grid, block, 0, s>>>(S, r, n, hp, occ, max_steps, stats);
-        else
-            trace_kernel<ANY, 32, 16><<<(unsigned)grid, block, 0, s>>>(S, r, n, hp, occ, max_steps, stats);
-    } else {
-        if (t.fetch == 32)
-            trace_kernel<ANY, 64, 32><<<(unsigned)grid, block, 0, s>>>(S, r, n, hp, occ, max_steps, stats);
-        else
-            trace_kernel<ANY, 64, 16><<<(unsigned)grid, block, 0, s>>>(S, r, n, hp, occ, max_steps, stats);
+            return launch_variant<ANY, 32, 32>(S, r, n, hp, occ, max_steps, cursor, stats, t, sm_count, s);
+        return launch_variant<ANY, 32, 16>(S, r, n, hp, occ, max_steps, cursor, stats, t, sm_count, s);
     }
-    return cudaGetLastError();
+    if (t.fetch == 32)
+        return launch_variant<ANY, 64, 32>(S, r, n, hp, occ, max_steps, cursor, stats, t, sm_count, s);
+    return launch_variant<ANY, 64, 16>(S, r, n, hp, occ, max_steps, cursor, stats, t, sm_count, s);
 }
 
 cudaError_t launch_trace(bool any, const DevScene& S, const void* rays, uint64_t n, void* hits,
-                         uint32_t* occ_bits, uint32_t max_steps, unsigned long long* stats,
-                         const Tune& t, cudaStream_t s) {
+                         uint32_t* occ_bits, uint32_t max_steps, unsigned long long* cursor,
+                         unsigned long long* stats, const Tune& t, int sm_count, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    return any ? launch_any_variant<true>(S, rays, n, hits, occ_bits, max_steps, stats, t, s)
-               : launch_any_variant<false>(S, rays, n, hits, occ_bits, max_steps, stats, t, s);
+    cudaError_t e = cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    if (any) {
+        e = cudaMemsetAsync(occ_bits, 0, sizeof(uint32_t) * ((n + 31) / 32), s);
+        if (e != cudaSuccess) return e;
+        return launch_any_variant<true>(S, rays, n, hits, occ_bits, max_steps, cursor, stats, t,
+                                        sm_count, s);
+    }
+    return launch_any_variant<false>(S, rays, n, hits, occ_bits, max_steps, cursor, stats, t,
+                                     sm_count, s);
 }
 
 }  // namespace qrt

@@ -1,22 +1,26 @@
 // Device-side traversal of the two-level quad BVH (qrt_layout.h).
 //
 // Top level: four-wide TLAS over instance world boxes.  At a TLAS leaf the ray
-// is moved into the instance's object space with the FP32 world->object
-// matrix (the direction is not renormalised, so t is shared by both levels)
-// and the object's BLAS is traversed on the same stack; when the stack drains
-// back to the level where the instance was entered, the world ray is
-// restored.  Leaves of a BLAS hold up to 16 quads stored contiguously.
+// is moved into the instance's object space in FP64 (the direction is not
+// renormalised, so t is shared by both levels), re-centred at the point of
+// closest approach to the object's origin, and only then rounded to FP32; the
+// object's BLAS is traversed on the same stack with a parameter s = t - t_e.
+// When the stack drains back to the level where the instance was entered,
+// the world ray is restored.  Leaves of a BLAS hold up to 16 quads stored
+// contiguously.
 //
 // Precision design.  Box tests are made conservative by widening every
 // dequantised box by delta, an absolute bound on the position error of the
-// FP32 ray in the current space (ray transform + slab arithmetic), so a node
-// is never culled that the exact ray enters.  The quad test is the watertight
-// test of Woop, Benthin and Wald (JCGT 2013) applied to both triangles of the
-// quad with the diagonal v0-v2 shared; an edge function whose magnitude is
-// within the same error bound of zero makes the decision uncertain, and only
-// then the quad is re-tested in FP64 from the world ray and the FP64 inverse
-// transform.  Hit/miss decisions therefore agree with exact arithmetic on the
-// given FP32 ray except when a hit lies within FP64 rounding of an edge.
+// FP32 ray in the current space (2^-20 (|o| + R) at the top level, where the
+// world ray is exact; 2^-21 (|o''| + R) in object space, where o'' is the
+// re-centred origin and R the object's radius), so a node is never culled
+// that the exact ray enters.  The quad test is the watertight test of Woop,
+// Benthin and Wald (JCGT 2013) applied to both triangles of the quad with the
+// diagonal v0-v2 shared; an edge function within the same error bound of zero
+// makes the decision uncertain, and only then the quad is re-tested in FP64
+// from the world ray and the FP64 transform.  Hit/miss decisions therefore
+// agree with exact arithmetic on the given FP32 ray except when a hit lies
+// within FP64 rounding of an edge.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -216,17 +220,22 @@ __device__ __forceinline__ int classify(float e0, float e1, float e2, float B) {
     return 2;
 }
 
-// Exact-enough re-test in FP64: object ray from the world ray and the FP64
-// world->object matrix, then the watertight test with FP64 arithmetic.
-// Returns 1 on a hit with t > tmin (t written, with quad-space u, v).
-static __device__ __noinline__ int quad_test64(const double* w2o, float wox, float woy, float woz,
-                                        float wdx, float wdy, float wdz, const float* v,
-                                        float tmin, double* t_out, float* u_out, float* v_out) {
+// Exact-enough re-test in FP64: object ray from the world ray and the
+// instance's FP64 world->object matrix, then the watertight test with FP64
+// arithmetic.  Returns 1 on a hit with t > tmin (world t written, with
+// quad-space u, v).
+static __device__ __noinline__ int quad_test64(const InstDev* ip, float wox, float woy, float woz,
+                                               float wdx, float wdy, float wdz, const float* v,
+                                               float tmin, double* t_out, float* u_out,
+                                               float* v_out) {
     double o[3], d[3];
-    const double wo[3] = {wox, woy, woz}, wd[3] = {wdx, wdy, wdz};
+    const double e[3] = {(double)wox - (double)ip->c[0], (double)woy - (double)ip->c[1],
+                         (double)woz - (double)ip->c[2]};
+    const double wd[3] = {wdx, wdy, wdz};
+    const double* w = ip->w;
     for (int r = 0; r < 3; ++r) {
-        o[r] = w2o[4 * r] * wo[0] + w2o[4 * r + 1] * wo[1] + w2o[4 * r + 2] * wo[2] + w2o[4 * r + 3];
-        d[r] = w2o[4 * r] * wd[0] + w2o[4 * r + 1] * wd[1] + w2o[4 * r + 2] * wd[2];
+        o[r] = w[3 * r] * e[0] + w[3 * r + 1] * e[1] + w[3 * r + 2] * e[2];
+        d[r] = w[3 * r] * wd[0] + w[3 * r + 1] * wd[1] + w[3 * r + 2] * wd[2];
     }
     int kz = (fabs(d[0]) > fabs(d[1])) ? ((fabs(d[0]) > fabs(d[2])) ? 0 : 2)
                                        : ((fabs(d[1]) > fabs(d[2])) ? 1 : 2);
@@ -286,10 +295,14 @@ static __device__ __noinline__ int quad_test64(const double* w2o, float wox, flo
 
 // FP32 test of one quad; returns 1 on a hit with tmin < t (t, u, v written);
 // may defer to quad_test64.
-__device__ __forceinline__ int quad_test(const RaySetup& r, const QuadDev* q, const double* w2o64,
+// FP32 test of one quad in the object-space parameter s (s > smin); an
+// uncertain quad is re-tested by quad_test64, which returns the world t, and
+// is reported with *exact64 = 1.  Returns 1 on a hit.
+__device__ __forceinline__ int quad_test(const RaySetup& r, const QuadDev* q, const InstDev* ip,
                                          float wox, float woy, float woz, float wdx, float wdy,
-                                         float wdz, float tmin, float* t_out, float* u_out,
-                                         float* v_out, uint32_t* n_fallback) {
+                                         float wdz, float smin, float tmin, float* t_out,
+                                         float* u_out, float* v_out, int* exact64,
+                                         uint32_t* n_fallback) {
     const float4* p = reinterpret_cast<const float4*>(q);
     const float4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
     const SV s0 = shear(r, a.x, a.y, a.z);
@@ -310,18 +323,21 @@ __device__ __forceinline__ int quad_test(const RaySetup& r, const QuadDev* q, co
         ++*n_fallback;
         double t64;
         float vv[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
-        if (!quad_test64(w2o64, wox, woy, woz, wdx, wdy, wdz, vv, tmin, &t64, u_out, v_out))
+        if (!quad_test64(ip, wox, woy, woz, wdx, wdy, wdz, vv, tmin, &t64, u_out, v_out))
             return 0;
         *t_out = (float)t64;
+        *exact64 = 1;
         return 1;
     }
+    *exact64 = 0;
+    const float tmin_ = smin;  // the FP32 path works in s
     float best = kInfF;
     int hit = 0;
     if (c0 == 1) {
         const float det = e21 + e02 + e10;
         const float T = __fmaf_rn(e21, s0.Z, __fmaf_rn(e02, s1.Z, __fmul_rn(e10, s2.Z)));
         const float tt = __fdiv_rn(T, det);
-        if (tt > tmin) {
+        if (tt > tmin_) {
             best = tt;
             hit = 1;
             *u_out = __fdiv_rn(e02 + e10, det);
@@ -332,7 +348,7 @@ __device__ __forceinline__ int quad_test(const RaySetup& r, const QuadDev* q, co
         const float det = e32 + e03 - e02;
         const float T = __fmaf_rn(e32, s0.Z, __fmaf_rn(e03, s2.Z, __fmul_rn(-e02, s3.Z)));
         const float tt = __fdiv_rn(T, det);
-        if (tt > tmin && tt < best) {
+        if (tt > tmin_ && tt < best) {
             best = tt;
             hit = 1;
             *u_out = __fdiv_rn(e03, det);
@@ -368,128 +384,93 @@ __device__ __forceinline__ void add_stats(unsigned long long* stats, const Trace
     }
 }
 
-// Closest hit (ANY = false) or any hit (ANY = true) of the world ray.
-// Returns device error bits (0 = fine).  For closest hit, h holds the best
-// hit found (inst = 0xFFFFFFFF if none).
+// Resumable two-level traversal of one world ray.  init() sets the ray up;
+// each step() processes the current node, leaf or instance entry and pops the
+// next stack entry, returning false once the ray is finished (or stopped by
+// an error).  Persistent kernels interleave step() with refilling finished
+// lanes, so no lane waits for the slowest ray of its warp.
 template <bool ANY, int STACK, int FETCH>
-__device__ __forceinline__ uint32_t trace_ray(const DevScene& S, float wox, float woy, float woz,
-                                              float wdx, float wdy, float wdz, float tmin,
-                                              float tmax, uint32_t max_steps, Hit& h,
-                                              TraceStats& st) {
-    h.t = tmax;
-    h.inst = 0xFFFFFFFFu;
-    h.prim = 0xFFFFFFFFu;
-    h.u = h.v = 0.f;
-    h.slot = 0;
-    ++st.rays;
-    if (S.n_inst == 0) return 0;
-    uint64_t stack[STACK];
-    int sp = 0;
-    int inst_sp = -1;
-    bool top = true;
-    uint32_t node_base = S.tlas_base;
-    uint32_t quad_base = 0;
-    uint32_t cur_inst = 0;
-    const double* w2o64 = nullptr;
+struct Traversal {
+    float wox, woy, woz, wdx, wdy, wdz, tmin, tmax;
+    float delta_top;
+    float te;  // object-space parameter offset: t = s + te
     RaySetup r;
-    const float delta_top = 9.5367431640625e-07f * (maxabs3(wox, woy, woz) + S.R_top);  // 2^-20
-    setup_boxes(r, wox, woy, woz, wdx, wdy, wdz, delta_top);
-    uint32_t cur = 0;  // TLAS root, an inner reference
-    bool have = true;
-    uint32_t steps = 0;
-    uint32_t err = 0;
-    for (;;) {
+    uint64_t stack[STACK];
+    int sp, inst_sp;
+    bool top, have;
+    uint32_t node_base, quad_base, cur_inst, cur, steps, max_steps, err;
+    Hit h;
+
+    __device__ __forceinline__ void init(const DevScene& S, float ox, float oy, float oz, float dx,
+                                         float dy, float dz, float t0, float t1, uint32_t msteps,
+                                         TraceStats& st) {
+        wox = ox;
+        woy = oy;
+        woz = oz;
+        wdx = dx;
+        wdy = dy;
+        wdz = dz;
+        tmin = t0;
+        tmax = t1;
+        h.t = t1;
+        h.inst = 0xFFFFFFFFu;
+        h.prim = 0xFFFFFFFFu;
+        h.u = h.v = 0.f;
+        h.slot = 0;
+        ++st.rays;
+        sp = 0;
+        inst_sp = -1;
+        top = true;
+        node_base = S.tlas_base;
+        quad_base = 0;
+        cur_inst = 0;
+        te = 0.f;
+        cur = 0;  // TLAS root, an inner reference
+        have = S.n_inst > 0;
+        steps = 0;
+        max_steps = msteps;
+        err = 0;
+        delta_top = 9.5367431640625e-07f * (maxabs3(ox, oy, oz) + S.R_top);  // 2^-20
+        setup_boxes(r, ox, oy, oz, dx, dy, dz, delta_top);
+    }
+
+    // far end of the interval in the current space (object space: s units,
+    // widened by the rounding of h.t - te)
+    __device__ __forceinline__ float limit() const {
+        return top ? h.t
+                   : __fadd_rn(__fsub_rn(h.t, te), 1.9073486328125e-06f * (fabsf(h.t) + fabsf(te)));
+    }
+
+    __device__ __forceinline__ bool step(const DevScene& S, TraceStats& st) {
         if (have) {
             if (!(cur & kRefLeaf)) {
                 if (++steps > max_steps) {
                     err |= kErrStepLimit;
-                    break;
+                    return false;
                 }
                 ++st.nodes;
                 float t[4];
                 uint32_t ref[4];
-                const int nh = node_children<FETCH>(S.nodes + node_base + cur, r, tmin, h.t, t, ref);
+                const float lo = top ? tmin : __fsub_rn(tmin, te);
+                const int nh = node_children<FETCH>(S.nodes + node_base + cur, r, lo, limit(), t, ref);
                 if (nh == 0) {
                     have = false;
                 } else {
                     if (sp + nh - 1 > STACK) {
                         err |= kErrStackOverflow;
-                        break;
+                        return false;
                     }
 #pragma unroll
                     for (int k = 3; k >= 1; --k)
-                        if (k < nh)
-                            stack[sp++] = ((uint64_t)__float_as_uint(t[k]) << 32) | ref[k];
+                        if (k < nh) stack[sp++] = ((uint64_t)__float_as_uint(t[k]) << 32) | ref[k];
                     cur = ref[0];
+                    return true;
                 }
-                continue;
-            }
-            if (top) {
-                // enter instance cur_inst
-                cur_inst = cur & kRefIndexMask;
-                const InstDev* ip = S.inst + cur_inst;
-                const float4* q4 = reinterpret_cast<const float4*>(ip);
-                const float4 m0 = __ldg(q4), m1 = __ldg(q4 + 1), m2 = __ldg(q4 + 2);
-                const uint4 m3 = __ldg(reinterpret_cast<const uint4*>(ip) + 3);
-                const float ox = __fmaf_rn(m0.x, wox, __fmaf_rn(m0.y, woy, __fmaf_rn(m0.z, woz, m0.w)));
-                const float oy = __fmaf_rn(m1.x, wox, __fmaf_rn(m1.y, woy, __fmaf_rn(m1.z, woz, m1.w)));
-                const float oz = __fmaf_rn(m2.x, wox, __fmaf_rn(m2.y, woy, __fmaf_rn(m2.z, woz, m2.w)));
-                const float dx = __fmaf_rn(m0.x, wdx, __fmaf_rn(m0.y, wdy, __fmul_rn(m0.z, wdz)));
-                const float dy = __fmaf_rn(m1.x, wdx, __fmaf_rn(m1.y, wdy, __fmul_rn(m1.z, wdz)));
-                const float dz = __fmaf_rn(m2.x, wdx, __fmaf_rn(m2.y, wdy, __fmul_rn(m2.z, wdz)));
-                node_base = m3.x;
-                quad_base = m3.y;
-                const float R = __uint_as_float(m3.z);
-                const float delta = 3.814697265625e-06f * (maxabs3(ox, oy, oz) + R);  // 2^-18
-                setup_boxes(r, ox, oy, oz, dx, dy, dz, delta);
-                setup_shear(r, dx, dy, dz);
-                w2o64 = S.inst64 + 12 * (size_t)cur_inst;
-                inst_sp = sp;
-                top = false;
-                ++st.insts;
-                cur = 0;
-                continue;
-            }
-            // BLAS leaf: test its quads
-            {
-                const uint32_t first = cur & kRefIndexMask;
-                const uint32_t cnt = ((cur >> 27) & 0xFu) + 1u;
-                bool done = false;
-                for (uint32_t k = 0; k < cnt; ++k) {
-                    const uint32_t slot = quad_base + first + k;
-                    float tt, uu, vv;
-                    ++st.quads;
-                    if (!quad_test(r, S.quads + slot, w2o64, wox, woy, woz, wdx, wdy, wdz, tmin,
-                                   &tt, &uu, &vv, &st.fallbacks))
-                        continue;
-                    if (!(tt < tmax)) continue;
-                    if (ANY) {
-                        h.t = tt;
-                        h.inst = cur_inst;
-                        h.prim = __ldg(S.prim + slot);
-                        h.slot = slot;
-                        done = true;
-                        break;
-                    }
-                    if (tt < h.t) {
-                        h.t = tt;
-                        h.inst = cur_inst;
-                        h.prim = __ldg(S.prim + slot);
-                        h.u = uu;
-                        h.v = vv;
-                        h.slot = slot;
-                    } else if (tt == h.t) {
-                        const uint32_t pr = __ldg(S.prim + slot);
-                        if (cur_inst < h.inst || (cur_inst == h.inst && pr < h.prim)) {
-                            h.inst = cur_inst;
-                            h.prim = pr;
-                            h.u = uu;
-                            h.v = vv;
-                            h.slot = slot;
-                        }
-                    }
-                }
-                if (done) break;
+            } else if (top) {
+                enter_instance(S, st);
+                return true;
+            } else {
+                if (leaf(S, st)) return false;  // any hit found
                 have = false;
             }
         }
@@ -497,15 +478,118 @@ __device__ __forceinline__ uint32_t trace_ray(const DevScene& S, float wox, floa
         if (!top && sp == inst_sp) {
             top = true;
             node_base = S.tlas_base;
+            te = 0.f;
             setup_boxes(r, wox, woy, woz, wdx, wdy, wdz, delta_top);
         }
-        if (sp == 0) break;
+        if (sp == 0) return false;
         const uint64_t e = stack[--sp];
-        if (__uint_as_float((uint32_t)(e >> 32)) > h.t) continue;
-        cur = (uint32_t)e;
-        have = true;
+        if (__uint_as_float((uint32_t)(e >> 32)) <= limit()) {
+            cur = (uint32_t)e;
+            have = true;
+        }
+        return true;
     }
-    return err;
+
+    // FP64 world->object move of the ray, re-centred at the closest approach
+    // to the object origin, then rounded to FP32.
+    __device__ __forceinline__ void enter_instance(const DevScene& S, TraceStats& st) {
+        cur_inst = cur & kRefIndexMask;
+        const InstDev* ip = S.inst + cur_inst;
+        const float4 m0 = __ldg(reinterpret_cast<const float4*>(ip));
+        const uint4 m1 = __ldg(reinterpret_cast<const uint4*>(ip) + 1);
+        const double2* wp = reinterpret_cast<const double2*>(ip) + 2;
+        const double2 w01 = __ldg(wp), w23 = __ldg(wp + 1), w45 = __ldg(wp + 2), w67 = __ldg(wp + 3);
+        const double w8 = __ldg(reinterpret_cast<const double*>(ip) + 12);
+        const double ex = (double)wox - (double)m0.x, ey = (double)woy - (double)m0.y,
+                     ez = (double)woz - (double)m0.z;
+        const double ox = fma(w01.x, ex, fma(w01.y, ey, w23.x * ez));
+        const double oy = fma(w23.y, ex, fma(w45.x, ey, w45.y * ez));
+        const double oz = fma(w67.x, ex, fma(w67.y, ey, w8 * ez));
+        const double dx = fma(w01.x, (double)wdx, fma(w01.y, (double)wdy, w23.x * (double)wdz));
+        const double dy = fma(w23.y, (double)wdx, fma(w45.x, (double)wdy, w45.y * (double)wdz));
+        const double dz = fma(w67.x, (double)wdx, fma(w67.y, (double)wdy, w8 * (double)wdz));
+        const float fdx = (float)dx, fdy = (float)dy, fdz = (float)dz;
+        // closest approach to the object origin (any offset is valid: it only
+        // moves where the FP32 origin sits along the ray)
+        const float fox = (float)ox, foy = (float)oy, foz = (float)oz;
+        const float dd = __fmaf_rn(fdx, fdx, __fmaf_rn(fdy, fdy, __fmul_rn(fdz, fdz)));
+        const float od = __fmaf_rn(fox, fdx, __fmaf_rn(foy, fdy, __fmul_rn(foz, fdz)));
+        te = fmaxf(tmin, __fdiv_rn(-od, dd));
+        if (!(te < h.t)) te = tmin;  // also catches a non-finite quotient
+        const double tte = (double)te;
+        const float rox = (float)fma(tte, dx, ox), roy = (float)fma(tte, dy, oy),
+                    roz = (float)fma(tte, dz, oz);
+        node_base = m1.x;
+        quad_base = m1.y;
+        const float delta = 4.76837158203125e-07f * (maxabs3(rox, roy, roz) + m0.w);  // 2^-21
+        setup_boxes(r, rox, roy, roz, fdx, fdy, fdz, delta);
+        setup_shear(r, fdx, fdy, fdz);
+        inst_sp = sp;
+        top = false;
+        ++st.insts;
+        cur = 0;
+    }
+
+    // Tests the quads of the current BLAS leaf; returns true when an any-hit
+    // query is answered.
+    __device__ __forceinline__ bool leaf(const DevScene& S, TraceStats& st) {
+        const uint32_t first = cur & kRefIndexMask;
+        const uint32_t cnt = ((cur >> 27) & 0xFu) + 1u;
+        const float smin = __fsub_rn(tmin, te);
+        const InstDev* ip = S.inst + cur_inst;
+        for (uint32_t k = 0; k < cnt; ++k) {
+            const uint32_t slot = quad_base + first + k;
+            float tt, uu, vv;
+            int ex64;
+            ++st.quads;
+            if (!quad_test(r, S.quads + slot, ip, wox, woy, woz, wdx, wdy, wdz, smin, tmin, &tt, &uu,
+                           &vv, &ex64, &st.fallbacks))
+                continue;
+            if (!ex64) tt = __fadd_rn(tt, te);
+            if (!(tt > tmin && tt < tmax)) continue;
+            if (ANY) {
+                h.t = tt;
+                h.inst = cur_inst;
+                h.prim = __ldg(S.prim + slot);
+                h.slot = slot;
+                return true;
+            }
+            if (tt < h.t) {
+                h.t = tt;
+                h.inst = cur_inst;
+                h.prim = __ldg(S.prim + slot);
+                h.u = uu;
+                h.v = vv;
+                h.slot = slot;
+            } else if (tt == h.t) {
+                const uint32_t pr = __ldg(S.prim + slot);
+                if (cur_inst < h.inst || (cur_inst == h.inst && pr < h.prim)) {
+                    h.inst = cur_inst;
+                    h.prim = pr;
+                    h.u = uu;
+                    h.v = vv;
+                    h.slot = slot;
+                }
+            }
+        }
+        return false;
+    }
+};
+
+// Closest hit (ANY = false) or any hit (ANY = true) of the world ray, run to
+// completion.  Returns device error bits (0 = fine); h holds the best hit
+// found (inst = 0xFFFFFFFF if none).
+template <bool ANY, int STACK, int FETCH>
+__device__ __forceinline__ uint32_t trace_ray(const DevScene& S, float wox, float woy, float woz,
+                                              float wdx, float wdy, float wdz, float tmin,
+                                              float tmax, uint32_t max_steps, Hit& h,
+                                              TraceStats& st) {
+    Traversal<ANY, STACK, FETCH> T;
+    T.init(S, wox, woy, woz, wdx, wdy, wdz, tmin, tmax, max_steps, st);
+    while (T.step(S, st)) {
+    }
+    h = T.h;
+    return T.err;
 }
 
 }  // namespace qrt

@@ -1,0 +1,382 @@
+// Wavefront path tracer: the same paths as the single-kernel renderer in
+// render.cu, split into stages so the ray-tracing kernels stay lean and every
+// lane stays busy.
+//
+// Per chunk of at most C paths (chunk boundaries fall on pixel boundaries):
+//   gen        camera ray of every path; closest-ray queue of depth 1
+//   for depth i = 1..D:
+//     trace    persistent closest-hit kernel over queue i; each lane takes the
+//              next ray as soon as its own is finished
+//     shade    misses add beta*env; hits fetch albedo and normal, queue a
+//              shadow ray toward the sun (pending term beta*a/pi*E*cos),
+//              multiply beta by a and queue the bounce ray for depth i+1
+//     shadow   persistent any-hit kernel over the shadow queue; an
+//              unoccluded ray adds its pending term to the path
+//   accumulate mean over each pixel's samples, summed in sample order
+// The adjoint runs the chunk twice: a primal pass that leaves each path's
+// radiance in Ltot, then a replay pass whose shade stage adds
+// w * (Ltot - sun terms before vertex i) / a_i into the albedo gradient.
+// Radiance is accumulated in the same order as render.cu, so the two
+// renderers give bit-identical images.
+#include <algorithm>
+
+#include "launch.h"
+#include "shading.cuh"
+#include "traverse.cuh"
+#include "wavefront.h"
+
+namespace qrt {
+
+__device__ __forceinline__ int find_view_by_path(const WaveArgs& A, uint64_t g) {
+    int lo = 0, hi = (int)A.n_views - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (A.views[mid].path_begin <= g)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int find_view_by_item(const WaveArgs& A, uint64_t item) {
+    int lo = 0, hi = (int)A.n_views - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (A.views[mid].item_begin <= item)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Appends j to a queue; lanes of a warp share one atomic.
+__device__ __forceinline__ void push(uint32_t* queue, uint32_t* count, uint32_t j) {
+    const unsigned m = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(m));
+    base = __shfl_sync(m, base, leader);
+    queue[base + __popc(m & ((1u << lane) - 1u))] = j;
+}
+
+__global__ void __launch_bounds__(256) wave_gen(const __grid_constant__ WaveArgs A, uint64_t P0,
+                                                uint32_t n) {
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j == 0) A.B.ctr[kCtrStride * 1 + kCtrClosest] = n;  // queue of depth 1 holds every path
+    if (j >= n) return;
+    const uint64_t g = P0 + j;
+    const ViewDev& V = A.views[find_view_by_path(A, g)];
+    const uint64_t local = g - V.path_begin;
+    const uint64_t pix = local / V.spp;
+    const uint32_t smp = (uint32_t)(local - pix * V.spp);
+    const uint32_t x = (uint32_t)(pix % V.w), y = (uint32_t)(pix / V.w);
+    const uint4 xi = draw(A.P.seed, V.pixel_base + pix, smp, 0);
+    const F3 d = camera_dir(V, x, y, u01(xi.x), u01(xi.y));
+    A.B.ray_o[j] = make_float4(V.eye[0], V.eye[1], V.eye[2], 0.f);
+    A.B.ray_d[j] = make_float4(d.x, d.y, d.z, kInfF);
+    A.B.beta[j] = make_float4(1.f, 1.f, 1.f, 0.f);
+    A.B.L[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    A.B.meta[j] = make_uint2((uint32_t)(V.item_begin + pix), smp);
+    A.B.q[1][j] = j;  // depth 1 uses queue 1 & 1
+    if (A.P.path_log) {
+        uint32_t* log = A.P.path_log + g * (2ull * A.P.max_depth + 1);
+        for (uint32_t k = 0; k < 2 * A.P.max_depth + 1; ++k) log[k] = k == 2 * A.P.max_depth ? 0u : 0xFFFFFFFFu;
+    }
+}
+
+// Persistent trace over a queue.  ANY = false: closest hit of ray_o/ray_d of
+// each queued path into hit[].  ANY = true: shadow ray from sray_o toward the
+// sun; an unoccluded ray adds pend[] into L[].
+template <bool ANY, int STACK, int FETCH>
+__global__ void __launch_bounds__(256, 2) wave_trace(const __grid_constant__ WaveArgs A, int depth) {
+    const uint32_t* ctr = A.B.ctr + kCtrStride * depth;
+    const uint32_t count = ANY ? ctr[kCtrShadow] : ctr[kCtrClosest];
+    uint32_t* fetch = A.B.ctr + kCtrStride * depth + (ANY ? kCtrFetchShadow : kCtrFetchClosest);
+    const uint32_t* queue = ANY ? A.B.qs : A.B.q[depth & 1];
+    const uint32_t batch = A.batch;
+    TraceStats st{0, 0, 0, 0, 0, 0};
+    Traversal<ANY, STACK, FETCH> T;
+    uint32_t next = 0, end = 0, j = 0;
+    uint32_t err = 0;
+    bool busy = false;
+    for (;;) {
+        if (!busy) {
+            if (next >= end) {
+                next = atomicAdd(fetch, batch);
+                end = min(next + batch, count);
+                if (next >= count) break;
+            }
+            j = queue[next++];
+            if (ANY) {
+                const float4 o = A.B.sray_o[j];
+                T.init(A.S, o.x, o.y, o.z, A.P.sun_l[0], A.P.sun_l[1], A.P.sun_l[2], 0.f, kInfF,
+                       A.P.max_steps, st);
+            } else {
+                const float4 o = A.B.ray_o[j], d = A.B.ray_d[j];
+                T.init(A.S, o.x, o.y, o.z, d.x, d.y, d.z, o.w, d.w, A.P.max_steps, st);
+            }
+            busy = true;
+        }
+        busy = T.step(A.S, st);
+        if (!busy) {
+            err |= T.err;
+            if (ANY) {
+                if (T.h.inst == 0xFFFFFFFFu) {
+                    const float4 p = A.B.pend[j];
+                    float4 l = A.B.L[j];
+                    l.x = __fadd_rn(l.x, p.x);
+                    l.y = __fadd_rn(l.y, p.y);
+                    l.z = __fadd_rn(l.z, p.z);
+                    A.B.L[j] = l;
+                } else if (A.P.path_log && depth <= 16) {
+                    const uint64_t g = A.P0 + j;
+                    A.P.path_log[g * (2ull * A.P.max_depth + 1) + 2 * A.P.max_depth] |=
+                        2u << (2 * (depth - 1));
+                }
+            } else {
+                A.B.hit[j] = make_uint4(__float_as_uint(T.h.t), T.h.inst, T.h.prim, T.h.slot);
+            }
+        }
+    }
+    if (err) atomicOr(A.S.err, err);
+    if (A.stats) {
+        // lanes leave the loop at different times; reconverge before the warp reduction
+        __syncwarp();
+        add_stats(A.stats, st);
+    }
+}
+
+// Shade stage of depth i (1-based).  replay = false: primal; true: replay
+// pass of the adjoint (gradient into A.grad, no env term, L holds the sun
+// terms gathered so far).
+__global__ void __launch_bounds__(256) wave_shade(const __grid_constant__ WaveArgs A, int depth,
+                                                  int replay) {
+    const uint32_t* ctr = A.B.ctr + kCtrStride * depth;
+    const uint32_t n = ctr[kCtrClosest];
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const uint32_t j = A.B.q[depth & 1][k];
+    const uint4 hb = A.B.hit[j];
+    const float t = __uint_as_float(hb.x);
+    const uint32_t inst = hb.y, prim = hb.z, slot = hb.w;
+    const uint32_t D = A.P.max_depth;
+    const uint64_t g = A.P0 + j;
+    uint32_t* log = A.P.path_log ? A.P.path_log + g * (2ull * D + 1) : nullptr;
+    if (log) {
+        log[2 * (depth - 1)] = inst;
+        log[2 * (depth - 1) + 1] = prim;
+    }
+    float4 b = A.B.beta[j];
+    if (inst == 0xFFFFFFFFu) {
+        if (!replay) {
+            float4 l = A.B.L[j];
+            l.x = __fmaf_rn(b.x, A.P.env[0], l.x);
+            l.y = __fmaf_rn(b.y, A.P.env[1], l.y);
+            l.z = __fmaf_rn(b.z, A.P.env[2], l.z);
+            A.B.L[j] = l;
+        }
+        return;
+    }
+    const float4 o4 = A.B.ray_o[j], d4 = A.B.ray_d[j];
+    const F3 o = f3(o4.x, o4.y, o4.z), d = f3(d4.x, d4.y, d4.z);
+    uint32_t qbase;
+    const F3 nrm = hit_normal(A.S, inst, slot, d, &qbase);
+    const uint32_t row = qbase + prim;
+    const float a0 = __ldg(A.albedo + 3 * (size_t)row);
+    const float a1 = __ldg(A.albedo + 3 * (size_t)row + 1);
+    const float a2 = __ldg(A.albedo + 3 * (size_t)row + 2);
+    const F3 sp = spawn_point(o, d, t, nrm);
+    if (replay) {
+        // d L / d a_i = (radiance leaving vertex i) / a_i, per channel
+        const uint2 mt = A.B.meta[j];
+        const ViewDev& V = A.views[find_view_by_item(A, mt.x)];
+        const float* di = V.dimage + 3 * (mt.x - V.item_begin);
+        const float inv_spp = __frcp_rn((float)V.spp);
+        const float w0 = __fmul_rn(__ldg(di), inv_spp), w1 = __fmul_rn(__ldg(di + 1), inv_spp),
+                    w2 = __fmul_rn(__ldg(di + 2), inv_spp);
+        const float4 lt = A.B.Ltot[j], s = A.B.L[j];
+        const float g0 = a0 != 0.f ? __fdiv_rn(__fmul_rn(w0, __fsub_rn(lt.x, s.x)), a0) : 0.f;
+        const float g1 = a1 != 0.f ? __fdiv_rn(__fmul_rn(w1, __fsub_rn(lt.y, s.y)), a1) : 0.f;
+        const float g2 = a2 != 0.f ? __fdiv_rn(__fmul_rn(w2, __fsub_rn(lt.z, s.z)), a2) : 0.f;
+        if (g0 != 0.f || g1 != 0.f || g2 != 0.f) grad_add(A.grad, row, g0, g1, g2);
+    }
+    if (A.P.sun_on) {
+        const float cl = dot3(nrm, f3(A.P.sun_l[0], A.P.sun_l[1], A.P.sun_l[2]));
+        if (cl > 0.f) {
+            if (log && depth <= 16) log[2 * D] |= 1u << (2 * (depth - 1));
+            const float kk = __fmul_rn(cl, 0.318309886183790671538f);  // cos / pi
+            A.B.pend[j] = make_float4(__fmul_rn(__fmul_rn(b.x, a0), __fmul_rn(A.P.sun_E[0], kk)),
+                                      __fmul_rn(__fmul_rn(b.y, a1), __fmul_rn(A.P.sun_E[1], kk)),
+                                      __fmul_rn(__fmul_rn(b.z, a2), __fmul_rn(A.P.sun_E[2], kk)), 0.f);
+            A.B.sray_o[j] = make_float4(sp.x, sp.y, sp.z, 0.f);
+            push(A.B.qs, A.B.ctr + kCtrStride * depth + kCtrShadow, j);
+        }
+    }
+    b.x = __fmul_rn(b.x, a0);
+    b.y = __fmul_rn(b.y, a1);
+    b.z = __fmul_rn(b.z, a2);
+    A.B.beta[j] = b;
+    if ((uint32_t)depth < D) {
+        const uint2 mt = A.B.meta[j];
+        const ViewDev& V = A.views[find_view_by_item(A, mt.x)];
+        const uint4 xi = draw(A.P.seed, V.pixel_base + (mt.x - V.item_begin), mt.y, (uint32_t)depth);
+        const F3 nd = sample_cosine(nrm, u01(xi.x), u01(xi.y));
+        A.B.ray_o[j] = make_float4(sp.x, sp.y, sp.z, 0.f);
+        A.B.ray_d[j] = make_float4(nd.x, nd.y, nd.z, kInfF);
+        push(A.B.q[(depth + 1) & 1], A.B.ctr + kCtrStride * (depth + 1) + kCtrClosest, j);
+    }
+    if (A.stats) atomicAdd(A.stats + 5, 1ull);
+}
+
+// Mean over each pixel's samples (in sample order) for items [I0, I0 + n).
+__global__ void __launch_bounds__(256) wave_accumulate(const __grid_constant__ WaveArgs A,
+                                                       uint64_t I0, uint32_t n) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const uint64_t item = I0 + k;
+    const ViewDev& V = A.views[find_view_by_item(A, item)];
+    const uint64_t pix = item - V.item_begin;
+    const uint64_t j0 = V.path_begin + pix * V.spp - A.P0;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    for (uint32_t s = 0; s < V.spp; ++s) {
+        const float4 l = A.B.L[j0 + s];
+        s0 = __fadd_rn(s0, l.x);
+        s1 = __fadd_rn(s1, l.y);
+        s2 = __fadd_rn(s2, l.z);
+    }
+    float* out = V.out + 3 * pix;
+    out[0] = __fdiv_rn(s0, (float)V.spp);
+    out[1] = __fdiv_rn(s1, (float)V.spp);
+    out[2] = __fdiv_rn(s2, (float)V.spp);
+}
+
+template <bool ANY, int STACK, int FETCH>
+static int trace_occupancy(int block) {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, wave_trace<ANY, STACK, FETCH>, block, 0);
+    return n;
+}
+
+template <bool ANY>
+static cudaError_t launch_wave_trace(const WaveArgs& A, int depth, const Tune& t, int sm_count,
+                                     cudaStream_t s) {
+    const bool s32 = t.stack <= 32, f32 = t.fetch == 32;
+    int per_sm = t.blocks_per_sm;
+    if (per_sm <= 0) {
+        per_sm = s32 ? (f32 ? trace_occupancy<ANY, 32, 32>(t.block) : trace_occupancy<ANY, 32, 16>(t.block))
+                     : (f32 ? trace_occupancy<ANY, 64, 32>(t.block) : trace_occupancy<ANY, 64, 16>(t.block));
+        if (per_sm < 1) per_sm = 1;
+    }
+    const dim3 g((unsigned)(sm_count * per_sm)), b((unsigned)t.block);
+    if (s32) {
+        if (f32) wave_trace<ANY, 32, 32><<<g, b, 0, s>>>(A, depth);
+        else wave_trace<ANY, 32, 16><<<g, b, 0, s>>>(A, depth);
+    } else {
+        if (f32) wave_trace<ANY, 64, 32><<<g, b, 0, s>>>(A, depth);
+        else wave_trace<ANY, 64, 16><<<g, b, 0, s>>>(A, depth);
+    }
+    return cudaGetLastError();
+}
+
+void wave_carve(void* base, uint64_t C, bool adjoint, WaveBufs& B) {
+    char* p = static_cast<char*>(base);
+    auto take = [&](size_t bytes) {
+        char* r = p;
+        p += (bytes + 255) & ~size_t(255);
+        return r;
+    };
+    B.ray_o = reinterpret_cast<float4*>(take(16 * C));
+    B.ray_d = reinterpret_cast<float4*>(take(16 * C));
+    B.beta = reinterpret_cast<float4*>(take(16 * C));
+    B.L = reinterpret_cast<float4*>(take(16 * C));
+    B.pend = reinterpret_cast<float4*>(take(16 * C));
+    B.sray_o = reinterpret_cast<float4*>(take(16 * C));
+    B.hit = reinterpret_cast<uint4*>(take(16 * C));
+    B.meta = reinterpret_cast<uint2*>(take(8 * C));
+    B.q[0] = reinterpret_cast<uint32_t*>(take(4 * C));
+    B.q[1] = reinterpret_cast<uint32_t*>(take(4 * C));
+    B.qs = reinterpret_cast<uint32_t*>(take(4 * C));
+    B.Ltot = adjoint ? reinterpret_cast<float4*>(take(16 * C)) : nullptr;
+    B.ctr = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * kCtrStride * 258));
+}
+
+size_t wave_workspace_bytes(uint64_t C, bool adjoint) {
+    // what wave_carve takes, each piece rounded to 256 bytes
+    auto r = [](size_t b) { return (b + 255) & ~size_t(255); };
+    size_t total = 7 * r(16 * C) + r(8 * C) + 3 * r(4 * C) + r(sizeof(uint32_t) * kCtrStride * 258);
+    if (adjoint) total += r(16 * C);
+    return total;
+}
+
+// One pass over paths [P0, P0 + n) of the launch.
+static cudaError_t wave_pass(WaveArgs& A, uint64_t P0, uint32_t n, int replay, const Tune& t,
+                             int sm_count, cudaStream_t s) {
+    A.P0 = P0;
+    cudaError_t e = cudaMemsetAsync(A.B.ctr, 0, sizeof(uint32_t) * kCtrStride * (A.P.max_depth + 2), s);
+    if (e != cudaSuccess) return e;
+    wave_gen<<<(n + 255) / 256, 256, 0, s>>>(A, P0, n);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    for (uint32_t i = 1; i <= A.P.max_depth; ++i) {
+        if ((e = launch_wave_trace<false>(A, (int)i, t, sm_count, s)) != cudaSuccess) return e;
+        wave_shade<<<(n + 255) / 256, 256, 0, s>>>(A, (int)i, replay);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (A.P.sun_on) {
+            if ((e = launch_wave_trace<true>(A, (int)i, t, sm_count, s)) != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_wave(WaveArgs& A, const Tune& t, int sm_count, cudaStream_t s) {
+    // chunks of at most A.capacity paths, cut at pixel boundaries
+    uint64_t P_total = 0;
+    for (uint32_t v = 0; v < A.n_views; ++v)
+        P_total = A.views[v].path_begin + (uint64_t)A.views[v].w * A.views[v].h * A.views[v].spp;
+    uint64_t P0 = A.views[0].path_begin;
+    cudaError_t e = cudaSuccess;
+    while (P0 < P_total) {
+        // view containing P0 and the chunk end rounded down to a pixel boundary
+        uint64_t P1 = std::min<uint64_t>(P_total, P0 + A.capacity);
+        int v1 = 0;
+        for (int v = 0; v < (int)A.n_views; ++v)
+            if (A.views[v].path_begin < P1) v1 = v;
+        const ViewDev& V1 = A.views[v1];
+        if (P1 < P_total) {
+            const uint64_t local = P1 - V1.path_begin;
+            P1 = V1.path_begin + (local / V1.spp) * V1.spp;
+        }
+        const uint32_t n = (uint32_t)(P1 - P0);
+        if (A.grad) {
+            if ((e = wave_pass(A, P0, n, 0, t, sm_count, s)) != cudaSuccess) return e;
+            // radiance of pass one becomes Ltot; L restarts at zero in the replay
+            e = cudaMemcpyAsync(A.B.Ltot, A.B.L, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return e;
+            if ((e = wave_pass(A, P0, n, 1, t, sm_count, s)) != cudaSuccess) return e;
+        } else {
+            if ((e = wave_pass(A, P0, n, 0, t, sm_count, s)) != cudaSuccess) return e;
+            // pixels of this chunk: items whose paths lie in [P0, P1)
+            int v0 = 0;
+            for (int v = 0; v < (int)A.n_views; ++v)
+                if (A.views[v].path_begin <= P0) v0 = v;
+            const ViewDev& V0 = A.views[v0];
+            const uint64_t I0 = V0.item_begin + (P0 - V0.path_begin) / V0.spp;
+            uint64_t I1;
+            if (P1 >= P_total) {
+                const ViewDev& VL = A.views[A.n_views - 1];
+                I1 = VL.item_begin + (uint64_t)VL.w * VL.h;
+            } else {
+                I1 = V1.item_begin + (P1 - V1.path_begin) / V1.spp;
+            }
+            const uint32_t ni = (uint32_t)(I1 - I0);
+            wave_accumulate<<<(ni + 255) / 256, 256, 0, s>>>(A, I0, ni);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        P0 = P1;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace qrt

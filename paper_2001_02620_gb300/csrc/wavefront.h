@@ -1,0 +1,52 @@
+// Wavefront renderer interface (wavefront.cu): per-path state in a
+// workspace of `capacity` paths, carved by wave_carve().
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "launch.h"
+#include "qrt_layout.h"
+
+namespace qrt {
+
+// Counter block per depth: queue lengths and the trace kernels' fetch cursors.
+constexpr int kCtrStride = 8;
+constexpr int kCtrClosest = 0;      // closest-ray queue length of this depth
+constexpr int kCtrShadow = 1;       // shadow-ray queue length of this depth
+constexpr int kCtrFetchClosest = 2;
+constexpr int kCtrFetchShadow = 3;
+
+struct WaveBufs {
+    float4* ray_o;   // origin.xyz, tmin
+    float4* ray_d;   // direction.xyz, tmax
+    float4* beta;    // throughput
+    float4* L;       // radiance (primal) / sun terms so far (replay)
+    float4* pend;    // sun term waiting for its shadow ray
+    float4* sray_o;  // shadow-ray origin
+    uint4* hit;      // t bits, instance, quad, slot
+    uint2* meta;     // (pixel item, sample)
+    uint32_t* q[2];  // closest-ray queues, ping-pong by depth parity
+    uint32_t* qs;    // shadow-ray queue
+    float4* Ltot;    // adjoint: radiance of the first pass
+    uint32_t* ctr;   // kCtrStride words per depth 0..max_depth+1
+};
+
+struct WaveArgs {
+    DevScene S;
+    const float* albedo;
+    float* grad;
+    ParamsDev P;
+    WaveBufs B;
+    unsigned long long* stats;
+    uint64_t P0;        // first path of the current chunk
+    uint64_t capacity;  // paths per chunk
+    uint32_t n_views;
+    uint32_t batch;     // rays a lane claims per fetch
+    ViewDev views[kMaxViewsPerLaunch];
+};
+
+size_t wave_workspace_bytes(uint64_t capacity, bool adjoint);
+void wave_carve(void* base, uint64_t capacity, bool adjoint, WaveBufs& B);
+cudaError_t launch_wave(WaveArgs& A, const Tune& t, int sm_count, cudaStream_t s);
+
+}  // namespace qrt

@@ -137,6 +137,45 @@ def test_render_tiny_sun_and_depth(api, tiny):
     assert (err <= 1e-4 * np.abs(r) + 1e-6).all(), err.max()
 
 
+@pytest.mark.parametrize("chunk_log2", [10, 13, 21])
+def test_wavefront_equals_single_kernel(api, tiny, chunk_log2):
+    """The two renderers compute the same paths with the same arithmetic; a
+    tiny chunk size cuts chunks inside views and pixels' sample runs."""
+    sc, gs, osc = tiny
+    views = I.batched_views(n_views=5, min_log2=5.0, max_log2=7.0, max_spp=5)
+    for v in views:
+        v.eye = (50.0 + (v.eye[0] - 2048.0) / 40, -120.0, 50.0)
+        v.look = (50.0, 50.0, 50.0)
+    params = I.Params(max_depth=4, sun_dir=I.MID_SUN_DIR, sun_E=(3.0, 3.0, 3.0))
+    alb = torch.from_numpy(I.albedo(sc.n_quads)).cuda()
+    D = params.max_depth
+    words = api.path_log_words(views, D)
+    log1 = torch.zeros(words, dtype=torch.int32, device="cuda")
+    log2 = torch.zeros(words, dtype=torch.int32, device="cuda")
+    a = gs.render(views, alb, params, tuning=dict(mode=1), path_log=log1)
+    b = gs.render(views, alb, params, tuning=dict(mode=2, chunk_log2=chunk_log2), path_log=log2)
+    gs.check()
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    assert torch.equal(log1, log2)
+
+
+def test_adjoint_modes_agree(api, tiny):
+    sc, gs, osc = tiny
+    view = I.tiny_view()
+    view.spp = 2
+    params = I.Params(max_depth=3, sun_dir=I.MID_SUN_DIR, sun_E=(3, 3, 3))
+    alb = torch.from_numpy(I.albedo(sc.n_quads)).cuda()
+    dimg = torch.from_numpy(np.random.default_rng(9).normal(size=(view.h, view.w, 3)).astype(np.float32)).cuda()
+    g1 = torch.zeros_like(alb)
+    g2 = torch.zeros_like(alb)
+    gs.adjoint([view], alb, [dimg], g1, params, tuning=dict(mode=1))
+    gs.adjoint([view], alb, [dimg], g2, params, tuning=dict(mode=2, chunk_log2=12))
+    gs.check()
+    # same terms, different atomic order
+    torch.testing.assert_close(g1, g2, rtol=1e-5, atol=1e-7)
+
+
 def test_white_furnace_gpu(api):
     v, q = I.sphere_mesh(24, 48, 5.0)
     sc = I.Scene([(v, q)], I.IDENTITY_XFORM[None].copy(), np.zeros(1, dtype=np.uint32))
