@@ -9,6 +9,7 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -24,16 +25,20 @@ using namespace qrt;
 
 namespace {
 
-thread_local std::string g_err;
+// Last error message of the calling thread, in a fixed buffer so that
+// reporting an error never allocates.
+thread_local char g_err[512];
 
-int fail(int code, const std::string& msg) {
-    g_err = msg;
+int fail(int code, const char* msg) {
+    std::snprintf(g_err, sizeof(g_err), "%s", msg);
     return code;
 }
 
+int fail(int code, const std::string& msg) { return fail(code, msg.c_str()); }
+
 int cuda_fail(cudaError_t e, const char* what) {
-    return fail(e == cudaErrorMemoryAllocation ? QRT_ERR_OOM : QRT_ERR_CUDA,
-                std::string(what) + ": " + cudaGetErrorString(e));
+    std::snprintf(g_err, sizeof(g_err), "%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? QRT_ERR_OOM : QRT_ERR_CUDA;
 }
 
 constexpr int kCounterSlots = 64;
@@ -57,6 +62,7 @@ struct qrt_scene_s {
     void* d_quads = nullptr;
     void* d_prim = nullptr;
     void* d_inst = nullptr;
+    void* d_inst64 = nullptr;
     uint32_t* d_err = nullptr;
     char* d_counters = nullptr;  // kCounterSlots counters, kSlotStride apart
     std::mutex mu;
@@ -101,6 +107,7 @@ void free_scene(qrt_scene_s* s) {
     cudaFree(s->d_quads);
     cudaFree(s->d_prim);
     cudaFree(s->d_inst);
+    cudaFree(s->d_inst64);
     cudaFree(s->d_err);
     cudaFree(s->d_counters);
     for (StreamSlot& sl : s->slots) cudaFree(sl.ws);
@@ -111,9 +118,11 @@ int check_device(const qrt_scene_s* s) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    if (dev != s->device)
-        return fail(QRT_ERR_INVALID_ARG, "scene belongs to device " + std::to_string(s->device) +
-                                             " but device " + std::to_string(dev) + " is current");
+    if (dev != s->device) {
+        std::snprintf(g_err, sizeof(g_err), "scene belongs to device %d but device %d is current",
+                      s->device, dev);
+        return QRT_ERR_INVALID_ARG;
+    }
     return QRT_OK;
 }
 
@@ -196,7 +205,7 @@ cudaError_t upload(void** dptr, const std::vector<T>& v) {
 
 extern "C" {
 
-const char* qrt_last_error(void) { return g_err.c_str(); }
+const char* qrt_last_error(void) { return g_err; }
 
 int qrt_version(void) { return QRT_VERSION; }
 
@@ -293,6 +302,7 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
 
     // 3. instances: FP64 inverse, world boxes
     std::vector<InstDev> inst(n_inst);
+    std::vector<InstDev64> inst64(n_inst);
     std::vector<FBox> wbox(n_inst);
     std::vector<float> meshR(n_mesh);
     for (uint32_t m = 0; m < n_mesh; ++m) {
@@ -313,7 +323,16 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
                         "instance " + std::to_string(i) + " has a non-finite or singular transform");
         InstDev& I = inst[i];
         std::memset(&I, 0, sizeof(I));
-        for (int k = 0; k < 9; ++k) I.w[k] = Ai[k];
+        std::memset(&inst64[i], 0, sizeof(InstDev64));
+        double na = 0.0, ni = 0.0;  // infinity norms (max row sum)
+        for (int r = 0; r < 3; ++r) {
+            na = std::max(na, std::fabs(A[3 * r]) + std::fabs(A[3 * r + 1]) + std::fabs(A[3 * r + 2]));
+            ni = std::max(ni, std::fabs(Ai[3 * r]) + std::fabs(Ai[3 * r + 1]) + std::fabs(Ai[3 * r + 2]));
+        }
+        for (int k = 0; k < 9; ++k) {
+            I.w[k] = (float)Ai[k];
+            inst64[i].w[k] = Ai[k];
+        }
         I.c[0] = x[3];
         I.c[1] = x[7];
         I.c[2] = x[11];
@@ -321,7 +340,7 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
         I.node_base = (uint32_t)node_base[m];
         I.quad_base = (uint32_t)quad_base[m];
         I.R = meshR[m];
-        I.mesh_id = m;
+        I.kappa = (float)(na * ni);
         wbox[i] = transform_box(blas[m].box, x);
     }
     TlasResult tlas;
@@ -368,6 +387,7 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
     if (e == cudaSuccess) e = upload(&s->d_quads, quads);
     if (e == cudaSuccess) e = upload(&s->d_prim, prim);
     if (e == cudaSuccess) e = upload(&s->d_inst, inst);
+    if (e == cudaSuccess) e = upload(&s->d_inst64, inst64);
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_err, 2 * sizeof(uint32_t));
     if (e == cudaSuccess) {
         const uint32_t init[2] = {0u, 0xFFFFFFFFu};
@@ -383,6 +403,7 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
     s->S.quads = static_cast<const QuadDev*>(s->d_quads);
     s->S.prim = static_cast<const uint32_t*>(s->d_prim);
     s->S.inst = static_cast<const InstDev*>(s->d_inst);
+    s->S.inst64 = static_cast<const InstDev64*>(s->d_inst64);
     s->S.tlas_base = (uint32_t)tlas_base;
     s->S.n_inst = (uint32_t)n_inst;
     s->S.R_top = R_top;
@@ -393,7 +414,7 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
     s->stats.blas_nodes = nn;
     s->stats.tlas_nodes = tlas.nodes.size();
     s->stats.device_bytes = nodes.size() * sizeof(QNode) + quads.size() * sizeof(QuadDev) +
-                            prim.size() * 4 + inst.size() * sizeof(InstDev);
+                            prim.size() * 4 + inst.size() * (sizeof(InstDev) + sizeof(InstDev64));
     s->stats.max_blas_depth = max_blas_depth;
     s->stats.tlas_depth = tlas.depth;
     s->stats.build_seconds = build_s;
@@ -453,10 +474,14 @@ int make_views(const qrt_view* views, uint32_t first, uint32_t count, const floa
     uint64_t items = 0, paths = path_begin0;
     for (uint32_t k = 0; k < count; ++k) {
         const qrt_view& v = views[first + k];
-        if (v.w == 0 || v.h == 0 || v.spp == 0)
-            return fail(QRT_ERR_INVALID_ARG, "view " + std::to_string(first + k) + " has zero size or spp");
-        if (!v.out_rgb && !d_dimage)
-            return fail(QRT_ERR_INVALID_ARG, "view " + std::to_string(first + k) + " has no out_rgb");
+        if (v.w == 0 || v.h == 0 || v.spp == 0) {
+            std::snprintf(g_err, sizeof(g_err), "view %u has zero size or spp", first + k);
+            return QRT_ERR_INVALID_ARG;
+        }
+        if (!v.out_rgb && !d_dimage) {
+            std::snprintf(g_err, sizeof(g_err), "view %u has no out_rgb", first + k);
+            return QRT_ERR_INVALID_ARG;
+        }
         if (v.out_rgb && !aligned(v.out_rgb, 4)) return fail(QRT_ERR_ALIGN, "out_rgb must be 4-byte aligned");
         double eye[3] = {v.eye[0], v.eye[1], v.eye[2]};
         double f[3] = {v.look[0] - eye[0], v.look[1] - eye[1], v.look[2] - eye[2]};
@@ -493,8 +518,10 @@ int make_views(const qrt_view* views, uint32_t first, uint32_t count, const floa
         d.path_begin = paths;
         d.out = v.out_rgb;
         d.dimage = d_dimage ? d_dimage[first + k] : nullptr;
-        if (d_dimage && !d.dimage)
-            return fail(QRT_ERR_INVALID_ARG, "d_dimage[" + std::to_string(first + k) + "] is NULL");
+        if (d_dimage && !d.dimage) {
+            std::snprintf(g_err, sizeof(g_err), "d_dimage[%u] is NULL", first + k);
+            return QRT_ERR_INVALID_ARG;
+        }
         items += (uint64_t)v.w * v.h;
         paths += (uint64_t)v.w * v.h * v.spp;
     }

@@ -4,7 +4,8 @@
 //   nodes   QNode[ sum of BLAS nodes | TLAS nodes ]   64 B each, 64-B aligned
 //   quads   QuadDev[ all meshes, leaf order ]          48 B each (4 x float3)
 //   prim    uint32[ same slots ]: original quad index within its mesh
-//   inst    InstDev[ n_inst ]                          128 B each
+//   inst    InstDev[ n_inst ]                          64 B each
+//   inst64  InstDev64[ n_inst ]: FP64 transform for the exact re-test, 80 B
 //
 // All indices are 32-bit offsets from 64-bit bases.  Stack references are
 // local to the current level (TLAS or one BLAS), so every object may hold up
@@ -43,21 +44,27 @@ struct alignas(16) QuadDev {
 };
 static_assert(sizeof(QuadDev) == 48, "QuadDev must be 48 bytes");
 
-// Instance record, one 128-byte line.  The world->object transform is kept
-// in FP64: a ray entering the instance is moved to object space and
-// re-centred near the object in FP64 before it is rounded to FP32, so the
-// FP32 ray's error scales with the object's size, not with its distance.
-struct alignas(128) InstDev {
+// Instance record, 64 bytes.  A ray entering the instance is re-centred on
+// the world ray with error-free FP32 transformations (the point o + t_e d and
+// its offset from c are formed exactly as float pairs), so the FP32 object-
+// space ray's error scales with the object's size and the transform's
+// condition number kappa, not with the object's distance.
+struct alignas(64) InstDev {
     float c[3];          // object origin in world space (translation of object->world)
     float R;             // max |coordinate| of the object's bounding box
+    float w[9];          // world->object linear part, row-major (FP32 of the FP64 inverse)
     uint32_t node_base;  // global index of this object's BLAS root
     uint32_t quad_base;  // global slot of its first quad == its first albedo row
-    uint32_t mesh_id;
-    uint32_t pad0;
-    double w[9];         // world->object linear part, row-major, FP64
-    uint32_t pad1[6];
+    float kappa;         // infinity-norm condition number of the linear part
 };
-static_assert(sizeof(InstDev) == 128, "InstDev must be 128 bytes");
+static_assert(sizeof(InstDev) == 64, "InstDev must be 64 bytes");
+
+// FP64 world->object linear part, read only by the exact quad re-test.
+struct alignas(16) InstDev64 {
+    double w[9];
+    double pad;
+};
+static_assert(sizeof(InstDev64) == 80, "InstDev64 must be 80 bytes");
 
 // Everything a kernel needs, passed by value.
 struct DevScene {
@@ -65,6 +72,7 @@ struct DevScene {
     const QuadDev* quads;
     const uint32_t* prim;
     const InstDev* inst;
+    const InstDev64* inst64;
     uint32_t tlas_base;  // global node index of the TLAS root
     uint32_t n_inst;
     float R_top;         // max |coordinate| of the world box

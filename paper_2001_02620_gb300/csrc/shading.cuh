@@ -81,11 +81,9 @@ __device__ __forceinline__ F3 sample_cosine(F3 n, float xi1, float xi2) {
 // to world space by the inverse transpose, faced against d) of a hit.
 __device__ __forceinline__ F3 hit_normal(const DevScene& S, uint32_t inst, uint32_t slot, F3 d,
                                          uint32_t* quad_base) {
-    const InstDev* ip = S.inst + inst;
-    *quad_base = __ldg(&ip->quad_base);
-    const double2* wp = reinterpret_cast<const double2*>(ip) + 2;
-    const double2 w01 = __ldg(wp), w23 = __ldg(wp + 1), w45 = __ldg(wp + 2), w67 = __ldg(wp + 3);
-    const double w8 = __ldg(reinterpret_cast<const double*>(ip) + 12);
+    const float4* ip = reinterpret_cast<const float4*>(S.inst + inst);
+    const float4 m1 = __ldg(ip + 1), m2 = __ldg(ip + 2), m3 = __ldg(ip + 3);
+    *quad_base = __float_as_uint(m3.z);
     const float4* qv = reinterpret_cast<const float4*>(S.quads + slot);
     const float4 qa = __ldg(qv), qb = __ldg(qv + 1), qc = __ldg(qv + 2);
     const F3 e1 = f3(__fsub_rn(qb.z, qa.x), __fsub_rn(qb.w, qa.y), __fsub_rn(qc.x, qa.z));  // v2 - v0
@@ -94,9 +92,8 @@ __device__ __forceinline__ F3 hit_normal(const DevScene& S, uint32_t inst, uint3
                      __fsub_rn(__fmul_rn(e1.z, e2.x), __fmul_rn(e1.x, e2.z)),
                      __fsub_rn(__fmul_rn(e1.x, e2.y), __fmul_rn(e1.y, e2.x)));
     // n_world = W^T n_obj, W = world->object rows (w0 w1 w2 / w3 w4 w5 / w6 w7 w8)
-    const float W0 = (float)w01.x, W1 = (float)w01.y, W2 = (float)w23.x, W3 = (float)w23.y,
-                W4 = (float)w45.x, W5 = (float)w45.y, W6 = (float)w67.x, W7 = (float)w67.y,
-                W8 = (float)w8;
+    const float W0 = m1.x, W1 = m1.y, W2 = m1.z, W3 = m1.w, W4 = m2.x, W5 = m2.y, W6 = m2.z,
+                W7 = m2.w, W8 = m3.x;
     F3 n = normalize3(f3(__fmaf_rn(W0, no.x, __fmaf_rn(W3, no.y, __fmul_rn(W6, no.z))),
                          __fmaf_rn(W1, no.x, __fmaf_rn(W4, no.y, __fmul_rn(W7, no.z))),
                          __fmaf_rn(W2, no.x, __fmaf_rn(W5, no.y, __fmul_rn(W8, no.z)))));

@@ -1,7 +1,7 @@
 // Ray-query kernels behind qrt_trace_closest / qrt_trace_any.  Persistent:
-// a grid of SMs x resident blocks, each lane claiming `batch` rays at a time
-// from a global cursor and starting its next ray as soon as its own is done,
-// so no lane idles while the rest of its warp finishes slower rays.
+// a grid of SMs x resident blocks running the warp-synchronous traversal loop
+// (persistent_trace); each lane claims `batch` rays at a time from a global
+// cursor and starts its next ray as soon as its own is done.
 #include "launch.h"
 #include "traverse.cuh"
 
@@ -18,43 +18,37 @@ __global__ void __launch_bounds__(256, 2) trace_kernel(const DevScene S, const f
     uint64_t next = 0, end = 0, i = 0;
     uint32_t err = 0;
     uint64_t bad = ~0ull;
-    bool busy = false;
-    for (;;) {
-        if (!busy) {
-            if (next >= end) {
-                next = atomicAdd(cursor, (unsigned long long)batch);
-                end = min(next + batch, n);
-                if (next >= n) break;
-            }
-            i = next++;
-            const float4 a = __ldg(rays + 2 * i), b = __ldg(rays + 2 * i + 1);
-            T.init(S, a.x, a.y, a.z, b.x, b.y, b.z, a.w, b.w, max_steps, st);
-            busy = true;
+    auto fetch_ray = [&]() -> bool {
+        if (next >= end) {
+            next = atomicAdd(cursor, (unsigned long long)batch);
+            end = min(next + batch, n);
+            if (next >= n) return false;
         }
-        busy = T.step(S, st);
-        if (!busy) {
-            if (T.err) {
-                err |= T.err;
-                bad = min(bad, i);
-            }
-            if (ANY) {
-                if (T.h.inst != 0xFFFFFFFFu) atomicOr(occ + (i >> 5), 1u << (i & 31));
-            } else {
-                const uint32_t uq = (uint32_t)__float2uint_rn(__saturatef(T.h.u) * 65535.f);
-                const uint32_t vq = (uint32_t)__float2uint_rn(__saturatef(T.h.v) * 65535.f);
-                const uint32_t uv = T.h.inst == 0xFFFFFFFFu ? 0u : (uq | (vq << 16));
-                hits[i] = make_uint4(__float_as_uint(T.h.t), T.h.inst, T.h.prim, uv);
-            }
+        i = next++;
+        const float4 a = __ldg(rays + 2 * i), b = __ldg(rays + 2 * i + 1);
+        T.init(S, a.x, a.y, a.z, b.x, b.y, b.z, a.w, b.w, max_steps, st);
+        return true;
+    };
+    auto finish_ray = [&]() {
+        if (T.err) {
+            err |= T.err;
+            bad = min(bad, i);
         }
-    }
+        if (ANY) {
+            if (T.h.inst != 0xFFFFFFFFu) atomicOr(occ + (i >> 5), 1u << (i & 31));
+        } else {
+            const uint32_t uq = (uint32_t)__float2uint_rn(__saturatef(T.h.u) * 65535.f);
+            const uint32_t vq = (uint32_t)__float2uint_rn(__saturatef(T.h.v) * 65535.f);
+            const uint32_t uv = T.h.inst == 0xFFFFFFFFu ? 0u : (uq | (vq << 16));
+            hits[i] = make_uint4(__float_as_uint(T.h.t), T.h.inst, T.h.prim, uv);
+        }
+    };
+    persistent_trace<ANY, STACK, FETCH>(S, T, st, fetch_ray, finish_ray);
     if (err) {
         atomicOr(S.err, err);
         atomicMin(S.err + 1, (uint32_t)min(bad, (uint64_t)0xFFFFFFFEu));
     }
-    if (stats) {
-        __syncwarp();
-        add_stats(stats, st);
-    }
+    if (stats) add_stats(stats, st);
 }
 
 template <bool ANY, int STACK, int FETCH>

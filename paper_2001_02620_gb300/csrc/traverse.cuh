@@ -1,10 +1,11 @@
 // Device-side traversal of the two-level quad BVH (qrt_layout.h).
 //
 // Top level: four-wide TLAS over instance world boxes.  At a TLAS leaf the ray
-// is moved into the instance's object space in FP64 (the direction is not
-// renormalised, so t is shared by both levels), re-centred at the point of
-// closest approach to the object's origin, and only then rounded to FP32; the
-// object's BLAS is traversed on the same stack with a parameter s = t - t_e.
+// is re-centred at its point of closest approach to the object's origin,
+// formed exactly with error-free FP32 transformations, and moved into the
+// instance's object space (the direction is not renormalised, so t is shared
+// by both levels); the object's BLAS is traversed on the same stack with a
+// parameter s = t - t_e.
 // When the stack drains back to the level where the instance was entered,
 // the world ray is restored.  Leaves of a BLAS hold up to 16 quads stored
 // contiguously.
@@ -12,8 +13,9 @@
 // Precision design.  Box tests are made conservative by widening every
 // dequantised box by delta, an absolute bound on the position error of the
 // FP32 ray in the current space (2^-20 (|o| + R) at the top level, where the
-// world ray is exact; 2^-21 (|o''| + R) in object space, where o'' is the
-// re-centred origin and R the object's radius), so a node is never culled
+// world ray is exact; 2^-22 (kappa + 2) (|o''| + R) in object space, where o''
+// is the re-centred origin, R the object's radius and kappa the condition
+// number of the transform), so a node is never culled
 // that the exact ray enters.  The quad test is the watertight test of Woop,
 // Benthin and Wald (JCGT 2013) applied to both triangles of the quad with the
 // diagonal v0-v2 shared; an edge function within the same error bound of zero
@@ -128,8 +130,11 @@ __device__ __forceinline__ void load_node(const QNode* n, uint4& a, uint4& b, ui
     }
 }
 
+// Byte i of w as a float, exactly: the byte is placed in the mantissa of
+// 2^23 with one byte permute and 2^23 is subtracted (full-rate integer and
+// FP32 instructions instead of an integer-to-float conversion).
 __device__ __forceinline__ float byte_f(uint32_t w, int i) {
-    return __uint2float_rn((w >> (8 * i)) & 0xFFu);
+    return __fsub_rn(__uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u | (uint32_t)i)), 8388608.0f);
 }
 
 __device__ __forceinline__ float exp2i(int e) { return __int_as_float((e + 127) << 23); }
@@ -224,15 +229,15 @@ __device__ __forceinline__ int classify(float e0, float e1, float e2, float B) {
 // instance's FP64 world->object matrix, then the watertight test with FP64
 // arithmetic.  Returns 1 on a hit with t > tmin (world t written, with
 // quad-space u, v).
-static __device__ __noinline__ int quad_test64(const InstDev* ip, float wox, float woy, float woz,
-                                               float wdx, float wdy, float wdz, const float* v,
-                                               float tmin, double* t_out, float* u_out,
-                                               float* v_out) {
+static __device__ __noinline__ int quad_test64(const InstDev* ip, const InstDev64* ip64, float wox,
+                                               float woy, float woz, float wdx, float wdy, float wdz,
+                                               const float* v, float tmin, double* t_out,
+                                               float* u_out, float* v_out) {
     double o[3], d[3];
     const double e[3] = {(double)wox - (double)ip->c[0], (double)woy - (double)ip->c[1],
                          (double)woz - (double)ip->c[2]};
     const double wd[3] = {wdx, wdy, wdz};
-    const double* w = ip->w;
+    const double* w = ip64->w;
     for (int r = 0; r < 3; ++r) {
         o[r] = w[3 * r] * e[0] + w[3 * r + 1] * e[1] + w[3 * r + 2] * e[2];
         d[r] = w[3 * r] * wd[0] + w[3 * r + 1] * wd[1] + w[3 * r + 2] * wd[2];
@@ -299,7 +304,7 @@ static __device__ __noinline__ int quad_test64(const InstDev* ip, float wox, flo
 // uncertain quad is re-tested by quad_test64, which returns the world t, and
 // is reported with *exact64 = 1.  Returns 1 on a hit.
 __device__ __forceinline__ int quad_test(const RaySetup& r, const QuadDev* q, const InstDev* ip,
-                                         float wox, float woy, float woz, float wdx, float wdy,
+                                         const InstDev64* ip64, float wox, float woy, float woz, float wdx, float wdy,
                                          float wdz, float smin, float tmin, float* t_out,
                                          float* u_out, float* v_out, int* exact64,
                                          uint32_t* n_fallback) {
@@ -323,7 +328,7 @@ __device__ __forceinline__ int quad_test(const RaySetup& r, const QuadDev* q, co
         ++*n_fallback;
         double t64;
         float vv[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
-        if (!quad_test64(ip, wox, woy, woz, wdx, wdy, wdz, vv, tmin, &t64, u_out, v_out))
+        if (!quad_test64(ip, ip64, wox, woy, woz, wdx, wdy, wdz, vv, tmin, &t64, u_out, v_out))
             return 0;
         *t_out = (float)t64;
         *exact64 = 1;
@@ -399,6 +404,7 @@ struct Traversal {
     int sp, inst_sp;
     bool top, have;
     uint32_t node_base, quad_base, cur_inst, cur, steps, max_steps, err;
+    uint32_t pleaf;  // postponed BLAS leaf reference (0 = none)
     Hit h;
 
     __device__ __forceinline__ void init(const DevScene& S, float ox, float oy, float oz, float dx,
@@ -430,6 +436,7 @@ struct Traversal {
         steps = 0;
         max_steps = msteps;
         err = 0;
+        pleaf = 0;
         delta_top = 9.5367431640625e-07f * (maxabs3(ox, oy, oz) + S.R_top);  // 2^-20
         setup_boxes(r, ox, oy, oz, dx, dy, dz, delta_top);
     }
@@ -490,44 +497,159 @@ struct Traversal {
         return true;
     }
 
-    // FP64 world->object move of the ray, re-centred at the closest approach
-    // to the object origin, then rounded to FP32.
+    // ---- warp-synchronous phases (used by the persistent kernels) --------
+    // A lane is in exactly one of: an inner node to test (wants_inner), a TLAS
+    // leaf to enter (at_instance), a BLAS leaf to test (at_leaf: postponed or
+    // current), or finished.
+
+    __device__ __forceinline__ bool wants_inner() const { return have && !(cur & kRefLeaf); }
+    __device__ __forceinline__ bool at_instance() const { return have && (cur & kRefLeaf) && top; }
+    __device__ __forceinline__ bool at_leaf() const {
+        return pleaf != 0 || (have && (cur & kRefLeaf) && !top);
+    }
+    __device__ __forceinline__ bool finished() const { return !have && pleaf == 0; }
+
+    __device__ __forceinline__ void stop(uint32_t e) {
+        err |= e;
+        have = false;
+        pleaf = 0;
+        sp = 0;
+    }
+
+    // Pops until cur holds an entry, the stack is empty, or the instance
+    // boundary is reached while a leaf of this instance is still postponed.
+    // BLAS leaves met on the way are postponed (one at a time) so that the
+    // lane keeps traversing inner nodes with the rest of its warp.
+    __device__ __forceinline__ void advance(const DevScene& S) {
+        for (;;) {
+            if (have) {
+                if (pleaf == 0 && !top && (cur & kRefLeaf)) {
+                    pleaf = cur;
+                    have = false;
+                } else {
+                    return;
+                }
+            }
+            if (!top && sp == inst_sp) {
+                if (pleaf) return;
+                top = true;
+                node_base = S.tlas_base;
+                te = 0.f;
+                setup_boxes(r, wox, woy, woz, wdx, wdy, wdz, delta_top);
+            }
+            if (sp == 0) return;
+            const uint64_t e = stack[--sp];
+            if (__uint_as_float((uint32_t)(e >> 32)) <= limit()) {
+                cur = (uint32_t)e;
+                have = true;
+            }
+        }
+    }
+
+    // Tests the inner node cur and moves on (precondition: wants_inner()).
+    __device__ __forceinline__ void inner_step(const DevScene& S, TraceStats& st) {
+        if (++steps > max_steps) {
+            stop(kErrStepLimit);
+            return;
+        }
+        ++st.nodes;
+        float t[4];
+        uint32_t ref[4];
+        const float lo = top ? tmin : __fsub_rn(tmin, te);
+        const int nh = node_children<FETCH>(S.nodes + node_base + cur, r, lo, limit(), t, ref);
+        if (nh == 0) {
+            have = false;
+        } else {
+            if (sp + nh - 1 > STACK) {
+                stop(kErrStackOverflow);
+                return;
+            }
+#pragma unroll
+            for (int k = 3; k >= 1; --k)
+                if (k < nh) stack[sp++] = ((uint64_t)__float_as_uint(t[k]) << 32) | ref[k];
+            cur = ref[0];
+        }
+        advance(S);
+    }
+
+    // Tests one BLAS leaf (the postponed one first); returns true when an
+    // any-hit query is answered (precondition: at_leaf()).
+    __device__ __forceinline__ bool leaf_step(const DevScene& S, TraceStats& st) {
+        if (pleaf) {
+            const uint32_t keep = cur;
+            cur = pleaf;
+            pleaf = 0;
+            const bool done = leaf(S, st);
+            cur = keep;
+            if (done) return true;
+        } else {
+            if (leaf(S, st)) return true;
+            have = false;
+        }
+        advance(S);
+        return false;
+    }
+
+    // Enters the instance of the TLAS leaf cur (precondition: at_instance()).
+    __device__ __forceinline__ void instance_step(const DevScene& S, TraceStats& st) {
+        enter_instance(S, st);
+    }
+
+    // Moves the ray into the instance's object space.  The world point
+    // p = o + te d nearest the object origin c and its offset p - c are
+    // formed exactly as float pairs (two-product / two-sum), so the FP32
+    // object-space origin W (p - c) carries an error proportional to the
+    // object's size only; the BLAS then works in s = t - te.
     __device__ __forceinline__ void enter_instance(const DevScene& S, TraceStats& st) {
         cur_inst = cur & kRefIndexMask;
-        const InstDev* ip = S.inst + cur_inst;
-        const float4 m0 = __ldg(reinterpret_cast<const float4*>(ip));
-        const uint4 m1 = __ldg(reinterpret_cast<const uint4*>(ip) + 1);
-        const double2* wp = reinterpret_cast<const double2*>(ip) + 2;
-        const double2 w01 = __ldg(wp), w23 = __ldg(wp + 1), w45 = __ldg(wp + 2), w67 = __ldg(wp + 3);
-        const double w8 = __ldg(reinterpret_cast<const double*>(ip) + 12);
-        const double ex = (double)wox - (double)m0.x, ey = (double)woy - (double)m0.y,
-                     ez = (double)woz - (double)m0.z;
-        const double ox = fma(w01.x, ex, fma(w01.y, ey, w23.x * ez));
-        const double oy = fma(w23.y, ex, fma(w45.x, ey, w45.y * ez));
-        const double oz = fma(w67.x, ex, fma(w67.y, ey, w8 * ez));
-        const double dx = fma(w01.x, (double)wdx, fma(w01.y, (double)wdy, w23.x * (double)wdz));
-        const double dy = fma(w23.y, (double)wdx, fma(w45.x, (double)wdy, w45.y * (double)wdz));
-        const double dz = fma(w67.x, (double)wdx, fma(w67.y, (double)wdy, w8 * (double)wdz));
-        const float fdx = (float)dx, fdy = (float)dy, fdz = (float)dz;
-        // closest approach to the object origin (any offset is valid: it only
-        // moves where the FP32 origin sits along the ray)
-        const float fox = (float)ox, foy = (float)oy, foz = (float)oz;
-        const float dd = __fmaf_rn(fdx, fdx, __fmaf_rn(fdy, fdy, __fmul_rn(fdz, fdz)));
-        const float od = __fmaf_rn(fox, fdx, __fmaf_rn(foy, fdy, __fmul_rn(foz, fdz)));
-        te = fmaxf(tmin, __fdiv_rn(-od, dd));
+        const float4* ip = reinterpret_cast<const float4*>(S.inst + cur_inst);
+        const float4 m0 = __ldg(ip), m1 = __ldg(ip + 1), m2 = __ldg(ip + 2), m3 = __ldg(ip + 3);
+        // m0 = (c, R); m1 = (w0 w1 w2 w3); m2 = (w4 w5 w6 w7); m3 = (w8, node_base, quad_base, kappa)
+        const float cx = __fsub_rn(m0.x, wox), cy = __fsub_rn(m0.y, woy), cz = __fsub_rn(m0.z, woz);
+        const float dd = __fmaf_rn(wdx, wdx, __fmaf_rn(wdy, wdy, __fmul_rn(wdz, wdz)));
+        const float cd = __fmaf_rn(cx, wdx, __fmaf_rn(cy, wdy, __fmul_rn(cz, wdz)));
+        te = fmaxf(tmin, __fdiv_rn(cd, dd));
         if (!(te < h.t)) te = tmin;  // also catches a non-finite quotient
-        const double tte = (double)te;
-        const float rox = (float)fma(tte, dx, ox), roy = (float)fma(tte, dy, oy),
-                    roz = (float)fma(tte, dz, oz);
-        node_base = m1.x;
-        quad_base = m1.y;
-        const float delta = 4.76837158203125e-07f * (maxabs3(rox, roy, roz) + m0.w);  // 2^-21
+        float exl, eyl, ezl;
+        const float ex = exact_offset(wox, wdx, te, m0.x, &exl);
+        const float ey = exact_offset(woy, wdy, te, m0.y, &eyl);
+        const float ez = exact_offset(woz, wdz, te, m0.z, &ezl);
+        const float rox = __fmaf_rn(m1.x, ex, __fmaf_rn(m1.y, ey, __fmaf_rn(m1.z, ez,
+                              __fmaf_rn(m1.x, exl, __fmaf_rn(m1.y, eyl, __fmul_rn(m1.z, ezl))))));
+        const float roy = __fmaf_rn(m1.w, ex, __fmaf_rn(m2.x, ey, __fmaf_rn(m2.y, ez,
+                              __fmaf_rn(m1.w, exl, __fmaf_rn(m2.x, eyl, __fmul_rn(m2.y, ezl))))));
+        const float roz = __fmaf_rn(m2.z, ex, __fmaf_rn(m2.w, ey, __fmaf_rn(m3.x, ez,
+                              __fmaf_rn(m2.z, exl, __fmaf_rn(m2.w, eyl, __fmul_rn(m3.x, ezl))))));
+        const float fdx = __fmaf_rn(m1.x, wdx, __fmaf_rn(m1.y, wdy, __fmul_rn(m1.z, wdz)));
+        const float fdy = __fmaf_rn(m1.w, wdx, __fmaf_rn(m2.x, wdy, __fmul_rn(m2.y, wdz)));
+        const float fdz = __fmaf_rn(m2.z, wdx, __fmaf_rn(m2.w, wdy, __fmul_rn(m3.x, wdz)));
+        node_base = __float_as_uint(m3.y);
+        quad_base = __float_as_uint(m3.z);
+        // 2^-22 (kappa + 2) (|o''| + R): rounding of W, of W (p - c), of W d and
+        // of the slab and shear arithmetic, with a factor-two margin
+        const float delta = __fmul_rn(2.384185791015625e-07f * (m3.w + 2.0f),
+                                      maxabs3(rox, roy, roz) + m0.w);
         setup_boxes(r, rox, roy, roz, fdx, fdy, fdz, delta);
         setup_shear(r, fdx, fdy, fdz);
         inst_sp = sp;
         top = false;
         ++st.insts;
         cur = 0;
+    }
+
+    // (o + te d) - c per axis as a float pair hi + *lo, exact up to the
+    // rounding of the small correction terms.
+    static __device__ __forceinline__ float exact_offset(float o, float d, float te, float c, float* lo) {
+        const float q = __fmul_rn(te, d);
+        const float rho = __fmaf_rn(te, d, -q);       // te d = q + rho exactly
+        const float s = __fadd_rn(o, q);
+        const float bb = __fsub_rn(s, o);
+        const float e1 = __fadd_rn(__fsub_rn(o, __fsub_rn(s, bb)), __fsub_rn(q, bb));  // o + q = s + e1
+        const float hi = __fsub_rn(s, c);
+        const float b2 = __fsub_rn(hi, s);
+        const float e2 = __fadd_rn(__fsub_rn(s, __fsub_rn(hi, b2)), __fsub_rn(-c, b2));  // s - c = hi + e2
+        *lo = __fadd_rn(e2, __fadd_rn(e1, rho));
+        return hi;
     }
 
     // Tests the quads of the current BLAS leaf; returns true when an any-hit
@@ -537,13 +659,14 @@ struct Traversal {
         const uint32_t cnt = ((cur >> 27) & 0xFu) + 1u;
         const float smin = __fsub_rn(tmin, te);
         const InstDev* ip = S.inst + cur_inst;
+        const InstDev64* ip64 = S.inst64 + cur_inst;
         for (uint32_t k = 0; k < cnt; ++k) {
             const uint32_t slot = quad_base + first + k;
             float tt, uu, vv;
             int ex64;
             ++st.quads;
-            if (!quad_test(r, S.quads + slot, ip, wox, woy, woz, wdx, wdy, wdz, smin, tmin, &tt, &uu,
-                           &vv, &ex64, &st.fallbacks))
+            if (!quad_test(r, S.quads + slot, ip, ip64, wox, woy, woz, wdx, wdy, wdz, smin, tmin, &tt,
+                           &uu, &vv, &ex64, &st.fallbacks))
                 continue;
             if (!ex64) tt = __fadd_rn(tt, te);
             if (!(tt > tmin && tt < tmax)) continue;
@@ -575,6 +698,48 @@ struct Traversal {
         return false;
     }
 };
+
+// Persistent warp-synchronous traversal loop.  Each lane holds one ray;
+// fetch(ray) claims the next ray (returns false when none is left) and
+// calls T.init; done() consumes the finished ray in T.  Per outer iteration
+// the warp first tests inner nodes together until no lane has one left
+// (lanes that reach a BLAS leaf postpone it and keep traversing), then lanes
+// enter instances or test one leaf each.  Finished lanes refill
+// immediately, so no lane waits for the slowest ray of its warp.
+template <bool ANY, int STACK, int FETCH, class Fetch, class Done>
+__device__ __forceinline__ void persistent_trace(const DevScene& S, Traversal<ANY, STACK, FETCH>& T,
+                                                 TraceStats& st, Fetch fetch, Done done) {
+    const unsigned FULL = 0xFFFFFFFFu;
+    bool busy = false, exhausted = false;
+    for (;;) {
+        if (!busy && !exhausted) {
+            if (fetch())
+                busy = true;
+            else
+                exhausted = true;
+        }
+        if (__all_sync(FULL, !busy)) break;
+        for (;;) {
+            const bool w = busy && T.wants_inner();
+            if (!__any_sync(FULL, w)) break;
+            if (w) T.inner_step(S, st);
+        }
+        if (busy) {
+            if (T.at_instance()) {
+                T.instance_step(S, st);
+            } else if (T.at_leaf()) {
+                if (T.leaf_step(S, st)) {
+                    T.have = false;
+                    T.pleaf = 0;
+                }
+            }
+            if (T.finished() || (ANY && T.h.inst != 0xFFFFFFFFu)) {
+                done();
+                busy = false;
+            }
+        }
+    }
+}
 
 // Closest hit (ANY = false) or any hit (ANY = true) of the world ray, run to
 // completion.  Returns device error bits (0 = fine); h holds the best hit

@@ -101,52 +101,45 @@ __global__ void __launch_bounds__(256, 2) wave_trace(const __grid_constant__ Wav
     Traversal<ANY, STACK, FETCH> T;
     uint32_t next = 0, end = 0, j = 0;
     uint32_t err = 0;
-    bool busy = false;
-    for (;;) {
-        if (!busy) {
-            if (next >= end) {
-                next = atomicAdd(fetch, batch);
-                end = min(next + batch, count);
-                if (next >= count) break;
-            }
-            j = queue[next++];
-            if (ANY) {
-                const float4 o = A.B.sray_o[j];
-                T.init(A.S, o.x, o.y, o.z, A.P.sun_l[0], A.P.sun_l[1], A.P.sun_l[2], 0.f, kInfF,
-                       A.P.max_steps, st);
-            } else {
-                const float4 o = A.B.ray_o[j], d = A.B.ray_d[j];
-                T.init(A.S, o.x, o.y, o.z, d.x, d.y, d.z, o.w, d.w, A.P.max_steps, st);
-            }
-            busy = true;
+    auto fetch_ray = [&]() -> bool {
+        if (next >= end) {
+            next = atomicAdd(fetch, batch);
+            end = min(next + batch, count);
+            if (next >= count) return false;
         }
-        busy = T.step(A.S, st);
-        if (!busy) {
-            err |= T.err;
-            if (ANY) {
-                if (T.h.inst == 0xFFFFFFFFu) {
-                    const float4 p = A.B.pend[j];
-                    float4 l = A.B.L[j];
-                    l.x = __fadd_rn(l.x, p.x);
-                    l.y = __fadd_rn(l.y, p.y);
-                    l.z = __fadd_rn(l.z, p.z);
-                    A.B.L[j] = l;
-                } else if (A.P.path_log && depth <= 16) {
-                    const uint64_t g = A.P0 + j;
-                    A.P.path_log[g * (2ull * A.P.max_depth + 1) + 2 * A.P.max_depth] |=
-                        2u << (2 * (depth - 1));
-                }
-            } else {
-                A.B.hit[j] = make_uint4(__float_as_uint(T.h.t), T.h.inst, T.h.prim, T.h.slot);
-            }
+        j = queue[next++];
+        if (ANY) {
+            const float4 o = A.B.sray_o[j];
+            T.init(A.S, o.x, o.y, o.z, A.P.sun_l[0], A.P.sun_l[1], A.P.sun_l[2], 0.f, kInfF,
+                   A.P.max_steps, st);
+        } else {
+            const float4 o = A.B.ray_o[j], d = A.B.ray_d[j];
+            T.init(A.S, o.x, o.y, o.z, d.x, d.y, d.z, o.w, d.w, A.P.max_steps, st);
         }
-    }
+        return true;
+    };
+    auto finish_ray = [&]() {
+        err |= T.err;
+        if (ANY) {
+            if (T.h.inst == 0xFFFFFFFFu) {
+                const float4 p = A.B.pend[j];
+                float4 l = A.B.L[j];
+                l.x = __fadd_rn(l.x, p.x);
+                l.y = __fadd_rn(l.y, p.y);
+                l.z = __fadd_rn(l.z, p.z);
+                A.B.L[j] = l;
+            } else if (A.P.path_log && depth <= 16) {
+                const uint64_t g = A.P0 + j;
+                A.P.path_log[g * (2ull * A.P.max_depth + 1) + 2 * A.P.max_depth] |=
+                    2u << (2 * (depth - 1));
+            }
+        } else {
+            A.B.hit[j] = make_uint4(__float_as_uint(T.h.t), T.h.inst, T.h.prim, T.h.slot);
+        }
+    };
+    persistent_trace<ANY, STACK, FETCH>(A.S, T, st, fetch_ray, finish_ray);
     if (err) atomicOr(A.S.err, err);
-    if (A.stats) {
-        // lanes leave the loop at different times; reconverge before the warp reduction
-        __syncwarp();
-        add_stats(A.stats, st);
-    }
+    if (A.stats) add_stats(A.stats, st);
 }
 
 // Shade stage of depth i (1-based).  replay = false: primal; true: replay
@@ -301,14 +294,6 @@ void wave_carve(void* base, uint64_t C, bool adjoint, WaveBufs& B) {
     B.qs = reinterpret_cast<uint32_t*>(take(4 * C));
     B.Ltot = adjoint ? reinterpret_cast<float4*>(take(16 * C)) : nullptr;
     B.ctr = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * kCtrStride * 258));
-}
-
-size_t wave_workspace_bytes(uint64_t C, bool adjoint) {
-    // what wave_carve takes, each piece rounded to 256 bytes
-    auto r = [](size_t b) { return (b + 255) & ~size_t(255); };
-    size_t total = 7 * r(16 * C) + r(8 * C) + 3 * r(4 * C) + r(sizeof(uint32_t) * kCtrStride * 258);
-    if (adjoint) total += r(16 * C);
-    return total;
 }
 
 // One pass over paths [P0, P0 + n) of the launch.

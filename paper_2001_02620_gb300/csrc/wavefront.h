@@ -45,7 +45,15 @@ struct WaveArgs {
     ViewDev views[kMaxViewsPerLaunch];
 };
 
-size_t wave_workspace_bytes(uint64_t capacity, bool adjoint);
+// Bytes wave_carve() takes for `capacity` paths (each piece 256-B aligned).
+constexpr size_t wave_workspace_bytes(uint64_t capacity, bool adjoint) {
+    return 7 * (((16 * capacity) + 255) & ~uint64_t(255)) + (((8 * capacity) + 255) & ~uint64_t(255)) +
+           3 * (((4 * capacity) + 255) & ~uint64_t(255)) +
+           ((sizeof(uint32_t) * kCtrStride * 258 + 255) & ~uint64_t(255)) +
+           (adjoint ? (((16 * capacity) + 255) & ~uint64_t(255)) : 0);
+}
+
+
 void wave_carve(void* base, uint64_t capacity, bool adjoint, WaveBufs& B);
 cudaError_t launch_wave(WaveArgs& A, const Tune& t, int sm_count, cudaStream_t s);
 
