@@ -216,6 +216,28 @@ int qrt_trace_any(qrt_scene scene, const qrt_ray* d_rays, uint64_t n, uint32_t* 
 int qrt_render_spp(qrt_scene scene, const qrt_view* views, uint32_t n_views,
                    const float* d_albedo, const qrt_params* params, qrt_stream stream);
 
+/* qrt_render_spp for callers that cannot allocate device memory -- for
+ * example code that runs while a stream is being captured into a CUDA graph,
+ * an interactive frame loop that must not stall on cudaMalloc, or a process
+ * whose device memory is owned by another allocator.  No paper counterpart:
+ * it is an interface variant of this library, with the same results as
+ * qrt_render_spp.
+ *
+ * It renders with the wavefront renderer, using as scratch a fixed array of
+ * about 17 MB compiled into the library (device global memory held on every
+ * GPU that loads the library, until the process exits), enough for chunks of
+ * 2^17 paths; any number of views and paths is processed chunk by chunk.
+ * The call allocates nothing and calls no cudaMalloc or cudaFree.  The first
+ * call on a device looks up the array's device address (once per device;
+ * make that first call before any stream capture).  tuning.chunk_log2 may be
+ * 0 (= 17) or at most 17, and tuning.mode 0 or 2; anything else is rejected
+ * with QRT_ERR_INVALID_ARG.  Every call shares the one array and clears what
+ * must start at zero itself, so calls that overlap on the GPU (different
+ * streams, or different host threads) race with each other: order them on
+ * one stream. */
+int qrt_render_spp_static(qrt_scene scene, const qrt_view* views, uint32_t n_views,
+                          const float* d_albedo, const qrt_params* params, qrt_stream stream);
+
 /* Adjoint of qrt_render_spp with respect to the albedo: adds
  * sum_v sum_pixel sum_c d_dimage[v][pixel*3+c] * dI_v[pixel,c]/d albedo[q,c]
  * into d_grad_albedo (DEVICE float [n_quads*3], accumulated, not cleared).

@@ -82,6 +82,7 @@ SIGNATURES = {
     "qrt_trace_closest": (_i, [_vp, _vp, _u64, _vp, C.POINTER(qrt_tuning), _vp]),
     "qrt_trace_any": (_i, [_vp, _vp, _u64, _vp, C.POINTER(qrt_tuning), _vp]),
     "qrt_render_spp": (_i, [_vp, C.POINTER(qrt_view), _u32, _vp, C.POINTER(qrt_params), _vp]),
+    "qrt_render_spp_static": (_i, [_vp, C.POINTER(qrt_view), _u32, _vp, C.POINTER(qrt_params), _vp]),
     "qrt_render_adjoint": (_i, [_vp, C.POINTER(qrt_view), _u32, _vp, C.POINTER(_vp), _vp,
                                 C.POINTER(qrt_params), _vp]),
     "qrt_l2_loss": (_i, [_vp, _vp, _u64, _vp, _vp, _vp]),

@@ -574,6 +574,46 @@ int ensure_workspace(StreamSlot& sl, size_t bytes, cudaStream_t s) {
     return QRT_OK;
 }
 
+// Enqueues the wavefront render (or adjoint) of all views on stream s in
+// the given workspace; W and R are the caller's storage for the launch
+// parameter blocks (so this function allocates nothing).
+int wave_enqueue(qrt_scene scene, const qrt_view* views, uint32_t n_views, const float* d_albedo,
+                 const float* const* d_dimage, float* d_grad, const qrt_params* params,
+                 const Tune& t, void* workspace, size_t ws_bytes, unsigned long long* stats,
+                 cudaStream_t s, WaveArgs& W, RenderArgs& R) {
+    static_assert(sizeof(WaveArgs) < 32000, "kernel parameter block too large");
+    const bool adjoint = d_grad != nullptr;
+    const uint64_t cap = 1ull << t.chunk_log2;
+    if (wave_workspace_bytes(cap, adjoint) > ws_bytes)
+        return fail(QRT_ERR_INVALID_ARG, "wavefront workspace too small for chunk_log2");
+    std::memset(&W, 0, sizeof(WaveArgs));
+    std::memset(&R, 0, sizeof(RenderArgs));
+    W.S = scene->S;
+    W.albedo = d_albedo;
+    W.grad = d_grad;
+    W.stats = stats;
+    W.capacity = cap;
+    W.batch = (uint32_t)t.batch;
+    wave_carve(workspace, cap, adjoint, W.B);
+    int rc = make_params(params, W.P);
+    if (adjoint) W.P.path_log = nullptr;
+    // the view table is shared with the single-kernel renderer's layout
+    uint64_t paths = 0;
+    for (uint32_t first = 0; rc == QRT_OK && first < n_views; first += kMaxViewsPerLaunch) {
+        const uint32_t cnt = std::min<uint32_t>(kMaxViewsPerLaunch, n_views - first);
+        rc = make_views(views, first, cnt, d_dimage, R, paths);
+        if (rc) break;
+        for (uint32_t k = 0; k < cnt; ++k) {
+            W.views[k] = R.views[k];
+            paths += (uint64_t)views[first + k].w * views[first + k].h * views[first + k].spp;
+        }
+        W.n_views = cnt;
+        cudaError_t e = launch_wave(W, t, scene->sm_count, s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "wavefront launch");
+    }
+    return rc;
+}
+
 // Enqueues the render (or adjoint) of all views on stream s.  counter serves
 // the single-kernel renderer, workspace (bytes) the wavefront one.
 int render_enqueue(qrt_scene scene, const qrt_view* views, uint32_t n_views, const float* d_albedo,
@@ -610,36 +650,10 @@ int render_enqueue(qrt_scene scene, const qrt_view* views, uint32_t n_views, con
         delete A;
         return rc;
     }
-    static_assert(sizeof(WaveArgs) < 32000, "kernel parameter block too large");
-    const uint64_t cap = 1ull << t.chunk_log2;
-    if (wave_workspace_bytes(cap, adjoint) > ws_bytes)
-        return fail(QRT_ERR_INVALID_ARG, "wavefront workspace too small for chunk_log2");
     WaveArgs* W = new WaveArgs();
-    std::memset(W, 0, sizeof(WaveArgs));
-    W->S = scene->S;
-    W->albedo = d_albedo;
-    W->grad = d_grad;
-    W->stats = stats;
-    W->capacity = cap;
-    W->batch = (uint32_t)t.batch;
-    wave_carve(workspace, cap, adjoint, W->B);
-    rc = make_params(params, W->P);
-    if (adjoint) W->P.path_log = nullptr;
-    // the view table is shared with the single-kernel renderer's layout
     RenderArgs* R = new RenderArgs();
-    uint64_t paths = 0;
-    for (uint32_t first = 0; rc == QRT_OK && first < n_views; first += kMaxViewsPerLaunch) {
-        const uint32_t cnt = std::min<uint32_t>(kMaxViewsPerLaunch, n_views - first);
-        rc = make_views(views, first, cnt, d_dimage, *R, paths);
-        if (rc) break;
-        for (uint32_t k = 0; k < cnt; ++k) {
-            W->views[k] = R->views[k];
-            paths += (uint64_t)views[first + k].w * views[first + k].h * views[first + k].spp;
-        }
-        W->n_views = cnt;
-        cudaError_t e = launch_wave(*W, t, scene->sm_count, s);
-        if (e != cudaSuccess) rc = cuda_fail(e, "wavefront launch");
-    }
+    rc = wave_enqueue(scene, views, n_views, d_albedo, d_dimage, d_grad, params, t, workspace,
+                      ws_bytes, stats, s, *W, *R);
     delete R;
     delete W;
     return rc;
@@ -689,6 +703,35 @@ int qrt_render_spp(qrt_scene scene, const qrt_view* views, uint32_t n_views, con
     if (rc) return rc;
     return render_enqueue(scene, views, n_views, d_albedo, nullptr, nullptr, params, ctr, ws, wsb,
                           nullptr, s);
+}
+
+// qrt_render_spp without any allocation: the wavefront renderer with its
+// workspace in a fixed device array of the library (see qrt.h).
+int qrt_render_spp_static(qrt_scene scene, const qrt_view* views, uint32_t n_views,
+                          const float* d_albedo, const qrt_params* params, qrt_stream stream) {
+    int rc = render_args_check(scene, views, n_views, d_albedo);
+    if (rc) return rc;
+    if (!params) return fail(QRT_ERR_INVALID_ARG, "params is NULL");
+    if (n_views == 0) return QRT_OK;
+    qrt_tuning tt = params->tuning;
+    if (tt.mode == 1)
+        return fail(QRT_ERR_INVALID_ARG,
+                    "qrt_render_spp_static runs the wavefront renderer only (tuning.mode 0 or 2)");
+    if (tt.chunk_log2 == 0) tt.chunk_log2 = kStaticChunkLog2;
+    if (tt.chunk_log2 > (uint32_t)kStaticChunkLog2)
+        return fail(QRT_ERR_INVALID_ARG,
+                    "tuning.chunk_log2 exceeds the static workspace (at most 17: 131072 paths "
+                    "per chunk)");
+    Tune t = resolve_tuning(&tt);
+    rc = validate_tuning(t);
+    if (rc) return rc;
+    void* ws = nullptr;
+    cudaError_t e = static_workspace(&ws);
+    if (e != cudaSuccess) return cuda_fail(e, "static workspace address");
+    WaveArgs W;  // parameter blocks on the stack: nothing is allocated
+    RenderArgs R;
+    return wave_enqueue(scene, views, n_views, d_albedo, nullptr, nullptr, params, t, ws,
+                        kStaticWorkspaceBytes, nullptr, reinterpret_cast<cudaStream_t>(stream), W, R);
 }
 
 // Same as qrt_render_spp with traversal counters added into d_stats (device

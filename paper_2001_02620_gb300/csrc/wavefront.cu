@@ -19,6 +19,7 @@
 // Radiance is accumulated in the same order as render.cu, so the two
 // renderers give bit-identical images.
 #include <algorithm>
+#include <mutex>
 
 #include "launch.h"
 #include "shading.cuh"
@@ -294,6 +295,29 @@ void wave_carve(void* base, uint64_t C, bool adjoint, WaveBufs& B) {
     B.qs = reinterpret_cast<uint32_t*>(take(4 * C));
     B.Ltot = adjoint ? reinterpret_cast<float4*>(take(16 * C)) : nullptr;
     B.ctr = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * kCtrStride * 258));
+}
+
+// Scratch of qrt_render_spp_static.  It lives as long as the library is
+// loaded on every device that runs it; concurrent calls share it.
+static __device__ __align__(256) unsigned char g_static_workspace[kStaticWorkspaceBytes];
+
+cudaError_t static_workspace(void** ptr) {
+    constexpr int kMaxDevices = 64;
+    static std::mutex mu;
+    static void* addr[kMaxDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> g(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_workspace);
+        if (e != cudaSuccess) return e;
+        addr[dev] = p;
+    }
+    *ptr = addr[dev];
+    return cudaSuccess;
 }
 
 // One pass over paths [P0, P0 + n) of the launch.

@@ -53,7 +53,14 @@ constexpr size_t wave_workspace_bytes(uint64_t capacity, bool adjoint) {
            (adjoint ? (((16 * capacity) + 255) & ~uint64_t(255)) : 0);
 }
 
+// Fixed device scratch for renders that must not allocate: a primal
+// workspace of 2^kStaticChunkLog2 paths in a file-scope __device__ array.
+constexpr int kStaticChunkLog2 = 17;
+constexpr size_t kStaticWorkspaceBytes = wave_workspace_bytes(1ull << kStaticChunkLog2, false);
 
+// Device address of that array on the current device (looked up once per
+// device with cudaGetSymbolAddress; allocates nothing).
+cudaError_t static_workspace(void** ptr);
 void wave_carve(void* base, uint64_t capacity, bool adjoint, WaveBufs& B);
 cudaError_t launch_wave(WaveArgs& A, const Tune& t, int sm_count, cudaStream_t s);
 
