@@ -89,7 +89,22 @@ def mid_workload():
     return sc, I.mid_view(), I.mid_params(), I.albedo(sc.n_quads)
 
 
-def oracle_sample(sc, view, params, alb, budget_s: float, rank_pixels: int = 0):
+def moana_workload(scale: float):
+    from paper_2001_02620_gb300 import inputs as I
+    sc = I.moana_scene(scale)
+    return sc, I.moana_view(sc.meta["extent"]), I.moana_params(), I.albedo(sc.n_quads)
+
+
+WORKLOADS = {
+    "mid": "mid: 64 prototypes (log-uniform 2^12..2^16 quads) + 2048^2-quad terrain = 5.73M "
+           "unique quads, 100k instances, 1024x1024, 4 spp, depth 5, env + sun shadow rays",
+    "moana": "moana-scale: 5000 prototypes (1000 Zipf 8M..~20k quads + 4000 of 16..512) + "
+             "2048^2 terrain = 261.1M unique quads, 39.3M clustered instances (82.4G instanced "
+             "quads), 1920x1080, 16 spp, depth 8, env + sun shadow rays",
+}
+
+
+def oracle_sample(sc, view, params, alb, budget_s: float, frame: str = "1024x1024 mid"):
     """Times the FP64 oracle on a bounded pixel sample of the same workload."""
     import oracle as O
     t0 = time.time()
@@ -115,7 +130,7 @@ def oracle_sample(sc, view, params, alb, budget_s: float, rank_pixels: int = 0):
         n *= 2
     cores = os.cpu_count() or 1
     return {"value": rays / elapsed / 1e6, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
-            "sample": f"{done} random pixels x {view.spp} spp of the 1024x1024 mid frame "
+            "sample": f"{done} random pixels x {view.spp} spp of the {frame} frame "
                       f"({rays} rays, {elapsed:.1f} s FP64, oracle BVH build {build_s:.1f} s excluded)",
             "paths_per_s": done * view.spp / elapsed}
 
@@ -138,15 +153,18 @@ def _time(fn, reps: int, warm: int = 2) -> float:
     return float(np.median(ts))
 
 
-def bench_trace(scene, sc, dev):
-    """trace_closest / trace_any throughput on 4M-ray sets of the mid scene."""
+def bench_trace(scene, sc, dev, tuning=None, eye=(2048.0, -300.0, 450.0)):
+    """trace_closest / trace_any throughput on 4M-ray sets over the scene:
+    a coherent bundle from the camera, incoherent rays from random origins,
+    and parallel rays toward the sun."""
     import torch
     from paper_2001_02620_gb300 import inputs as I
+    ext = float(sc.meta.get("extent", 4096.0))
     lo = np.array([0.0, 0.0, -150.0])
-    hi = np.array([4096.0, 4096.0, 250.0])
+    hi = np.array([ext, ext, 250.0])
     n = 1 << 22
     sets = {
-        "primary": I.rays_focused(n, (2048.0, -300.0, 450.0), lo, hi, seed=51),
+        "primary": I.rays_focused(n, eye, lo, hi, seed=51),
         "incoherent": I.rays_random(n, lo, hi, seed=52),
         "shadow": I.rays_parallel(n, lo, hi, I.MID_SUN_DIR, seed=53),
     }
@@ -155,8 +173,8 @@ def bench_trace(scene, sc, dev):
     bits = torch.empty(((n + 31) // 32,), dtype=torch.int32, device=dev)
     for name, rays in sets.items():
         d = torch.from_numpy(rays).to(dev)
-        tc = _time(lambda: scene.trace_closest(d, hits), 5)
-        ta = _time(lambda: scene.trace_any(d, bits), 5)
+        tc = _time(lambda: scene.trace_closest(d, hits, tuning=tuning), 5)
+        ta = _time(lambda: scene.trace_any(d, bits, tuning=tuning), 5)
         st = torch.zeros(STAT_WORDS, dtype=torch.int64, device=dev)
         scene.trace_stats(d, False, hits, st)
         s = st.cpu().numpy()
@@ -168,7 +186,7 @@ def bench_trace(scene, sc, dev):
     return out
 
 
-def bench_batched(api, scene, d_alb, dev):
+def bench_batched(api, scene, d_alb, dev, tuning=None):
     """32 uneven views of the mid scene: one graph-captured persistent launch
     versus 32 plain launches on one stream; images must be bit-identical."""
     import torch
@@ -178,11 +196,11 @@ def bench_batched(api, scene, d_alb, dev):
     paths = sum(v.w * v.h * v.spp for v in views)
     outs_b = [torch.empty((v.h, v.w, 3), device=dev) for v in views]
     outs_p = [torch.empty((v.h, v.w, 3), device=dev) for v in views]
-    graph = api.RenderGraph(scene, views, d_alb, params, outs=outs_b)
+    graph = api.RenderGraph(scene, views, d_alb, params, outs=outs_b, tuning=tuning)
 
     def plain():
         for v, o in zip(views, outs_p):
-            scene.render([v], d_alb, params, outs=[o])
+            scene.render([v], d_alb, params, outs=[o], tuning=tuning)
 
     tb = _time(graph.launch, 3, warm=1)
     tp = _time(plain, 3, warm=1)
@@ -193,7 +211,7 @@ def bench_batched(api, scene, d_alb, dev):
             "batched_ms": tb * 1e3, "plain_ms": tp * 1e3}
 
 
-def bench_adjoint(api, scene, sc, dev):
+def bench_adjoint(api, scene, sc, dev, tuning=None):
     """Adjoint workload (512x512, 8 spp, depth 4): replay adjoint vs primal."""
     import torch
     from paper_2001_02620_gb300 import inputs as I
@@ -205,9 +223,9 @@ def bench_adjoint(api, scene, sc, dev):
     img = torch.empty_like(target)
     dimg = torch.empty_like(target)
     grad = torch.zeros_like(alb)
-    tp = _time(lambda: scene.render([view], alb, params, outs=[img]), 5)
+    tp = _time(lambda: scene.render([view], alb, params, outs=[img], tuning=tuning), 5)
     api.l2_loss(img, target, dimg)
-    ta = _time(lambda: scene.adjoint([view], alb, [dimg], grad, params), 5)
+    ta = _time(lambda: scene.adjoint([view], alb, [dimg], grad, params, tuning=tuning), 5)
     scene.check()
     return {"primal_ms": tp * 1e3, "adjoint_ms": ta * 1e3, "ratio": ta / tp,
             "paths": view.w * view.h * view.spp, "n_params": int(a0.size)}
@@ -250,6 +268,10 @@ def main():
     ap.add_argument("--res", type=int, default=0,
                     help="override the view side (small profiling captures only)")
     ap.add_argument("--spp", type=int, default=0, help="override spp (profiling only)")
+    ap.add_argument("--no-tune", action="store_true", help="library default launch parameters")
+    ap.add_argument("--workload", default="mid", choices=sorted(WORKLOADS))
+    ap.add_argument("--moana-scale", type=float, default=1.0,
+                    help="moana workload: fraction of the full counts (1 = 261M quads)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -269,7 +291,12 @@ def main():
     from paper_2001_02620_gb300 import api, inputs as I
     from paper_2001_02620_gb300 import build as B
     B.build()
-    sc, view, params, alb = mid_workload()
+    t_gen = time.time()
+    if args.workload == "moana":
+        sc, view, params, alb = moana_workload(args.moana_scale)
+    else:
+        sc, view, params, alb = mid_workload()
+    gen_s = time.time() - t_gen
     if args.res:
         view.w = view.h = args.res
     if args.spp:
@@ -283,12 +310,20 @@ def main():
     img = torch.empty((view.h, view.w, 3), device=dev)
     stream = torch.cuda.current_stream()
 
+    tuning = None
+    tune_s = 0.0
+    if not args.no_tune:
+        from paper_2001_02620_gb300 import autotune
+        t0 = time.time()
+        tuning = autotune.tune(scene, view, d_alb, params, scene_name="mid")
+        tune_s = time.time() - t0
+
     def step():
-        scene.render([view], d_alb, params, outs=[img])
+        scene.render([view], d_alb, params, outs=[img], tuning=tuning)
 
     # counters of one render (same launch configuration, counters added)
     stats = torch.zeros(STAT_WORDS, dtype=torch.int64, device=dev)
-    scene.render([view], d_alb, params, outs=[img], stats=stats)
+    scene.render([view], d_alb, params, outs=[img], stats=stats, tuning=tuning)
     scene.check()
     st = stats.cpu().numpy()
     rays, nodes, quads, insts, fallbacks, verts = [int(x) for x in st]
@@ -324,7 +359,7 @@ def main():
     h_img = torch.empty((view.h, view.w, 3)).pin_memory()
     for _ in range(2):
         d_alb.copy_(h_alb, non_blocking=True)
-        scene.render([view], d_alb, params, outs=[img])
+        scene.render([view], d_alb, params, outs=[img], tuning=tuning)
         h_img.copy_(img, non_blocking=True)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -332,7 +367,7 @@ def main():
     e0.record(stream)
     for _ in range(args.steps):
         d_alb.copy_(h_alb, non_blocking=True)
-        scene.render([view], d_alb, params, outs=[img])
+        scene.render([view], d_alb, params, outs=[img], tuning=tuning)
         h_img.copy_(img, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -346,10 +381,10 @@ def main():
         "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "mid: 64 prototypes (log-uniform 2^12..2^16 quads) + 2048^2-quad "
-                               "terrain = 5.73M unique quads, 100k instances, 1024x1024, 4 spp, "
-                               "depth 5, env + sun shadow rays",
-                   "parallelism": f"replicas{world}", "l2": "working set 0.47 GB > L2 (no flush)"},
+        "config": {"workload": WORKLOADS[args.workload] if args.workload != "moana" or
+                   args.moana_scale == 1.0 else WORKLOADS["moana"] + f" x {args.moana_scale}",
+                   "parallelism": f"replicas{world}",
+                   "l2": f"working set {scene.stats['device_bytes'] / 1e9:.2f} GB > L2 (no flush)"},
         "path_samples_per_s": world * paths / (ms * 1e-3),
         "rays_per_step": rays, "paths_per_step": paths,
         "counters": {"nodes": nodes, "quads": quads, "instance_entries": insts,
@@ -362,17 +397,23 @@ def main():
                 "ms_per_step": e2e_ms},
         "gpu_launches": args.steps,
         "clocks": clk,
-        "scene_build_s": build_s,
+        "scene_build_s": build_s, "scene_gen_s": gen_s,
+        "scene": {k: scene.stats[k] for k in ("n_quads", "n_instances", "blas_nodes", "tlas_nodes",
+                                              "device_bytes", "max_blas_depth", "tlas_depth")},
+        "tuning": tuning, "tune_s": tune_s,
     }
     extras = [] if args.extras == "none" else args.extras.split(",")
+    if args.workload != "mid":
+        extras = [e for e in extras if e == "trace"]
     if "trace" in extras:
-        line["trace"] = bench_trace(scene, sc, dev)
+        line["trace"] = bench_trace(scene, sc, dev, tuning, eye=view.eye)
     if "batched" in extras:
-        line["batched_vs_plain"] = bench_batched(api, scene, d_alb, dev)
+        line["batched_vs_plain"] = bench_batched(api, scene, d_alb, dev, tuning)
     if "adjoint" in extras:
-        line["adjoint_vs_primal"] = bench_adjoint(api, scene, sc, dev)
+        line["adjoint_vs_primal"] = bench_adjoint(api, scene, sc, dev, tuning)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = oracle_sample(sc, view, params, alb, budget_s=12.0)
+        line["cpu_baseline"] = oracle_sample(sc, view, params, alb, budget_s=12.0,
+                                             frame=f"{view.w}x{view.h} {args.workload}")
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

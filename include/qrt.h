@@ -109,7 +109,8 @@ typedef struct {
  *                  of 32; wavefront: rays a lane claims per fetch
  *   stack          traversal stack entries per ray (32 or 64)
  *   fetch          node fetch width in bytes (16: 4x128-bit, 32: 2x256-bit loads)
- *   adjoint_mode   reserved (0)
+ *   occupancy      trace kernels' register budget as resident warps per SM:
+ *                  16 (up to 128 registers a thread, default) or 24 (up to 85)
  *   mode           renderer: 0 = default (wavefront), 1 = single persistent
  *                  kernel (a lane renders whole pixels), 2 = wavefront (stages
  *                  gen / trace / shade / shadow / accumulate over queues; a
@@ -123,7 +124,7 @@ typedef struct {
     uint32_t batch;
     uint32_t stack;
     uint32_t fetch;
-    uint32_t adjoint_mode;
+    uint32_t occupancy;
     uint32_t mode;
     uint32_t chunk_log2;
 } qrt_tuning;

@@ -43,7 +43,7 @@ class qrt_view(C.Structure):
 
 class qrt_tuning(C.Structure):
     _fields_ = [("block", C.c_uint32), ("blocks_per_sm", C.c_uint32), ("batch", C.c_uint32),
-                ("stack", C.c_uint32), ("fetch", C.c_uint32), ("adjoint_mode", C.c_uint32),
+                ("stack", C.c_uint32), ("fetch", C.c_uint32), ("occupancy", C.c_uint32),
                 ("mode", C.c_uint32), ("chunk_log2", C.c_uint32)]
 
 

@@ -1,9 +1,10 @@
-"""Autotuner for the launch parameters of the render kernel.
+"""Autotuner for the launch parameters of the renderer.
 
-Searches traversal stack depth, node-fetch width, block size and the number of
-32-pixel groups a warp claims per fetch by timing renders of a proxy view
-(the target view at reduced resolution, same spp and depth) and keeps the
-fastest configuration that raised no device error.  Results are cached as
+Searches traversal stack depth, node-fetch width, block size, rays a lane
+claims per fetch and the trace kernels' register budget (resident warps per
+SM) by timing renders of a proxy view (the target view at reduced
+resolution, same spp and depth) and keeps the fastest configuration that
+raised no device error.  Results are cached as
 JSON keyed by (GPU name, SM count, scene class), so later runs skip the
 search.  None of the parameters changes a rendered value: images are
 bit-identical under every candidate.
@@ -19,11 +20,13 @@ import time
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                              "autotune_cache", "qrt_tuning.json")
 
+# The stack depth is not searched: a shallower stack that suffices on the
+# proxy view can overflow on another view, and an overflow changes results.
 SPACE = {
     "block": [64, 128, 256],
-    "stack": [32, 64],
     "fetch": [16, 32],
-    "batch": [1, 2, 4],
+    "batch": [1, 4],
+    "occupancy": [16, 24],
 }
 
 
@@ -73,7 +76,7 @@ def pick_best(timings: dict) -> tuple[str, float]:
     return k, ok[k]
 
 
-def proxy_view(view, max_side: int = 256):
+def proxy_view(view, max_side: int = 384):
     s = min(1.0, max_side / max(view.w, view.h))
     return dataclasses.replace(view, w=max(32, int(view.w * s)), h=max(32, int(view.h * s)))
 

@@ -134,7 +134,7 @@ Tune resolve_tuning(const qrt_tuning* t) {
     if (t->batch) r.batch = (int)t->batch;
     if (t->stack) r.stack = (int)t->stack;
     if (t->fetch) r.fetch = (int)t->fetch;
-    if (t->adjoint_mode) r.adjoint_mode = (int)t->adjoint_mode;
+    if (t->occupancy) r.occupancy = (int)t->occupancy;
     if (t->mode) r.mode = (int)t->mode;
     if (t->chunk_log2) r.chunk_log2 = (int)t->chunk_log2;
     return r;
@@ -150,7 +150,8 @@ int validate_tuning(const Tune& t) {
     if (t.batch < 1 || t.batch > 64) return fail(QRT_ERR_INVALID_ARG, "tuning.batch must be 1..64");
     if (t.blocks_per_sm < 0 || t.blocks_per_sm > 32)
         return fail(QRT_ERR_INVALID_ARG, "tuning.blocks_per_sm must be 0..32");
-    if (t.adjoint_mode != 0) return fail(QRT_ERR_INVALID_ARG, "tuning.adjoint_mode must be 0");
+    if (t.occupancy != 16 && t.occupancy != 24)
+        return fail(QRT_ERR_INVALID_ARG, "tuning.occupancy must be 0, 16 or 24");
     if (t.mode < 1 || t.mode > 2) return fail(QRT_ERR_INVALID_ARG, "tuning.mode must be 0, 1 or 2");
     if (t.chunk_log2 < 10 || t.chunk_log2 > 26)
         return fail(QRT_ERR_INVALID_ARG, "tuning.chunk_log2 must be 10..26");

@@ -7,8 +7,8 @@
 
 namespace qrt {
 
-template <bool ANY, int STACK, int FETCH>
-__global__ void __launch_bounds__(256, 2) trace_kernel(const DevScene S, const float4* __restrict__ rays,
+template <bool ANY, int STACK, int FETCH, int MINB>
+__global__ void __launch_bounds__(256, MINB) trace_kernel(const DevScene S, const float4* __restrict__ rays,
                                                        uint64_t n, uint4* __restrict__ hits,
                                                        uint32_t* __restrict__ occ, uint32_t max_steps,
                                                        unsigned long long* cursor, uint32_t batch,
@@ -51,24 +51,21 @@ __global__ void __launch_bounds__(256, 2) trace_kernel(const DevScene S, const f
     if (stats) add_stats(stats, st);
 }
 
-template <bool ANY, int STACK, int FETCH>
-static int occupancy(int block) {
-    int k = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, trace_kernel<ANY, STACK, FETCH>, block, 0);
-    return k;
-}
-
-template <bool ANY, int STACK, int FETCH>
+template <bool ANY, int STACK, int FETCH, int MINB>
 static cudaError_t launch_variant(const DevScene& S, const float4* rays, uint64_t n, uint4* hits,
                                   uint32_t* occ, uint32_t max_steps, unsigned long long* cursor,
                                   unsigned long long* stats, const Tune& t, int sm_count,
                                   cudaStream_t s) {
-    int per_sm = t.blocks_per_sm > 0 ? t.blocks_per_sm : occupancy<ANY, STACK, FETCH>(t.block);
-    if (per_sm < 1) per_sm = 1;
+    int per_sm = t.blocks_per_sm;
+    if (per_sm <= 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel<ANY, STACK, FETCH, MINB>,
+                                                      t.block, 0);
+        if (per_sm < 1) per_sm = 1;
+    }
     uint64_t grid = (uint64_t)sm_count * per_sm;
     const uint64_t want = (n + (uint64_t)t.block - 1) / (uint64_t)t.block;
     if (want < grid) grid = want;
-    trace_kernel<ANY, STACK, FETCH><<<(unsigned)grid, t.block, 0, s>>>(
+    trace_kernel<ANY, STACK, FETCH, MINB><<<(unsigned)grid, t.block, 0, s>>>(
         S, rays, n, hits, occ, max_steps, cursor, (uint32_t)t.batch, stats);
     return cudaGetLastError();
 }
@@ -80,14 +77,18 @@ static cudaError_t launch_any_variant(const DevScene& S, const void* rays, uint6
                                       cudaStream_t s) {
     const float4* r = static_cast<const float4*>(rays);
     uint4* hp = static_cast<uint4*>(hits);
-    if (t.stack <= 32) {
-        if (t.fetch == 32)
-            return launch_variant<ANY, 32, 32>(S, r, n, hp, occ, max_steps, cursor, stats, t, sm_count, s);
-        return launch_variant<ANY, 32, 16>(S, r, n, hp, occ, max_steps, cursor, stats, t, sm_count, s);
+    const bool s32 = t.stack <= 32, f32 = t.fetch == 32, o24 = t.occupancy == 24;
+#define QRT_TV(ST, FE, MB) \
+    return launch_variant<ANY, ST, FE, MB>(S, r, n, hp, occ, max_steps, cursor, stats, t, sm_count, s)
+    if (o24) {
+        if (s32) { if (f32) QRT_TV(32, 32, 3); QRT_TV(32, 16, 3); }
+        if (f32) QRT_TV(64, 32, 3);
+        QRT_TV(64, 16, 3);
     }
-    if (t.fetch == 32)
-        return launch_variant<ANY, 64, 32>(S, r, n, hp, occ, max_steps, cursor, stats, t, sm_count, s);
-    return launch_variant<ANY, 64, 16>(S, r, n, hp, occ, max_steps, cursor, stats, t, sm_count, s);
+    if (s32) { if (f32) QRT_TV(32, 32, 2); QRT_TV(32, 16, 2); }
+    if (f32) QRT_TV(64, 32, 2);
+    QRT_TV(64, 16, 2);
+#undef QRT_TV
 }
 
 cudaError_t launch_trace(bool any, const DevScene& S, const void* rays, uint64_t n, void* hits,

@@ -1,8 +1,8 @@
 // Device-side traversal of the two-level quad BVH (qrt_layout.h).
 //
 // Top level: four-wide TLAS over instance world boxes.  At a TLAS leaf the ray
-// is re-centred at its point of closest approach to the object's origin,
-// formed exactly with error-free FP32 transformations, and moved into the
+// is re-centred at the point where it enters the instance's box, formed
+// exactly with error-free FP32 transformations, and moved into the
 // instance's object space (the direction is not renormalised, so t is shared
 // by both levels); the object's BLAS is traversed on the same stack with a
 // parameter s = t - t_e.
@@ -52,6 +52,9 @@ struct RaySetup {
     float ry0, ry1, ry2, cy;
     float rz0, rz1, rz2, cz;
     float delta;
+    float dx, dy, dz;  // direction in the current space (for the shear, set lazily)
+    float eps_t;       // bound on the error of an FP32 hit distance (t units)
+    bool sheared;      // shear rows valid for the current space
 };
 
 __device__ __forceinline__ float clamp_dir(float d) {
@@ -74,9 +77,15 @@ __device__ __forceinline__ void setup_boxes(RaySetup& r, float ox, float oy, flo
     r.pz = __fmul_rn(delta, fabsf(r.iz));
     r.neg = (r.ix < 0.f ? 1u : 0u) | (r.iy < 0.f ? 2u : 0u) | (r.iz < 0.f ? 4u : 0u);
     r.delta = delta;
+    r.dx = dx;
+    r.dy = dy;
+    r.dz = dz;
+    r.sheared = false;
 }
 
-__device__ __forceinline__ void setup_shear(RaySetup& r, float dx, float dy, float dz) {
+__device__ __forceinline__ void setup_shear(RaySetup& r) {
+    const float dx = r.dx, dy = r.dy, dz = r.dz;
+    r.sheared = true;
     const float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
     // kz = dominant axis, (kx, ky) the next two in cyclic order; selects
     // instead of indexed arrays keep everything in registers
@@ -87,7 +96,9 @@ __device__ __forceinline__ void setup_shear(RaySetup& r, float dx, float dy, flo
     const float okx = kz == 0 ? r.oy : (kz == 1 ? r.oz : r.ox);
     const float oky = kz == 0 ? r.oz : (kz == 1 ? r.ox : r.oy);
     const float okz = kz == 0 ? r.ox : (kz == 1 ? r.oy : r.oz);
-    const float Sx = __fdiv_rn(dkx, dkz), Sy = __fdiv_rn(dky, dkz), Sz = __frcp_rn(dkz);
+    // one reciprocal; the products' extra rounding is covered by delta
+    const float Sz = __frcp_rn(dkz);
+    const float Sx = __fmul_rn(dkx, Sz), Sy = __fmul_rn(dky, Sz);
     // row X: +1 at kx, -Sx at kz; row Y: +1 at ky, -Sy at kz; row Z: Sz at kz
     r.rx0 = kz == 0 ? -Sx : (kz == 2 ? 1.f : 0.f);
     r.rx1 = kz == 1 ? -Sx : (kz == 0 ? 1.f : 0.f);
@@ -101,6 +112,9 @@ __device__ __forceinline__ void setup_shear(RaySetup& r, float dx, float dy, flo
     r.cx = __fmaf_rn(-Sx, okz, okx);
     r.cy = __fmaf_rn(-Sy, okz, oky);
     r.cz = __fmul_rn(Sz, okz);
+    // a position error of delta moves the distance along the dominant axis
+    // by delta |Sz|; twice that bounds the FP32 hit distance's error
+    r.eps_t = 2.0f * __fmul_rn(r.delta, fabsf(Sz));
 }
 
 __device__ __forceinline__ float maxabs3(float a, float b, float c) {
@@ -300,14 +314,16 @@ static __device__ __noinline__ int quad_test64(const InstDev* ip, const InstDev6
 
 // FP32 test of one quad; returns 1 on a hit with tmin < t (t, u, v written);
 // may defer to quad_test64.
-// FP32 test of one quad in the object-space parameter s (s > smin); an
-// uncertain quad is re-tested by quad_test64, which returns the world t, and
-// is reported with *exact64 = 1.  Returns 1 on a hit.
+// FP32 test of one quad in the object-space parameter s (smin < s < smax).
+// A quad whose hit/miss decision is uncertain -- an edge function within its
+// error band of zero, or the hit distance within eps_t of either end of the
+// interval -- is re-tested by quad_test64, which returns the world t
+// (*t64_out, *exact64 = 1).  Returns 1 on a hit.
 __device__ __forceinline__ int quad_test(const RaySetup& r, const QuadDev* q, const InstDev* ip,
-                                         const InstDev64* ip64, float wox, float woy, float woz, float wdx, float wdy,
-                                         float wdz, float smin, float tmin, float* t_out,
-                                         float* u_out, float* v_out, int* exact64,
-                                         uint32_t* n_fallback) {
+                                         const InstDev64* ip64, float wox, float woy, float woz,
+                                         float wdx, float wdy, float wdz, float smin, float smax,
+                                         float tmin, float* t_out, double* t64_out, float* u_out,
+                                         float* v_out, int* exact64, uint32_t* n_fallback) {
     const float4* p = reinterpret_cast<const float4*>(q);
     const float4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
     const SV s0 = shear(r, a.x, a.y, a.z);
@@ -324,44 +340,64 @@ __device__ __forceinline__ int quad_test(const RaySetup& r, const QuadDev* q, co
     const int c0 = classify(e21, e02, e10, B);
     const int c1 = classify(e32, e03, -e02, B);
     if (c0 == 0 && c1 == 0) return 0;
-    if (c0 == 2 || c1 == 2) {
+    bool uncertain = c0 == 2 || c1 == 2;
+    float best = kInfF;
+    int hit = 0;
+    if (!uncertain) {
+        if (c0 == 1) {
+            const float det = e21 + e02 + e10;
+            const float T = __fmaf_rn(e21, s0.Z, __fmaf_rn(e02, s1.Z, __fmul_rn(e10, s2.Z)));
+            const float tt = __fdiv_rn(T, det);
+            if (tt > smin) {
+                best = tt;
+                hit = 1;
+                *u_out = __fdiv_rn(e02 + e10, det);
+                *v_out = __fdiv_rn(e10, det);
+            }
+            uncertain |= fabsf(tt - smin) <= r.eps_t || fabsf(tt - smax) <= r.eps_t;
+        }
+        if (c1 == 1) {
+            const float det = e32 + e03 - e02;
+            const float T = __fmaf_rn(e32, s0.Z, __fmaf_rn(e03, s2.Z, __fmul_rn(-e02, s3.Z)));
+            const float tt = __fdiv_rn(T, det);
+            if (tt > smin && tt < best) {
+                best = tt;
+                hit = 1;
+                *u_out = __fdiv_rn(e03, det);
+                *v_out = __fdiv_rn(e03 - e02, det);
+            }
+            uncertain |= fabsf(tt - smin) <= r.eps_t || fabsf(tt - smax) <= r.eps_t;
+        }
+    }
+    if (uncertain) {
         ++*n_fallback;
         double t64;
         float vv[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
         if (!quad_test64(ip, ip64, wox, woy, woz, wdx, wdy, wdz, vv, tmin, &t64, u_out, v_out))
             return 0;
         *t_out = (float)t64;
+        *t64_out = t64;
         *exact64 = 1;
         return 1;
     }
     *exact64 = 0;
-    const float tmin_ = smin;  // the FP32 path works in s
-    float best = kInfF;
-    int hit = 0;
-    if (c0 == 1) {
-        const float det = e21 + e02 + e10;
-        const float T = __fmaf_rn(e21, s0.Z, __fmaf_rn(e02, s1.Z, __fmul_rn(e10, s2.Z)));
-        const float tt = __fdiv_rn(T, det);
-        if (tt > tmin_) {
-            best = tt;
-            hit = 1;
-            *u_out = __fdiv_rn(e02 + e10, det);
-            *v_out = __fdiv_rn(e10, det);
-        }
-    }
-    if (c1 == 1) {
-        const float det = e32 + e03 - e02;
-        const float T = __fmaf_rn(e32, s0.Z, __fmaf_rn(e03, s2.Z, __fmul_rn(-e02, s3.Z)));
-        const float tt = __fdiv_rn(T, det);
-        if (tt > tmin_ && tt < best) {
-            best = tt;
-            hit = 1;
-            *u_out = __fdiv_rn(e03, det);
-            *v_out = __fdiv_rn(e03 - e02, det);
-        }
-    }
     *t_out = best;
     return hit;
+}
+
+// Exact (FP64) hit distance of quad `slot` of instance `inst` for the world
+// ray, or +inf if the FP64 test misses it.
+static __device__ __noinline__ double exact_t(const DevScene& S, uint32_t inst, uint32_t slot,
+                                              float wox, float woy, float woz, float wdx, float wdy,
+                                              float wdz, float tmin) {
+    const float* v = S.quads[slot].v;
+    float vv[12];
+    for (int k = 0; k < 12; ++k) vv[k] = v[k];
+    double t64;
+    float u, w;
+    if (!quad_test64(S.inst + inst, S.inst64 + inst, wox, woy, woz, wdx, wdy, wdz, vv, tmin, &t64, &u, &w))
+        return __longlong_as_double(0x7ff0000000000000ll);
+    return t64;
 }
 
 // --------------------------------------------------------------------------
@@ -404,6 +440,8 @@ struct Traversal {
     int sp, inst_sp;
     bool top, have;
     uint32_t node_base, quad_base, cur_inst, cur, steps, max_steps, err;
+    float cur_t;     // entry distance of the box of cur (from its parent's test)
+    float h_eps;     // error bound of h.t (0 if exact)
     uint32_t pleaf;  // postponed BLAS leaf reference (0 = none)
     Hit h;
 
@@ -432,6 +470,8 @@ struct Traversal {
         cur_inst = 0;
         te = 0.f;
         cur = 0;  // TLAS root, an inner reference
+        cur_t = t0;
+        h_eps = 0.f;
         have = S.n_inst > 0;
         steps = 0;
         max_steps = msteps;
@@ -471,6 +511,7 @@ struct Traversal {
                     for (int k = 3; k >= 1; --k)
                         if (k < nh) stack[sp++] = ((uint64_t)__float_as_uint(t[k]) << 32) | ref[k];
                     cur = ref[0];
+                    cur_t = t[0];
                     return true;
                 }
             } else if (top) {
@@ -490,8 +531,10 @@ struct Traversal {
         }
         if (sp == 0) return false;
         const uint64_t e = stack[--sp];
-        if (__uint_as_float((uint32_t)(e >> 32)) <= limit()) {
+        const float tn = __uint_as_float((uint32_t)(e >> 32));
+        if (tn <= limit()) {
             cur = (uint32_t)e;
+            cur_t = tn;
             have = true;
         }
         return true;
@@ -539,8 +582,10 @@ struct Traversal {
             }
             if (sp == 0) return;
             const uint64_t e = stack[--sp];
-            if (__uint_as_float((uint32_t)(e >> 32)) <= limit()) {
+            const float tn = __uint_as_float((uint32_t)(e >> 32));
+            if (tn <= limit()) {
                 cur = (uint32_t)e;
+                cur_t = tn;
                 have = true;
             }
         }
@@ -568,6 +613,7 @@ struct Traversal {
             for (int k = 3; k >= 1; --k)
                 if (k < nh) stack[sp++] = ((uint64_t)__float_as_uint(t[k]) << 32) | ref[k];
             cur = ref[0];
+            cur_t = t[0];
         }
         advance(S);
     }
@@ -596,20 +642,20 @@ struct Traversal {
     }
 
     // Moves the ray into the instance's object space.  The world point
-    // p = o + te d nearest the object origin c and its offset p - c are
-    // formed exactly as float pairs (two-product / two-sum), so the FP32
-    // object-space origin W (p - c) carries an error proportional to the
-    // object's size only; the BLAS then works in s = t - te.
+    // p = o + te d where the ray enters the instance's box and its offset
+    // p - c from the object origin are formed exactly as float pairs
+    // (two-product / two-sum), so the FP32 object-space origin W (p - c)
+    // carries an error proportional to the object's size only; the BLAS then
+    // works in s = t - te.
     __device__ __forceinline__ void enter_instance(const DevScene& S, TraceStats& st) {
         cur_inst = cur & kRefIndexMask;
         const float4* ip = reinterpret_cast<const float4*>(S.inst + cur_inst);
         const float4 m0 = __ldg(ip), m1 = __ldg(ip + 1), m2 = __ldg(ip + 2), m3 = __ldg(ip + 3);
         // m0 = (c, R); m1 = (w0 w1 w2 w3); m2 = (w4 w5 w6 w7); m3 = (w8, node_base, quad_base, kappa)
-        const float cx = __fsub_rn(m0.x, wox), cy = __fsub_rn(m0.y, woy), cz = __fsub_rn(m0.z, woz);
-        const float dd = __fmaf_rn(wdx, wdx, __fmaf_rn(wdy, wdy, __fmul_rn(wdz, wdz)));
-        const float cd = __fmaf_rn(cx, wdx, __fmaf_rn(cy, wdy, __fmul_rn(cz, wdz)));
-        te = fmaxf(tmin, __fdiv_rn(cd, dd));
-        if (!(te < h.t)) te = tmin;  // also catches a non-finite quotient
+        // Re-centre where the ray enters the instance's world box (never
+        // before tmin): every hit lies beyond it, so s = t - te starts at 0 and
+        // keeps full precision near the origin of rays that start on a surface.
+        te = (cur_t < h.t) ? fmaxf(tmin, cur_t) : tmin;
         float exl, eyl, ezl;
         const float ex = exact_offset(wox, wdx, te, m0.x, &exl);
         const float ey = exact_offset(woy, wdy, te, m0.y, &eyl);
@@ -629,8 +675,7 @@ struct Traversal {
         // of the slab and shear arithmetic, with a factor-two margin
         const float delta = __fmul_rn(2.384185791015625e-07f * (m3.w + 2.0f),
                                       maxabs3(rox, roy, roz) + m0.w);
-        setup_boxes(r, rox, roy, roz, fdx, fdy, fdz, delta);
-        setup_shear(r, fdx, fdy, fdz);
+        setup_boxes(r, rox, roy, roz, fdx, fdy, fdz, delta);  // shear follows at the first leaf
         inst_sp = sp;
         top = false;
         ++st.insts;
@@ -653,20 +698,24 @@ struct Traversal {
     }
 
     // Tests the quads of the current BLAS leaf; returns true when an any-hit
-    // query is answered.
+    // query is answered.  Two candidates whose FP32 distances are within
+    // their error bounds of each other are ordered by their FP64 distances.
     __device__ __forceinline__ bool leaf(const DevScene& S, TraceStats& st) {
+        if (!r.sheared) setup_shear(r);
         const uint32_t first = cur & kRefIndexMask;
         const uint32_t cnt = ((cur >> 27) & 0xFu) + 1u;
         const float smin = __fsub_rn(tmin, te);
+        const float smax = __fsub_rn(tmax, te);
         const InstDev* ip = S.inst + cur_inst;
         const InstDev64* ip64 = S.inst64 + cur_inst;
         for (uint32_t k = 0; k < cnt; ++k) {
             const uint32_t slot = quad_base + first + k;
             float tt, uu, vv;
+            double t64;
             int ex64;
             ++st.quads;
-            if (!quad_test(r, S.quads + slot, ip, ip64, wox, woy, woz, wdx, wdy, wdz, smin, tmin, &tt,
-                           &uu, &vv, &ex64, &st.fallbacks))
+            if (!quad_test(r, S.quads + slot, ip, ip64, wox, woy, woz, wdx, wdy, wdz, smin, smax, tmin,
+                           &tt, &t64, &uu, &vv, &ex64, &st.fallbacks))
                 continue;
             if (!ex64) tt = __fadd_rn(tt, te);
             if (!(tt > tmin && tt < tmax)) continue;
@@ -677,6 +726,28 @@ struct Traversal {
                 h.slot = slot;
                 return true;
             }
+            const float eps = fmaxf(r.eps_t, h_eps);
+            if (h.inst != 0xFFFFFFFFu && fabsf(tt - h.t) <= eps &&
+                !(h.slot == slot && h.inst == cur_inst)) {
+                // near tie with the current best: decide on FP64 distances
+                ++st.fallbacks;
+                const double tb = exact_t(S, h.inst, h.slot, wox, woy, woz, wdx, wdy, wdz, tmin);
+                const double tc = ex64 ? t64
+                                       : exact_t(S, cur_inst, slot, wox, woy, woz, wdx, wdy, wdz, tmin);
+                const uint32_t pr = __ldg(S.prim + slot);
+                const bool better = tc < tb || (tc == tb && (cur_inst < h.inst ||
+                                                             (cur_inst == h.inst && pr < h.prim)));
+                if (better && tc < (double)tmax) {
+                    h.t = (float)tc;
+                    h.inst = cur_inst;
+                    h.prim = pr;
+                    h.u = uu;
+                    h.v = vv;
+                    h.slot = slot;
+                    h_eps = r.eps_t;
+                }
+                continue;
+            }
             if (tt < h.t) {
                 h.t = tt;
                 h.inst = cur_inst;
@@ -684,6 +755,7 @@ struct Traversal {
                 h.u = uu;
                 h.v = vv;
                 h.slot = slot;
+                h_eps = ex64 ? 0.f : r.eps_t;
             } else if (tt == h.t) {
                 const uint32_t pr = __ldg(S.prim + slot);
                 if (cur_inst < h.inst || (cur_inst == h.inst && pr < h.prim)) {
@@ -692,6 +764,7 @@ struct Traversal {
                     h.u = uu;
                     h.v = vv;
                     h.slot = slot;
+                    h_eps = ex64 ? 0.f : r.eps_t;
                 }
             }
         }

@@ -91,8 +91,8 @@ __global__ void __launch_bounds__(256) wave_gen(const __grid_constant__ WaveArgs
 // Persistent trace over a queue.  ANY = false: closest hit of ray_o/ray_d of
 // each queued path into hit[].  ANY = true: shadow ray from sray_o toward the
 // sun; an unoccluded ray adds pend[] into L[].
-template <bool ANY, int STACK, int FETCH>
-__global__ void __launch_bounds__(256, 2) wave_trace(const __grid_constant__ WaveArgs A, int depth) {
+template <bool ANY, int STACK, int FETCH, int MINB>
+__global__ void __launch_bounds__(256, MINB) wave_trace(const __grid_constant__ WaveArgs A, int depth) {
     const uint32_t* ctr = A.B.ctr + kCtrStride * depth;
     const uint32_t count = ANY ? ctr[kCtrShadow] : ctr[kCtrClosest];
     uint32_t* fetch = A.B.ctr + kCtrStride * depth + (ANY ? kCtrFetchShadow : kCtrFetchClosest);
@@ -247,32 +247,33 @@ __global__ void __launch_bounds__(256) wave_accumulate(const __grid_constant__ W
     out[2] = __fdiv_rn(s2, (float)V.spp);
 }
 
-template <bool ANY, int STACK, int FETCH>
-static int trace_occupancy(int block) {
-    int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, wave_trace<ANY, STACK, FETCH>, block, 0);
-    return n;
+template <bool ANY, int STACK, int FETCH, int MINB>
+static cudaError_t launch_wave_trace_v(const WaveArgs& A, int depth, const Tune& t, int sm_count,
+                                       cudaStream_t s) {
+    int per_sm = t.blocks_per_sm;
+    if (per_sm <= 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wave_trace<ANY, STACK, FETCH, MINB>,
+                                                      t.block, 0);
+        if (per_sm < 1) per_sm = 1;
+    }
+    wave_trace<ANY, STACK, FETCH, MINB><<<(unsigned)(sm_count * per_sm), t.block, 0, s>>>(A, depth);
+    return cudaGetLastError();
 }
 
 template <bool ANY>
 static cudaError_t launch_wave_trace(const WaveArgs& A, int depth, const Tune& t, int sm_count,
                                      cudaStream_t s) {
-    const bool s32 = t.stack <= 32, f32 = t.fetch == 32;
-    int per_sm = t.blocks_per_sm;
-    if (per_sm <= 0) {
-        per_sm = s32 ? (f32 ? trace_occupancy<ANY, 32, 32>(t.block) : trace_occupancy<ANY, 32, 16>(t.block))
-                     : (f32 ? trace_occupancy<ANY, 64, 32>(t.block) : trace_occupancy<ANY, 64, 16>(t.block));
-        if (per_sm < 1) per_sm = 1;
+    const bool s32 = t.stack <= 32, f32 = t.fetch == 32, o24 = t.occupancy == 24;
+#define QRT_WT(ST, FE, MB) return launch_wave_trace_v<ANY, ST, FE, MB>(A, depth, t, sm_count, s)
+    if (o24) {
+        if (s32) { if (f32) QRT_WT(32, 32, 3); QRT_WT(32, 16, 3); }
+        if (f32) QRT_WT(64, 32, 3);
+        QRT_WT(64, 16, 3);
     }
-    const dim3 g((unsigned)(sm_count * per_sm)), b((unsigned)t.block);
-    if (s32) {
-        if (f32) wave_trace<ANY, 32, 32><<<g, b, 0, s>>>(A, depth);
-        else wave_trace<ANY, 32, 16><<<g, b, 0, s>>>(A, depth);
-    } else {
-        if (f32) wave_trace<ANY, 64, 32><<<g, b, 0, s>>>(A, depth);
-        else wave_trace<ANY, 64, 16><<<g, b, 0, s>>>(A, depth);
-    }
-    return cudaGetLastError();
+    if (s32) { if (f32) QRT_WT(32, 32, 2); QRT_WT(32, 16, 2); }
+    if (f32) QRT_WT(64, 32, 2);
+    QRT_WT(64, 16, 2);
+#undef QRT_WT
 }
 
 void wave_carve(void* base, uint64_t C, bool adjoint, WaveBufs& B) {

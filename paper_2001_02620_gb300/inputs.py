@@ -315,7 +315,7 @@ def mid_scene(seed_geom: int = SEED_GEOMETRY, seed_inst: int = SEED_INSTANCES,
     xf = np.concatenate([xf, IDENTITY_XFORM[None]], axis=0)
     ids = np.concatenate([ids, np.array([terrain_id], dtype=np.uint32)])
     return Scene(meshes, xf, ids, name="mid",
-                 meta={"n_proto": n_proto, "terrain_mesh": terrain_id})
+                 meta={"n_proto": n_proto, "terrain_mesh": terrain_id, "extent": extent})
 
 
 def mid_view(w: int = 1024, h: int = 1024, spp: int = 4) -> View:
@@ -465,3 +465,135 @@ def plane_mesh(n: int = 8):
     X, Y = np.meshgrid(xs, xs, indexing="xy")
     verts = np.stack([X.ravel(), Y.ravel(), np.zeros(X.size)], axis=1).astype(np.float32)
     return verts, grid_quads(n, n)
+
+
+# --------------------------------------------------------------------------
+# Moana-scale workload
+# --------------------------------------------------------------------------
+
+MOANA_QUADS = 261_100_000          # unique quads (Section 1)
+MOANA_INSTANCES = 39_300_000       # instances (Section 1)
+MOANA_INSTANCED_QUADS = 82.4e9     # quads after instancing (Section 1)
+MOANA_PROTOS = 5000
+MOANA_NMAX = 8_000_000             # multi-million-quad trees (Section 4.2)
+MOANA_EXTENT = 8192.0
+MOANA_TERRAIN_QUADS = 2048
+
+
+def _solve_bisect(f, lo, hi, iters=100):
+    flo = f(lo)
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        fm = f(mid)
+        if (fm > 0) == (flo > 0):
+            lo, flo = mid, fm
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def moana_sizes(scale: float = 1.0, seed: int = SEED_GEOMETRY):
+    """Prototype quad counts and instance counts of the Moana-scale workload.
+
+    Two populations, as the island has (Section 4.2): 1000 large objects with
+    quad counts n_p = n_max p^-gamma (trees of millions of quads down to
+    rocks and bushes), gamma solved so that all unique quads total 261 M; and
+    4000 small objects of 2^U(4, 9) quads (leaves, buds, pebbles).  Instance
+    counts: large objects c_p proportional to n_p^-1/2, small ones uniform;
+    the split between the two is solved so that the instances total 39.3 M
+    and the instanced quads 82.4 G.  scale < 1 shrinks every total."""
+    s1 = min(1.0, scale ** 0.5)
+    PL = max(4, int(round(1000 * s1)))
+    PS = max(4, int(round(4000 * s1)))
+    rng = np.random.default_rng(seed + 77)
+    ns = np.round(2.0 ** rng.uniform(4.0, 9.0, size=PS)).astype(np.int64)
+    terrain = MOANA_TERRAIN_QUADS ** 2 if scale >= 0.5 else int(MOANA_TERRAIN_QUADS * scale ** 0.5) ** 2
+    QL = MOANA_QUADS * scale - terrain - ns.sum()
+    nmax = max(256.0, MOANA_NMAX * scale)
+    p = np.arange(1, PL + 1, dtype=np.float64)
+    gamma = _solve_bisect(lambda g: np.maximum(16.0, nmax * p ** -g).sum() - QL, 0.01, 6.0)
+    nl = np.maximum(16, np.round(nmax * p ** -gamma)).astype(np.int64)
+    N = MOANA_INSTANCES * scale
+    QI = MOANA_INSTANCED_QUADS * scale
+    wl = nl.astype(np.float64) ** -0.5
+    mL = (wl * nl).sum() / wl.sum()
+    mS = float(ns.mean())
+    NL = (QI - N * mS) / (mL - mS)
+    NL = float(np.clip(NL, PL, N - PS))
+    cl = np.maximum(1, np.round(NL * wl / wl.sum())).astype(np.int64)
+    ws = rng.uniform(0.5, 1.5, size=PS)
+    cs = np.maximum(1, np.round((N - NL) * ws / ws.sum())).astype(np.int64)
+    return np.concatenate([nl, ns]), np.concatenate([cl, cs]), terrain
+
+
+def moana_scene(scale: float = 1.0, seed_geom: int = SEED_GEOMETRY,
+                seed_inst: int = SEED_INSTANCES) -> Scene:
+    """Synthetic Moana-scale island: Zipf-sized prototypes (displaced grids and
+    closed blobs) instanced as clustered vegetation over a heightfield terrain
+    (Thomas cluster process), rotation about z with up to 15 degrees of tilt,
+    isotropic scale U(0.5, 2) times a size that grows with the prototype's
+    quad count.  scale < 1 shrinks every total proportionally."""
+    n, c, terrain_q = moana_sizes(scale, seed_geom)
+    extent = MOANA_EXTENT * (scale ** 0.5 if scale < 1.0 else 1.0)
+    rng = np.random.default_rng(seed_geom)
+    meshes = []
+    for k, nq in enumerate(n):
+        meshes.append(displaced_grid(rng, int(nq)) if k % 2 == 0 else noisy_blob(rng, int(nq)))
+    tq = int(round(terrain_q ** 0.5))
+    heights = terrain_heights(seed_geom + 7, tq, amplitude=220.0)
+    meshes.append(terrain_mesh(heights, extent))
+    terrain_id = len(meshes) - 1
+
+    rng = np.random.default_rng(seed_inst)
+    ids = np.repeat(np.arange(len(n), dtype=np.uint32), c)
+    rng.shuffle(ids)
+    N = ids.shape[0]
+    # Thomas cluster process: parents uniform, children Gaussian around them
+    n_par = max(1, N // 300)
+    par = rng.uniform(0.0, extent, size=(n_par, 2))
+    which = rng.integers(0, n_par, size=N)
+    xy = par[which] + rng.normal(0.0, extent / 400.0, size=(N, 2))
+    xy = np.clip(xy, 0.0, extent)
+    z = _terrain_height_at(heights, extent, xy[:, 0], xy[:, 1])
+    # rotation: tilt <= 15 degrees about a horizontal axis, then spin about z
+    phi = rng.uniform(0.0, 2 * math.pi, size=N)
+    tilt = np.radians(rng.uniform(0.0, 15.0, size=N))
+    ax = rng.uniform(0.0, 2 * math.pi, size=N)
+    size = 0.5 * (n[ids].astype(np.float64) / 16.0) ** 0.3 * rng.uniform(0.5, 2.0, size=N)
+    cz, sz = np.cos(phi), np.sin(phi)
+    ux, uy = np.cos(ax), np.sin(ax)
+    ct, st = np.cos(tilt), np.sin(tilt)
+    # Rodrigues rotation about (ux, uy, 0) by tilt
+    T = np.empty((N, 3, 3))
+    T[:, 0, 0] = ct + ux * ux * (1 - ct)
+    T[:, 0, 1] = ux * uy * (1 - ct)
+    T[:, 0, 2] = uy * st
+    T[:, 1, 0] = ux * uy * (1 - ct)
+    T[:, 1, 1] = ct + uy * uy * (1 - ct)
+    T[:, 1, 2] = -ux * st
+    T[:, 2, 0] = -uy * st
+    T[:, 2, 1] = ux * st
+    T[:, 2, 2] = ct
+    Z = np.zeros((N, 3, 3))
+    Z[:, 0, 0] = cz
+    Z[:, 0, 1] = -sz
+    Z[:, 1, 0] = sz
+    Z[:, 1, 1] = cz
+    Z[:, 2, 2] = 1.0
+    L = np.einsum("nij,njk->nik", T, Z) * size[:, None, None]
+    xf = pack_xforms(L, np.stack([xy[:, 0], xy[:, 1], z], axis=1))
+    xf = np.concatenate([xf, IDENTITY_XFORM[None]], axis=0)
+    ids = np.concatenate([ids, np.array([terrain_id], dtype=np.uint32)])
+    return Scene(meshes, xf, ids, name="moana",
+                 meta={"n_proto": int(len(n)), "terrain_mesh": terrain_id, "extent": extent,
+                       "instanced_quads": int((n[ids[:-1]]).sum()) + terrain_q})
+
+
+def moana_view(extent: float = MOANA_EXTENT, w: int = 1920, h: int = 1080, spp: int = 16) -> View:
+    return View(eye=(0.5 * extent, -0.07 * extent, 0.11 * extent),
+                look=(0.5 * extent, 0.45 * extent, 0.0), up=(0.0, 0.0, 1.0),
+                vfov_deg=50.0, w=w, h=h, spp=spp)
+
+
+def moana_params() -> Params:
+    return mid_params(max_depth=8)

@@ -176,6 +176,25 @@ def test_adjoint_modes_agree(api, tiny):
     torch.testing.assert_close(g1, g2, rtol=1e-5, atol=1e-7)
 
 
+def test_autotuner_choice_is_valid_and_changes_no_pixel(api, tiny, tmp_path):
+    from paper_2001_02620_gb300 import autotune
+    sc, gs, osc = tiny
+    view = I.tiny_view()
+    params = I.Params(max_depth=3, sun_dir=I.MID_SUN_DIR, sun_E=(3.0, 3.0, 3.0))
+    alb = torch.from_numpy(I.albedo(sc.n_quads)).cuda()
+    space = {"block": [64, 128], "stack": [32, 64], "occupancy": [16, 24], "batch": [1, 4]}
+    cache = str(tmp_path / "tune.json")
+    best = autotune.tune(gs, view, alb, params, space=space, reps=1, cache_path=cache,
+                         scene_name="tiny")
+    assert set(best) == set(space) and all(best[k] in space[k] for k in space)
+    assert autotune.tune(gs, view, alb, params, space=space, cache_path=cache,
+                         scene_name="tiny") == best  # served from the cache
+    ref = gs.render([view], alb, params)[0]
+    for cand in autotune.candidates(space):
+        assert torch.equal(gs.render([view], alb, params, tuning=cand)[0], ref)
+    gs.check()
+
+
 def test_white_furnace_gpu(api):
     v, q = I.sphere_mesh(24, 48, 5.0)
     sc = I.Scene([(v, q)], I.IDENTITY_XFORM[None].copy(), np.zeros(1, dtype=np.uint32))
