@@ -25,7 +25,33 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Mrays/s closest-hit & path samples/s, batched vs plain launch; adjoint/primal"
-STAT_WORDS = 6  # rays, nodes, quads, instance entries, fp64 re-tests, shading vertices
+# per kernel kind (closest-hit, then shadow): rays, nodes, quads, instance
+# entries, fp64 re-tests, shaded vertices
+STAT_WORDS = 12
+KERNEL_SOURCES = ["paper_2001_02620_gb300/csrc/traverse.cuh", "paper_2001_02620_gb300/csrc/wavefront.cu",
+                  "paper_2001_02620_gb300/csrc/qrt_layout.h", "paper_2001_02620_gb300/csrc/shading.cuh"]
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str):
+    """DRAM bytes per launch of the closest-hit trace kernel from the committed
+    ncu summary, if it was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None, None
+    e = d.get(workload)
+    if not e or e.get("kernel_source_hash") != kernel_source_hash():
+        return None, None
+    return float(e["dram_bytes_per_launch"]), e.get("kernel")
 
 
 def peaks():
@@ -175,7 +201,7 @@ def bench_trace(scene, sc, dev, tuning=None, eye=(2048.0, -300.0, 450.0)):
         d = torch.from_numpy(rays).to(dev)
         tc = _time(lambda: scene.trace_closest(d, hits, tuning=tuning), 5)
         ta = _time(lambda: scene.trace_any(d, bits, tuning=tuning), 5)
-        st = torch.zeros(STAT_WORDS, dtype=torch.int64, device=dev)
+        st = torch.zeros(6, dtype=torch.int64, device=dev)
         scene.trace_stats(d, False, hits, st)
         s = st.cpu().numpy()
         out[name] = {"closest_mrays_s": n / tc / 1e6, "any_mrays_s": n / ta / 1e6,
@@ -319,19 +345,23 @@ def main():
         tune_s = time.time() - t0
 
     def step():
-        scene.render([view], d_alb, params, outs=[img], tuning=tuning)
+        scene.render([view], d_alb, params, outs=[img], tuning=tuning, stage_times=True)
 
     # counters of one render (same launch configuration, counters added)
     stats = torch.zeros(STAT_WORDS, dtype=torch.int64, device=dev)
     scene.render([view], d_alb, params, outs=[img], stats=stats, tuning=tuning)
     scene.check()
-    st = stats.cpu().numpy()
-    rays, nodes, quads, insts, fallbacks, verts = [int(x) for x in st]
+    st = [int(x) for x in stats.cpu().numpy()]
+    c_rays, c_nodes, c_quads, c_insts, c_fb, verts = st[0:6]
+    s_rays, s_nodes, s_quads, s_insts, s_fb, _ = st[6:12]
+    rays, nodes, quads, insts, fallbacks = (c_rays + s_rays, c_nodes + s_nodes, c_quads + s_quads,
+                                            c_insts + s_insts, c_fb + s_fb)
     paths = view.w * view.h * view.spp
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    scene.stage_times(reset=True)
     if world > 1:
         dist.barrier()
     clocks = Clocks(local)
@@ -348,6 +378,7 @@ def main():
         dist.barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
     clk = clocks.stop()
+    stages = scene.stage_times(reset=True)
     scene.check()
     if world > 1:
         t = torch.tensor([ms], device=dev)
@@ -374,8 +405,17 @@ def main():
     e2e_ms = e0.elapsed_time(e1) / args.steps
 
     hbm, peak_kind = peaks()
-    alg_bytes = 64 * nodes + 48 * quads + 64 * insts + (12 + 48 + 64) * verts + 12 * view.w * view.h
-    achieved = alg_bytes / (ms * 1e-3) / 1e9
+    # algorithmic bytes: 64 B per node, 48 B per quad tested, 64 B per instance
+    # entry; per ray of the closest-hit kernel also 32 B ray + 4 B queue slot
+    # read and a 16 B hit written
+    closest_bytes = 64 * c_nodes + 48 * c_quads + 64 * c_insts + (32 + 4 + 16) * c_rays
+    shadow_bytes = 64 * s_nodes + 48 * s_quads + 64 * s_insts + (16 + 4 + 16 + 16) * s_rays
+    frame_bytes = closest_bytes + shadow_bytes + (12 + 48 + 64) * verts + 12 * view.w * view.h
+    tr_ms, tr_n = stages["trace_closest"]
+    tr_ms_step = tr_ms / args.steps
+    launches_step = tr_n / args.steps
+    achieved = closest_bytes / (tr_ms_step * 1e-3) / 1e9 if tr_ms_step > 0 else None
+    traffic, traffic_kernel = recorded_traffic(args.workload)
     value = world * rays / (ms * 1e-3) / 1e6
     line = {
         "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
@@ -387,15 +427,24 @@ def main():
                    "l2": f"working set {scene.stats['device_bytes'] / 1e9:.2f} GB > L2 (no flush)"},
         "path_samples_per_s": world * paths / (ms * 1e-3),
         "rays_per_step": rays, "paths_per_step": paths,
-        "counters": {"nodes": nodes, "quads": quads, "instance_entries": insts,
-                     "fp64_retests": fallbacks, "vertices": verts},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
-                     "peak_kind": peak_kind + " hbm_gbs (of " + peak_kind + ")"},
+        "counters": {"closest": {"rays": c_rays, "nodes": c_nodes, "quads": c_quads,
+                                 "instance_entries": c_insts, "fp64_retests": c_fb},
+                     "shadow": {"rays": s_rays, "nodes": s_nodes, "quads": s_quads,
+                                "instance_entries": s_insts, "fp64_retests": s_fb},
+                     "vertices": verts},
+        "roofline": {"bound": "hbm", "kernel": "wave_trace<closest> (closest-hit trace, "
+                     f"{launches_step:.0f} launches per step, {100 * tr_ms_step / ms:.1f}% of the step)",
+                     "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm if achieved else None,
+                     "traffic": traffic, "traffic_kernel": traffic_kernel,
+                     "algorithmic_bytes_per_launch": closest_bytes / max(1.0, launches_step),
+                     "peak_kind": f"{peak_kind} hbm_gbs ({'of measured' if peak_kind == 'measured' else 'of fallback'})",
+                     "frame_algorithmic_gbs": frame_bytes / (ms * 1e-3) / 1e9},
+        "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
         "e2e": {"value": world * rays / (e2e_ms * 1e-3) / 1e6, "unit": "Mrays/s",
                 "h2d_bytes_per_step": int(alb.nbytes), "d2h_bytes_per_step": int(img.numel() * 4),
                 "ms_per_step": e2e_ms},
-        "gpu_launches": args.steps,
+        "gpu_launches": int(sum(v[1] for v in stages.values())),
         "clocks": clk,
         "scene_build_s": build_s, "scene_gen_s": gen_s,
         "scene": {k: scene.stats[k] for k in ("n_quads", "n_instances", "blas_nodes", "tlas_nodes",
@@ -414,6 +463,8 @@ def main():
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = oracle_sample(sc, view, params, alb, budget_s=12.0,
                                              frame=f"{view.w}x{view.h} {args.workload}")
+    import resource
+    line["host_peak_rss_gb"] = resource.getrusage(resource.RUSAGE_SELF).ru_maxrss / 1e6
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -41,6 +41,9 @@ extern "C" {
 
 #define QRT_VERSION 1
 
+/* qrt_params.flags */
+#define QRT_FLAG_STAGE_TIMES 1u /* record GPU time of each wavefront stage (qrt_stage_times) */
+
 enum {
     QRT_OK = 0,
     QRT_ERR_INVALID_ARG = -1,    /* bad handle, NULL pointer, size or value */
@@ -108,7 +111,8 @@ typedef struct {
  *   batch          single kernel: pixels a warp claims per fetch, in units
  *                  of 32; wavefront: rays a lane claims per fetch
  *   stack          traversal stack entries per ray (32 or 64)
- *   fetch          node fetch width in bytes (16: 4x128-bit, 32: 2x256-bit loads)
+ *   fetch          node fetch width in bytes (16: 4x128-bit, 32: 2x256-bit
+ *                  loads, default)
  *   occupancy      trace kernels' register budget as resident warps per SM:
  *                  16 (up to 128 registers a thread, default) or 24 (up to 85)
  *   mode           renderer: 0 = default (wavefront), 1 = single persistent
@@ -275,6 +279,15 @@ int qrt_render_spp_stats(qrt_scene scene, const qrt_view* views, uint32_t n_view
                          unsigned long long* d_stats, qrt_stream stream);
 int qrt_trace_stats(qrt_scene scene, int any, const qrt_ray* d_rays, uint64_t n, void* d_out,
                     const qrt_tuning* tuning, unsigned long long* d_stats, qrt_stream stream);
+
+/* Per-stage GPU time of wavefront renders made with QRT_FLAG_STAGE_TIMES (the
+ * breakdown of the paper's Table 1): after waiting for the stream, writes the
+ * milliseconds and launch counts accumulated since the last reset for the
+ * stages 0 camera-ray generation, 1 closest-hit tracing, 2 shading,
+ * 3 shadow-ray tracing, 4 accumulation (ms[5], launches[5]); reset != 0
+ * starts a new accumulation.  Timers are per scene: time one stream at a
+ * time. */
+int qrt_stage_times(qrt_scene scene, qrt_stream stream, double* ms, uint32_t* launches, int reset);
 
 /* Wait for the stream, then read and clear the scene's device error word.
  * Returns QRT_OK, QRT_ERR_STACK_OVERFLOW, QRT_ERR_STEP_LIMIT or QRT_ERR_CUDA. */

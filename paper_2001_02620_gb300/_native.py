@@ -21,6 +21,9 @@ QRT_ERR_STACK_OVERFLOW = -5
 QRT_ERR_STEP_LIMIT = -6
 QRT_ERR_NOT_READY = -7
 
+QRT_FLAG_STAGE_TIMES = 1
+STAGES = ("gen", "trace_closest", "shade", "trace_shadow", "accumulate")
+
 ERROR_NAMES = {
     QRT_ERR_INVALID_ARG: "QRT_ERR_INVALID_ARG", QRT_ERR_ALIGN: "QRT_ERR_ALIGN",
     QRT_ERR_OOM: "QRT_ERR_OOM", QRT_ERR_CUDA: "QRT_ERR_CUDA",
@@ -93,6 +96,7 @@ SIGNATURES = {
     "qrt_render_spp_stats": (_i, [_vp, C.POINTER(qrt_view), _u32, _vp, C.POINTER(qrt_params),
                                   _vp, _vp]),
     "qrt_trace_stats": (_i, [_vp, _i, _vp, _u64, _vp, C.POINTER(qrt_tuning), _vp, _vp]),
+    "qrt_stage_times": (_i, [_vp, _vp, C.POINTER(C.c_double), C.POINTER(C.c_uint32), _i]),
     "qrt_check": (_i, [_vp, _vp]),
     "qrt_blas_build_check": (_i, [C.POINTER(qrt_mesh), C.POINTER(qrt_build_opts),
                                   C.POINTER(C.c_uint64), C.POINTER(C.c_uint32)]),

@@ -29,9 +29,10 @@ def make_tuning(tuning: dict | None) -> N.qrt_tuning:
 
 
 def make_params(p: Params, tuning: dict | None = None, path_log: torch.Tensor | None = None,
-                max_steps: int = 0) -> N.qrt_params:
+                max_steps: int = 0, stage_times: bool = False) -> N.qrt_params:
     cp = N.qrt_params()
     cp.max_depth = int(p.max_depth)
+    cp.flags = N.QRT_FLAG_STAGE_TIMES if stage_times else 0
     cp.seed = int(p.seed)
     cp.env[:] = [float(x) for x in p.env]
     cp.sun_dir[:] = [float(x) for x in p.sun_dir]
@@ -138,7 +139,8 @@ class Scene:
     # -- rendering -----------------------------------------------------------
     def render(self, views, albedo: torch.Tensor, params: Params, outs=None,
                tuning: dict | None = None, path_log: torch.Tensor | None = None,
-               max_steps: int = 0, stats: torch.Tensor | None = None, stream=None):
+               max_steps: int = 0, stats: torch.Tensor | None = None, stream=None,
+               stage_times: bool = False):
         """Renders views (list of inputs.View) into float32 [h, w, 3] tensors."""
         if isinstance(views, View):
             views = [views]
@@ -146,7 +148,7 @@ class Scene:
             outs = [torch.empty((v.h, v.w, 3), dtype=torch.float32, device=albedo.device)
                     for v in views]
         cv = make_views(views, outs)
-        cp = make_params(params, tuning, path_log, max_steps)
+        cp = make_params(params, tuning, path_log, max_steps, stage_times)
         L = N.lib()
         if stats is None:
             N.check(L.qrt_render_spp(self.handle, cv, len(views), _ptr(albedo), C.byref(cp),
@@ -167,6 +169,13 @@ class Scene:
         N.check(N.lib().qrt_render_adjoint(self.handle, cv, len(views), _ptr(albedo), dptr,
                                            _ptr(grad), C.byref(cp), _stream(stream)))
         return grad
+
+    def stage_times(self, reset: bool = True, stream=None) -> dict:
+        """{stage: (total ms, launches)} of renders made with stage_times=True."""
+        ms = (C.c_double * 5)()
+        n = (C.c_uint32 * 5)()
+        N.check(N.lib().qrt_stage_times(self.handle, _stream(stream), ms, n, 1 if reset else 0))
+        return {name: (ms[k], n[k]) for k, name in enumerate(N.STAGES)}
 
     def check(self, stream=None) -> None:
         """Raises QrtError if a kernel flagged a stack overflow or step limit."""

@@ -46,6 +46,68 @@ constexpr size_t kSlotStride = 128;  // bytes between counters (own cache line)
 
 }  // namespace
 
+// CUDA events around each wavefront stage launch, accumulated per stage
+// until read by qrt_stage_times (one stream at a time per scene).
+struct StageTimer : StageHook {
+    struct Rec {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::mutex mu;
+    std::vector<cudaEvent_t> pool;
+    std::vector<Rec> done;
+    Rec open[kStages] = {};
+
+    cudaEvent_t take() {
+        cudaEvent_t e = nullptr;
+        if (!pool.empty()) {
+            e = pool.back();
+            pool.pop_back();
+        } else {
+            cudaEventCreate(&e);
+        }
+        return e;
+    }
+    void begin(int stage, cudaStream_t s) override {
+        std::lock_guard<std::mutex> g(mu);
+        open[stage] = Rec{stage, take(), nullptr};
+        cudaEventRecord(open[stage].a, s);
+    }
+    void end(int stage, cudaStream_t s) override {
+        std::lock_guard<std::mutex> g(mu);
+        Rec r = open[stage];
+        r.b = take();
+        cudaEventRecord(r.b, s);
+        done.push_back(r);
+    }
+    void read(double* ms, uint32_t* n, bool reset) {
+        std::lock_guard<std::mutex> g(mu);
+        for (int k = 0; k < kStages; ++k) {
+            ms[k] = 0.0;
+            n[k] = 0;
+        }
+        for (const Rec& r : done) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) ms[r.stage] += t;
+            n[r.stage]++;
+        }
+        if (reset) {
+            for (const Rec& r : done) {
+                pool.push_back(r.a);
+                pool.push_back(r.b);
+            }
+            done.clear();
+        }
+    }
+    ~StageTimer() override {
+        for (const Rec& r : done) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    }
+};
+
 // Scratch of one stream: a work counter for the single-kernel renderer and
 // the wavefront workspace (grown on demand, outside stream capture).
 struct StreamSlot {
@@ -70,6 +132,7 @@ struct qrt_scene_s {
     std::vector<StreamSlot> slots;
     int next_slot = 0;
     qrt_scene_stats stats{};
+    StageTimer timer;
 
     // Calls on one stream are ordered, so they may share scratch; different
     // streams get different slots (up to kCounterSlots, then reused).
@@ -609,7 +672,8 @@ int wave_enqueue(qrt_scene scene, const qrt_view* views, uint32_t n_views, const
             paths += (uint64_t)views[first + k].w * views[first + k].h * views[first + k].spp;
         }
         W.n_views = cnt;
-        cudaError_t e = launch_wave(W, t, scene->sm_count, s);
+        StageHook* hook = (params && (params->flags & QRT_FLAG_STAGE_TIMES)) ? &scene->timer : nullptr;
+        cudaError_t e = launch_wave(W, t, scene->sm_count, s, hook);
         if (e != cudaSuccess) rc = cuda_fail(e, "wavefront launch");
     }
     return rc;
@@ -875,6 +939,14 @@ int qrt_graph_destroy(qrt_graph graph) {
     cudaFree(graph->d_counter);
     cudaFree(graph->ws);
     delete graph;
+    return QRT_OK;
+}
+
+int qrt_stage_times(qrt_scene scene, qrt_stream stream, double* ms, uint32_t* launches, int reset) {
+    if (!scene || !ms || !launches) return fail(QRT_ERR_INVALID_ARG, "NULL argument");
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    scene->timer.read(ms, launches, reset != 0);
     return QRT_OK;
 }
 

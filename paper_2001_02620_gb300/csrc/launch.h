@@ -14,7 +14,7 @@ struct Tune {
     int blocks_per_sm = 0;  // 0 = occupancy maximum
     int batch = 1;          // 32-item groups a warp claims per fetch
     int stack = 64;         // 32 or 64
-    int fetch = 16;         // 16 or 32
+    int fetch = 32;         // node fetch bytes per load: 16 or 32
     int occupancy = 16;     // trace kernels: target resident warps per SM (16 or 24)
     int mode = 2;           // 1 = single persistent kernel, 2 = wavefront
     int chunk_log2 = 21;    // wavefront paths per chunk = 2^chunk_log2

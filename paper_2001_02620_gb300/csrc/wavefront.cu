@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(256, MINB) wave_trace(const __grid_constant__ 
     };
     persistent_trace<ANY, STACK, FETCH>(A.S, T, st, fetch_ray, finish_ray);
     if (err) atomicOr(A.S.err, err);
-    if (A.stats) add_stats(A.stats, st);
+    if (A.stats) add_stats(A.stats + (ANY ? 6 : 0), st);
 }
 
 // Shade stage of depth i (1-based).  replay = false: primal; true: replay
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(256) wave_shade(const __grid_constant__ WaveAr
         A.B.ray_d[j] = make_float4(nd.x, nd.y, nd.z, kInfF);
         push(A.B.q[(depth + 1) & 1], A.B.ctr + kCtrStride * (depth + 1) + kCtrClosest, j);
     }
-    if (A.stats) atomicAdd(A.stats + 5, 1ull);
+    if (A.stats) atomicAdd(A.stats + 5, 1ull);  // shaded vertices (closest-hit counters)
 }
 
 // Mean over each pixel's samples (in sample order) for items [I0, I0 + n).
@@ -323,24 +323,35 @@ cudaError_t static_workspace(void** ptr) {
 
 // One pass over paths [P0, P0 + n) of the launch.
 static cudaError_t wave_pass(WaveArgs& A, uint64_t P0, uint32_t n, int replay, const Tune& t,
-                             int sm_count, cudaStream_t s) {
+                             int sm_count, cudaStream_t s, StageHook* hook) {
     A.P0 = P0;
     cudaError_t e = cudaMemsetAsync(A.B.ctr, 0, sizeof(uint32_t) * kCtrStride * (A.P.max_depth + 2), s);
     if (e != cudaSuccess) return e;
+    if (hook) hook->begin(kStageGen, s);
     wave_gen<<<(n + 255) / 256, 256, 0, s>>>(A, P0, n);
+    if (hook) hook->end(kStageGen, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     for (uint32_t i = 1; i <= A.P.max_depth; ++i) {
-        if ((e = launch_wave_trace<false>(A, (int)i, t, sm_count, s)) != cudaSuccess) return e;
+        if (hook) hook->begin(kStageTrace, s);
+        e = launch_wave_trace<false>(A, (int)i, t, sm_count, s);
+        if (hook) hook->end(kStageTrace, s);
+        if (e != cudaSuccess) return e;
+        if (hook) hook->begin(kStageShade, s);
         wave_shade<<<(n + 255) / 256, 256, 0, s>>>(A, (int)i, replay);
+        if (hook) hook->end(kStageShade, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (A.P.sun_on) {
-            if ((e = launch_wave_trace<true>(A, (int)i, t, sm_count, s)) != cudaSuccess) return e;
+            if (hook) hook->begin(kStageShadow, s);
+            e = launch_wave_trace<true>(A, (int)i, t, sm_count, s);
+            if (hook) hook->end(kStageShadow, s);
+            if (e != cudaSuccess) return e;
         }
     }
     return cudaSuccess;
 }
 
-cudaError_t launch_wave(WaveArgs& A, const Tune& t, int sm_count, cudaStream_t s) {
+cudaError_t launch_wave(WaveArgs& A, const Tune& t, int sm_count, cudaStream_t s,
+                        StageHook* hook) {
     // chunks of at most A.capacity paths, cut at pixel boundaries
     uint64_t P_total = 0;
     for (uint32_t v = 0; v < A.n_views; ++v)
@@ -360,13 +371,13 @@ cudaError_t launch_wave(WaveArgs& A, const Tune& t, int sm_count, cudaStream_t s
         }
         const uint32_t n = (uint32_t)(P1 - P0);
         if (A.grad) {
-            if ((e = wave_pass(A, P0, n, 0, t, sm_count, s)) != cudaSuccess) return e;
+            if ((e = wave_pass(A, P0, n, 0, t, sm_count, s, hook)) != cudaSuccess) return e;
             // radiance of pass one becomes Ltot; L restarts at zero in the replay
             e = cudaMemcpyAsync(A.B.Ltot, A.B.L, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s);
             if (e != cudaSuccess) return e;
-            if ((e = wave_pass(A, P0, n, 1, t, sm_count, s)) != cudaSuccess) return e;
+            if ((e = wave_pass(A, P0, n, 1, t, sm_count, s, hook)) != cudaSuccess) return e;
         } else {
-            if ((e = wave_pass(A, P0, n, 0, t, sm_count, s)) != cudaSuccess) return e;
+            if ((e = wave_pass(A, P0, n, 0, t, sm_count, s, hook)) != cudaSuccess) return e;
             // pixels of this chunk: items whose paths lie in [P0, P1)
             int v0 = 0;
             for (int v = 0; v < (int)A.n_views; ++v)
@@ -381,7 +392,9 @@ cudaError_t launch_wave(WaveArgs& A, const Tune& t, int sm_count, cudaStream_t s
                 I1 = V1.item_begin + (P1 - V1.path_begin) / V1.spp;
             }
             const uint32_t ni = (uint32_t)(I1 - I0);
+            if (hook) hook->begin(kStageAccum, s);
             wave_accumulate<<<(ni + 255) / 256, 256, 0, s>>>(A, I0, ni);
+            if (hook) hook->end(kStageAccum, s);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
         P0 = P1;

@@ -31,6 +31,15 @@ struct WaveBufs {
     uint32_t* ctr;   // kCtrStride words per depth 0..max_depth+1
 };
 
+// Host-side hook around each stage launch (stage timers); may be null.
+enum Stage { kStageGen = 0, kStageTrace = 1, kStageShade = 2, kStageShadow = 3, kStageAccum = 4,
+             kStages = 5 };
+struct StageHook {
+    virtual void begin(int stage, cudaStream_t s) = 0;
+    virtual void end(int stage, cudaStream_t s) = 0;
+    virtual ~StageHook() {}
+};
+
 struct WaveArgs {
     DevScene S;
     const float* albedo;
@@ -62,6 +71,7 @@ constexpr size_t kStaticWorkspaceBytes = wave_workspace_bytes(1ull << kStaticChu
 // device with cudaGetSymbolAddress; allocates nothing).
 cudaError_t static_workspace(void** ptr);
 void wave_carve(void* base, uint64_t capacity, bool adjoint, WaveBufs& B);
-cudaError_t launch_wave(WaveArgs& A, const Tune& t, int sm_count, cudaStream_t s);
+cudaError_t launch_wave(WaveArgs& A, const Tune& t, int sm_count, cudaStream_t s,
+                        StageHook* hook = nullptr);
 
 }  // namespace qrt

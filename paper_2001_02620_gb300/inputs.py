@@ -13,8 +13,8 @@ seed 2, albedo seed 3, render seed 4):
   environment light only.
 * ``mid``   -- 64 prototypes (half displaced grids, half closed noisy blobs)
   with log-uniform quad counts in [2^12, 2^16], a 2048x2048-quad heightfield
-  terrain, 100k random affine instances standing on the terrain,
-  1024x1024, 4 spp, depth 5, environment plus a directional sun.
+  terrain in 8x8 tiles, 100k random affine instances standing on the
+  terrain, 1024x1024, 4 spp, depth 5, environment plus a directional sun.
 * ``batched`` -- 32 views of the mid scene with uneven resolution and spp.
 * ``adjoint`` -- the mid scene at 512x512, 8 spp, depth 4, plus a perturbed
   target albedo.
@@ -275,6 +275,30 @@ def terrain_mesh(heights: np.ndarray, extent: float):
     return verts, grid_quads(n, n)
 
 
+def terrain_tiles(heights: np.ndarray, extent: float, tiles: int = 8):
+    """The heightfield as tiles x tiles meshes, each in coordinates local to
+    its tile centre, with the instance translations that put them back.  The
+    grid spacing and tile size are powers of two, so every local coordinate
+    and translation is exact and the world-space vertices equal those of
+    terrain_mesh() bit for bit."""
+    n = heights.shape[0] - 1
+    assert n % tiles == 0
+    k = n // tiles
+    step = extent / n
+    meshes, trans = [], []
+    for j in range(tiles):
+        for i in range(tiles):
+            h = heights[j * k:(j + 1) * k + 1, i * k:(i + 1) * k + 1]
+            cx = (i + 0.5) * k * step
+            cy = (j + 0.5) * k * step
+            xs = (np.arange(k + 1) - 0.5 * k) * step
+            X, Y = np.meshgrid(xs, xs, indexing="xy")
+            verts = np.stack([X.ravel(), Y.ravel(), h.ravel()], axis=1).astype(np.float32)
+            meshes.append((verts, grid_quads(k, k)))
+            trans.append((cx, cy, 0.0))
+    return meshes, np.asarray(trans)
+
+
 def _terrain_height_at(heights: np.ndarray, extent: float, x, y):
     n = heights.shape[0] - 1
     gx = np.clip(x / extent * n, 0, n - 1e-9)
@@ -299,8 +323,9 @@ def mid_scene(seed_geom: int = SEED_GEOMETRY, seed_inst: int = SEED_INSTANCES,
         nq = int(round(2.0 ** rng.uniform(12.0, 16.0)))
         meshes.append(displaced_grid(rng, nq) if p % 2 == 0 else noisy_blob(rng, nq))
     heights = terrain_heights(seed_geom, terrain_quads)
-    meshes.append(terrain_mesh(heights, extent))
-    terrain_id = len(meshes) - 1
+    tiles, tile_t = terrain_tiles(heights, extent)
+    terrain_first = len(meshes)
+    meshes.extend(tiles)
 
     rng = np.random.default_rng(seed_inst)
     R = random_rotations(rng, n_inst)
@@ -312,10 +337,11 @@ def mid_scene(seed_geom: int = SEED_GEOMETRY, seed_inst: int = SEED_INSTANCES,
     z = _terrain_height_at(heights, extent, x, y)
     xf = pack_xforms(L, np.stack([x, y, z], axis=1))
     ids = rng.integers(0, n_proto, size=n_inst).astype(np.uint32)
-    xf = np.concatenate([xf, IDENTITY_XFORM[None]], axis=0)
-    ids = np.concatenate([ids, np.array([terrain_id], dtype=np.uint32)])
+    nt = len(tiles)
+    xf = np.concatenate([xf, pack_xforms(np.broadcast_to(np.eye(3), (nt, 3, 3)), tile_t)], axis=0)
+    ids = np.concatenate([ids, np.arange(terrain_first, terrain_first + nt, dtype=np.uint32)])
     return Scene(meshes, xf, ids, name="mid",
-                 meta={"n_proto": n_proto, "terrain_mesh": terrain_id, "extent": extent})
+                 meta={"n_proto": n_proto, "terrain_meshes": (terrain_first, nt), "extent": extent})
 
 
 def mid_view(w: int = 1024, h: int = 1024, spp: int = 4) -> View:
@@ -541,8 +567,10 @@ def moana_scene(scale: float = 1.0, seed_geom: int = SEED_GEOMETRY,
         meshes.append(displaced_grid(rng, int(nq)) if k % 2 == 0 else noisy_blob(rng, int(nq)))
     tq = int(round(terrain_q ** 0.5))
     heights = terrain_heights(seed_geom + 7, tq, amplitude=220.0)
-    meshes.append(terrain_mesh(heights, extent))
-    terrain_id = len(meshes) - 1
+    ntile = 8 if tq % 8 == 0 else 1
+    tiles, tile_t = terrain_tiles(heights, extent, ntile)
+    terrain_first = len(meshes)
+    meshes.extend(tiles)
 
     rng = np.random.default_rng(seed_inst)
     ids = np.repeat(np.arange(len(n), dtype=np.uint32), c)
@@ -582,11 +610,13 @@ def moana_scene(scale: float = 1.0, seed_geom: int = SEED_GEOMETRY,
     Z[:, 2, 2] = 1.0
     L = np.einsum("nij,njk->nik", T, Z) * size[:, None, None]
     xf = pack_xforms(L, np.stack([xy[:, 0], xy[:, 1], z], axis=1))
-    xf = np.concatenate([xf, IDENTITY_XFORM[None]], axis=0)
-    ids = np.concatenate([ids, np.array([terrain_id], dtype=np.uint32)])
+    nt = len(tiles)
+    inst_q = int(n[ids].sum()) + terrain_q
+    xf = np.concatenate([xf, pack_xforms(np.broadcast_to(np.eye(3), (nt, 3, 3)), tile_t)], axis=0)
+    ids = np.concatenate([ids, np.arange(terrain_first, terrain_first + nt, dtype=np.uint32)])
     return Scene(meshes, xf, ids, name="moana",
-                 meta={"n_proto": int(len(n)), "terrain_mesh": terrain_id, "extent": extent,
-                       "instanced_quads": int((n[ids[:-1]]).sum()) + terrain_q})
+                 meta={"n_proto": int(len(n)), "terrain_meshes": (terrain_first, nt),
+                       "extent": extent, "instanced_quads": inst_q})
 
 
 def moana_view(extent: float = MOANA_EXTENT, w: int = 1920, h: int = 1080, spp: int = 16) -> View:
