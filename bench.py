@@ -357,6 +357,9 @@ def main():
     rays, nodes, quads, insts, fallbacks = (c_rays + s_rays, c_nodes + s_nodes, c_quads + s_quads,
                                             c_insts + s_insts, c_fb + s_fb)
     paths = view.w * view.h * view.spp
+    # L2 read bandwidth of this GPU (a 64 MB L2-resident buffer swept 40
+    # times with L2-only loads): the second roofline denominator
+    l2_gbs = api.read_bandwidth_gbs(64 << 20, 40)
 
     for _ in range(args.warmup):
         step()
@@ -439,6 +442,8 @@ def main():
                      "traffic": traffic, "traffic_kernel": traffic_kernel,
                      "algorithmic_bytes_per_launch": closest_bytes / max(1.0, launches_step),
                      "peak_kind": f"{peak_kind} hbm_gbs ({'of measured' if peak_kind == 'measured' else 'of fallback'})",
+                     "l2_read_gbs": l2_gbs, "l2_frac": achieved / l2_gbs if achieved else None,
+                     "l2_kind": "measured here: qrt_read_bandwidth over a 64 MB buffer, 40 sweeps",
                      "frame_algorithmic_gbs": frame_bytes / (ms * 1e-3) / 1e9},
         "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
         "e2e": {"value": world * rays / (e2e_ms * 1e-3) / 1e6, "unit": "Mrays/s",

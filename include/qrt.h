@@ -114,7 +114,9 @@ typedef struct {
  *   fetch          node fetch width in bytes (16: 4x128-bit, 32: 2x256-bit
  *                  loads, default)
  *   occupancy      trace kernels' register budget as resident warps per SM:
- *                  16 (up to 128 registers a thread, default) or 24 (up to 85)
+ *                  16 (up to 128 registers a thread), 24 (80) or 32 (64,
+ *                  default; more warps hide the latency of the dependent
+ *                  node loads better than the spills they cost)
  *   mode           renderer: 0 = default (wavefront), 1 = single persistent
  *                  kernel (a lane renders whole pixels), 2 = wavefront (stages
  *                  gen / trace / shade / shadow / accumulate over queues; a
@@ -288,6 +290,16 @@ int qrt_trace_stats(qrt_scene scene, int any, const qrt_ray* d_rays, uint64_t n,
  * starts a new accumulation.  Timers are per scene: time one stream at a
  * time. */
 int qrt_stage_times(qrt_scene scene, qrt_stream stream, double* ms, uint32_t* launches, int reset);
+
+/* Measurement helper with no counterpart in the paper: reads the DEVICE
+ * buffer d_buf (16-byte aligned, bytes a multiple of 16) reps times with
+ * L2-only 16-byte loads on the current device, XOR-folding the data into
+ * *d_sink (DEVICE uint32, its value meaningless).  Timed by the caller on
+ * the stream; with a buffer that fits in L2 it gives the L2 read bandwidth
+ * that bounds traversal of a cache-resident BVH.  bytes = 0 or reps = 0 is a
+ * no-op. */
+int qrt_read_bandwidth(const void* d_buf, uint64_t bytes, uint32_t reps, uint32_t* d_sink,
+                       qrt_stream stream);
 
 /* Wait for the stream, then read and clear the scene's device error word.
  * Returns QRT_OK, QRT_ERR_STACK_OVERFLOW, QRT_ERR_STEP_LIMIT or QRT_ERR_CUDA. */

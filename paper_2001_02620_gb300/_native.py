@@ -89,6 +89,7 @@ SIGNATURES = {
     "qrt_render_adjoint": (_i, [_vp, C.POINTER(qrt_view), _u32, _vp, C.POINTER(_vp), _vp,
                                 C.POINTER(qrt_params), _vp]),
     "qrt_l2_loss": (_i, [_vp, _vp, _u64, _vp, _vp, _vp]),
+    "qrt_read_bandwidth": (_i, [_vp, _u64, _u32, _vp, _vp]),
     "qrt_render_graph_create": (_i, [_vp, C.POINTER(qrt_view), _u32, _vp, C.POINTER(qrt_params),
                                      C.POINTER(_vp)]),
     "qrt_graph_launch": (_i, [_vp, _vp]),

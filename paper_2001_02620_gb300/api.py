@@ -217,6 +217,24 @@ class RenderGraph:
             pass
 
 
+def read_bandwidth_gbs(nbytes: int, reps: int, stream=None) -> float:
+    """GB/s of repeated L2-only reads over a fresh device buffer of nbytes
+    (qrt_read_bandwidth, timed with CUDA events on the stream).  With nbytes
+    well inside L2 this is the L2 read bandwidth."""
+    buf = torch.zeros(nbytes // 4, dtype=torch.int32, device="cuda")
+    sink = torch.zeros(1, dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream() if stream is None else stream
+    L = N.lib()
+    N.check(L.qrt_read_bandwidth(_ptr(buf), buf.numel() * 4, 2, _ptr(sink), _stream(s)))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    N.check(L.qrt_read_bandwidth(_ptr(buf), buf.numel() * 4, reps, _ptr(sink), _stream(s)))
+    e1.record(s)
+    e1.synchronize()
+    return buf.numel() * 4 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
+
 def l2_loss(img: torch.Tensor, target: torch.Tensor, dimage: torch.Tensor | None = None,
             stream=None):
     """Mean squared error (FP64 scalar tensor) and, if given, its gradient into dimage."""

@@ -26,7 +26,7 @@ SPACE = {
     "block": [64, 128, 256],
     "fetch": [16, 32],
     "batch": [1, 4],
-    "occupancy": [16, 24],
+    "occupancy": [16, 24, 32],
 }
 
 
@@ -76,8 +76,12 @@ def pick_best(timings: dict) -> tuple[str, float]:
     return k, ok[k]
 
 
-def proxy_view(view, max_side: int = 384):
-    s = min(1.0, max_side / max(view.w, view.h))
+def proxy_view(view, max_paths: int = 1 << 22):
+    """The view scaled down (same aspect and spp) to at most max_paths paths.
+    The proxy must still fill the GPU several times over: with a small one
+    the launch tail dominates and the tuner prefers the wrong occupancy."""
+    paths = view.w * view.h * view.spp
+    s = min(1.0, (max_paths / paths) ** 0.5)
     return dataclasses.replace(view, w=max(32, int(view.w * s)), h=max(32, int(view.h * s)))
 
 

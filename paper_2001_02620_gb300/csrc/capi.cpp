@@ -213,8 +213,8 @@ int validate_tuning(const Tune& t) {
     if (t.batch < 1 || t.batch > 64) return fail(QRT_ERR_INVALID_ARG, "tuning.batch must be 1..64");
     if (t.blocks_per_sm < 0 || t.blocks_per_sm > 32)
         return fail(QRT_ERR_INVALID_ARG, "tuning.blocks_per_sm must be 0..32");
-    if (t.occupancy != 16 && t.occupancy != 24)
-        return fail(QRT_ERR_INVALID_ARG, "tuning.occupancy must be 0, 16 or 24");
+    if (t.occupancy != 16 && t.occupancy != 24 && t.occupancy != 32)
+        return fail(QRT_ERR_INVALID_ARG, "tuning.occupancy must be 0, 16, 24 or 32");
     if (t.mode < 1 || t.mode > 2) return fail(QRT_ERR_INVALID_ARG, "tuning.mode must be 0, 1 or 2");
     if (t.chunk_log2 < 10 || t.chunk_log2 > 26)
         return fail(QRT_ERR_INVALID_ARG, "tuning.chunk_log2 must be 10..26");
@@ -866,6 +866,22 @@ int qrt_l2_loss(const float* d_img, const float* d_target, uint64_t n, double* d
     cudaError_t e = launch_l2_loss(d_img, d_target, n, d_loss, d_dimage,
                                    reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "loss launch");
+    return QRT_OK;
+}
+
+int qrt_read_bandwidth(const void* d_buf, uint64_t bytes, uint32_t reps, uint32_t* d_sink,
+                       qrt_stream stream) {
+    if (bytes == 0 || reps == 0) return QRT_OK;
+    if (!d_buf || !d_sink) return fail(QRT_ERR_INVALID_ARG, "NULL buffer");
+    if (!aligned(d_buf, 16) || bytes % 16 != 0)
+        return fail(QRT_ERR_ALIGN, "d_buf must be 16-byte aligned and bytes a multiple of 16");
+    if (!aligned(d_sink, 4)) return fail(QRT_ERR_ALIGN, "d_sink must be 4-byte aligned");
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = launch_read_sweep(d_buf, bytes, reps, d_sink, sms, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "read sweep launch");
     return QRT_OK;
 }
 

@@ -9,13 +9,17 @@
 namespace qrt {
 
 // Resolved launch configuration.
+// Register budget per thread that lets `warps` warps reside on one SM
+// (65,536 registers per SM, allocated in multiples of 8 per thread).
+constexpr int occupancy_regs(int warps) { return (65536 / (32 * warps)) & ~7; }
+
 struct Tune {
     int block = 128;
     int blocks_per_sm = 0;  // 0 = occupancy maximum
     int batch = 1;          // 32-item groups a warp claims per fetch
     int stack = 64;         // 32 or 64
     int fetch = 32;         // node fetch bytes per load: 16 or 32
-    int occupancy = 16;     // trace kernels: target resident warps per SM (16 or 24)
+    int occupancy = 32;     // trace kernels: target resident warps per SM (16, 24 or 32)
     int mode = 2;           // 1 = single persistent kernel, 2 = wavefront
     int chunk_log2 = 21;    // wavefront paths per chunk = 2^chunk_log2
 };
@@ -70,6 +74,8 @@ constexpr int kStatsWords = 6;
 // A.counter must be zero when the kernel starts.
 cudaError_t launch_render(const RenderArgs& A, const Tune& t, int sm_count, cudaStream_t s);
 
+cudaError_t launch_read_sweep(const void* buf, uint64_t bytes, uint32_t reps, uint32_t* sink,
+                              int sm_count, cudaStream_t s);
 cudaError_t launch_l2_loss(const float* img, const float* target, uint64_t n, double* loss,
                            float* dimage, cudaStream_t s);
 

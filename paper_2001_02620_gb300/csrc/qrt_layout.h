@@ -84,4 +84,8 @@ struct DevScene {
 constexpr uint32_t kErrStackOverflow = 1u;
 constexpr uint32_t kErrStepLimit = 2u;
 
+// Traversal stack entries per ray allocated by the ray-query and wavefront
+// trace kernels; tuning.stack caps how many a ray may use (32 or 64).
+constexpr int kMaxStack = 64;
+
 }  // namespace qrt

@@ -7,14 +7,16 @@
 
 namespace qrt {
 
-template <bool ANY, int STACK, int FETCH, int MINB>
-__global__ void __launch_bounds__(256, MINB) trace_kernel(const DevScene S, const float4* __restrict__ rays,
+// Work counters are kept only in the STATS variant (dead code elsewhere).
+template <bool ANY, int FETCH, int OCC, bool STATS>
+__global__ void __maxnreg__(occupancy_regs(OCC)) trace_kernel(const DevScene S, const float4* __restrict__ rays,
                                                        uint64_t n, uint4* __restrict__ hits,
                                                        uint32_t* __restrict__ occ, uint32_t max_steps,
                                                        unsigned long long* cursor, uint32_t batch,
-                                                       unsigned long long* stats) {
+                                                       unsigned long long* stats, int stack_cap) {
     TraceStats st{0, 0, 0, 0, 0, 0};
-    Traversal<ANY, STACK, FETCH> T;
+    Traversal<ANY, kMaxStack, FETCH> T;
+    T.cap = stack_cap;
     uint64_t next = 0, end = 0, i = 0;
     uint32_t err = 0;
     uint64_t bad = ~0ull;
@@ -43,30 +45,30 @@ __global__ void __launch_bounds__(256, MINB) trace_kernel(const DevScene S, cons
             hits[i] = make_uint4(__float_as_uint(T.h.t), T.h.inst, T.h.prim, uv);
         }
     };
-    persistent_trace<ANY, STACK, FETCH>(S, T, st, fetch_ray, finish_ray);
+    persistent_trace<ANY, kMaxStack, FETCH>(S, T, st, fetch_ray, finish_ray);
     if (err) {
         atomicOr(S.err, err);
         atomicMin(S.err + 1, (uint32_t)min(bad, (uint64_t)0xFFFFFFFEu));
     }
-    if (stats) add_stats(stats, st);
+    if constexpr (STATS) add_stats(stats, st);
 }
 
-template <bool ANY, int STACK, int FETCH, int MINB>
+template <bool ANY, int FETCH, int OCC, bool STATS>
 static cudaError_t launch_variant(const DevScene& S, const float4* rays, uint64_t n, uint4* hits,
                                   uint32_t* occ, uint32_t max_steps, unsigned long long* cursor,
                                   unsigned long long* stats, const Tune& t, int sm_count,
                                   cudaStream_t s) {
     int per_sm = t.blocks_per_sm;
     if (per_sm <= 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel<ANY, STACK, FETCH, MINB>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel<ANY, FETCH, OCC, STATS>,
                                                       t.block, 0);
         if (per_sm < 1) per_sm = 1;
     }
     uint64_t grid = (uint64_t)sm_count * per_sm;
     const uint64_t want = (n + (uint64_t)t.block - 1) / (uint64_t)t.block;
     if (want < grid) grid = want;
-    trace_kernel<ANY, STACK, FETCH, MINB><<<(unsigned)grid, t.block, 0, s>>>(
-        S, rays, n, hits, occ, max_steps, cursor, (uint32_t)t.batch, stats);
+    trace_kernel<ANY, FETCH, OCC, STATS><<<(unsigned)grid, t.block, 0, s>>>(
+        S, rays, n, hits, occ, max_steps, cursor, (uint32_t)t.batch, stats, t.stack);
     return cudaGetLastError();
 }
 
@@ -77,18 +79,21 @@ static cudaError_t launch_any_variant(const DevScene& S, const void* rays, uint6
                                       cudaStream_t s) {
     const float4* r = static_cast<const float4*>(rays);
     uint4* hp = static_cast<uint4*>(hits);
-    const bool s32 = t.stack <= 32, f32 = t.fetch == 32, o24 = t.occupancy == 24;
-#define QRT_TV(ST, FE, MB) \
-    return launch_variant<ANY, ST, FE, MB>(S, r, n, hp, occ, max_steps, cursor, stats, t, sm_count, s)
-    if (o24) {
-        if (s32) { if (f32) QRT_TV(32, 32, 3); QRT_TV(32, 16, 3); }
-        if (f32) QRT_TV(64, 32, 3);
-        QRT_TV(64, 16, 3);
+    const bool st = stats != nullptr, f32 = t.fetch == 32;
+#define QRT_TV(FE, OC, ST) \
+    return launch_variant<ANY, FE, OC, ST>(S, r, n, hp, occ, max_steps, cursor, stats, t, sm_count, s)
+#define QRT_TV_OCC(OC)                                          \
+    if (t.occupancy == OC) {                                    \
+        if (st) { if (f32) QRT_TV(32, OC, true); QRT_TV(16, OC, true); } \
+        if (f32) QRT_TV(32, OC, false);                         \
+        QRT_TV(16, OC, false);                                  \
     }
-    if (s32) { if (f32) QRT_TV(32, 32, 2); QRT_TV(32, 16, 2); }
-    if (f32) QRT_TV(64, 32, 2);
-    QRT_TV(64, 16, 2);
+    QRT_TV_OCC(32)
+    QRT_TV_OCC(24)
+    QRT_TV_OCC(16)
+#undef QRT_TV_OCC
 #undef QRT_TV
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_trace(bool any, const DevScene& S, const void* rays, uint64_t n, void* hits,
@@ -105,6 +110,40 @@ cudaError_t launch_trace(bool any, const DevScene& S, const void* rays, uint64_t
     }
     return launch_any_variant<false>(S, rays, n, hits, occ_bits, max_steps, cursor, stats, t,
                                      sm_count, s);
+}
+
+// Read-bandwidth sweep (a measurement helper, not part of the path): every
+// thread reads 16-byte words of buf with L2-only loads, reps times over the
+// whole buffer, and folds them into one word per warp so the loads stay live.
+// With a buffer that fits in L2 this measures the L2 read bandwidth that
+// bounds traversal of a cache-resident BVH.
+__global__ void __launch_bounds__(256) read_sweep_kernel(const uint4* __restrict__ buf, uint64_t n16,
+                                                         uint32_t reps, uint32_t* sink) {
+    uint32_t acc = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint32_t r = 0; r < reps; ++r) {
+#pragma unroll 4
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) {
+            const uint4 v = __ldcg(buf + i);
+            acc ^= v.x ^ v.y ^ v.z ^ v.w;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc ^= __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicXor(sink, acc);
+}
+
+cudaError_t launch_read_sweep(const void* buf, uint64_t bytes, uint32_t reps, uint32_t* sink,
+                              int sm_count, cudaStream_t s) {
+    const uint64_t n16 = bytes / 16;
+    if (n16 == 0 || reps == 0) return cudaSuccess;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, read_sweep_kernel, 256, 0);
+    if (per_sm < 1) per_sm = 1;
+    uint64_t grid = (uint64_t)sm_count * per_sm;
+    const uint64_t want = (n16 + 255) / 256;
+    if (want < grid) grid = want;
+    read_sweep_kernel<<<(unsigned)grid, 256, 0, s>>>(static_cast<const uint4*>(buf), n16, reps, sink);
+    return cudaGetLastError();
 }
 
 }  // namespace qrt

@@ -47,14 +47,19 @@ struct RaySetup {
     float oix, oiy, oiz;  // o * inv
     float px, py, pz;     // box widening in t units (delta * |inv|)
     uint32_t neg;         // bit a: direction negative along axis a
-    // watertight shear in affine form: X = V . rx - cx, Y = V . ry - cy, Z = V . rz - cz
+    float delta;
+    float dx, dy, dz;  // direction in the current space (for the shear)
+};
+
+// Watertight shear of the current-space ray in affine form,
+// X = V . rx - cx, Y = V . ry - cy, Z = V . rz - cz.  Built at the start of
+// each leaf rather than kept for the whole ray: it is needed only there, and
+// twelve fewer live registers per ray buy resident warps.
+struct Shear {
     float rx0, rx1, rx2, cx;
     float ry0, ry1, ry2, cy;
     float rz0, rz1, rz2, cz;
-    float delta;
-    float dx, dy, dz;  // direction in the current space (for the shear, set lazily)
-    float eps_t;       // bound on the error of an FP32 hit distance (t units)
-    bool sheared;      // shear rows valid for the current space
+    float eps_t;  // bound on the error of an FP32 hit distance (t units)
 };
 
 __device__ __forceinline__ float clamp_dir(float d) {
@@ -80,12 +85,11 @@ __device__ __forceinline__ void setup_boxes(RaySetup& r, float ox, float oy, flo
     r.dx = dx;
     r.dy = dy;
     r.dz = dz;
-    r.sheared = false;
 }
 
-__device__ __forceinline__ void setup_shear(RaySetup& r) {
+__device__ __forceinline__ Shear make_shear(const RaySetup& r) {
+    Shear sh;
     const float dx = r.dx, dy = r.dy, dz = r.dz;
-    r.sheared = true;
     const float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
     // kz = dominant axis, (kx, ky) the next two in cyclic order; selects
     // instead of indexed arrays keep everything in registers
@@ -100,21 +104,22 @@ __device__ __forceinline__ void setup_shear(RaySetup& r) {
     const float Sz = __frcp_rn(dkz);
     const float Sx = __fmul_rn(dkx, Sz), Sy = __fmul_rn(dky, Sz);
     // row X: +1 at kx, -Sx at kz; row Y: +1 at ky, -Sy at kz; row Z: Sz at kz
-    r.rx0 = kz == 0 ? -Sx : (kz == 2 ? 1.f : 0.f);
-    r.rx1 = kz == 1 ? -Sx : (kz == 0 ? 1.f : 0.f);
-    r.rx2 = kz == 2 ? -Sx : (kz == 1 ? 1.f : 0.f);
-    r.ry0 = kz == 0 ? -Sy : (kz == 1 ? 1.f : 0.f);
-    r.ry1 = kz == 1 ? -Sy : (kz == 2 ? 1.f : 0.f);
-    r.ry2 = kz == 2 ? -Sy : (kz == 0 ? 1.f : 0.f);
-    r.rz0 = kz == 0 ? Sz : 0.f;
-    r.rz1 = kz == 1 ? Sz : 0.f;
-    r.rz2 = kz == 2 ? Sz : 0.f;
-    r.cx = __fmaf_rn(-Sx, okz, okx);
-    r.cy = __fmaf_rn(-Sy, okz, oky);
-    r.cz = __fmul_rn(Sz, okz);
+    sh.rx0 = kz == 0 ? -Sx : (kz == 2 ? 1.f : 0.f);
+    sh.rx1 = kz == 1 ? -Sx : (kz == 0 ? 1.f : 0.f);
+    sh.rx2 = kz == 2 ? -Sx : (kz == 1 ? 1.f : 0.f);
+    sh.ry0 = kz == 0 ? -Sy : (kz == 1 ? 1.f : 0.f);
+    sh.ry1 = kz == 1 ? -Sy : (kz == 2 ? 1.f : 0.f);
+    sh.ry2 = kz == 2 ? -Sy : (kz == 0 ? 1.f : 0.f);
+    sh.rz0 = kz == 0 ? Sz : 0.f;
+    sh.rz1 = kz == 1 ? Sz : 0.f;
+    sh.rz2 = kz == 2 ? Sz : 0.f;
+    sh.cx = __fmaf_rn(-Sx, okz, okx);
+    sh.cy = __fmaf_rn(-Sy, okz, oky);
+    sh.cz = __fmul_rn(Sz, okz);
     // a position error of delta moves the distance along the dominant axis
     // by delta |Sz|; twice that bounds the FP32 hit distance's error
-    r.eps_t = 2.0f * __fmul_rn(r.delta, fabsf(Sz));
+    sh.eps_t = 2.0f * __fmul_rn(r.delta, fabsf(Sz));
+    return sh;
 }
 
 __device__ __forceinline__ float maxabs3(float a, float b, float c) {
@@ -217,11 +222,11 @@ struct SV {
     float X, Y, Z;
 };
 
-__device__ __forceinline__ SV shear(const RaySetup& r, float x, float y, float z) {
+__device__ __forceinline__ SV shear(const Shear& sh, float x, float y, float z) {
     SV s;
-    s.X = __fmaf_rn(x, r.rx0, __fmaf_rn(y, r.rx1, __fmaf_rn(z, r.rx2, -r.cx)));
-    s.Y = __fmaf_rn(x, r.ry0, __fmaf_rn(y, r.ry1, __fmaf_rn(z, r.ry2, -r.cy)));
-    s.Z = __fmaf_rn(x, r.rz0, __fmaf_rn(y, r.rz1, __fmaf_rn(z, r.rz2, -r.cz)));
+    s.X = __fmaf_rn(x, sh.rx0, __fmaf_rn(y, sh.rx1, __fmaf_rn(z, sh.rx2, -sh.cx)));
+    s.Y = __fmaf_rn(x, sh.ry0, __fmaf_rn(y, sh.ry1, __fmaf_rn(z, sh.ry2, -sh.cy)));
+    s.Z = __fmaf_rn(x, sh.rz0, __fmaf_rn(y, sh.rz1, __fmaf_rn(z, sh.rz2, -sh.cz)));
     return s;
 }
 
@@ -319,17 +324,18 @@ static __device__ __noinline__ int quad_test64(const InstDev* ip, const InstDev6
 // error band of zero, or the hit distance within eps_t of either end of the
 // interval -- is re-tested by quad_test64, which returns the world t
 // (*t64_out, *exact64 = 1).  Returns 1 on a hit.
-__device__ __forceinline__ int quad_test(const RaySetup& r, const QuadDev* q, const InstDev* ip,
+__device__ __forceinline__ int quad_test(const RaySetup& r, const Shear& sh, const QuadDev* q,
+                                         const InstDev* ip,
                                          const InstDev64* ip64, float wox, float woy, float woz,
                                          float wdx, float wdy, float wdz, float smin, float smax,
                                          float tmin, float* t_out, double* t64_out, float* u_out,
                                          float* v_out, int* exact64, uint32_t* n_fallback) {
     const float4* p = reinterpret_cast<const float4*>(q);
     const float4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
-    const SV s0 = shear(r, a.x, a.y, a.z);
-    const SV s1 = shear(r, a.w, b.x, b.y);
-    const SV s2 = shear(r, b.z, b.w, c.x);
-    const SV s3 = shear(r, c.y, c.z, c.w);
+    const SV s0 = shear(sh, a.x, a.y, a.z);
+    const SV s1 = shear(sh, a.w, b.x, b.y);
+    const SV s2 = shear(sh, b.z, b.w, c.x);
+    const SV s3 = shear(sh, c.y, c.z, c.w);
     const float e21 = edge(s2, s1), e02 = edge(s0, s2), e10 = edge(s1, s0);
     const float e32 = edge(s3, s2), e03 = edge(s0, s3);
     // one error band for the whole quad: covers delta-perturbed vertices and
@@ -354,7 +360,7 @@ __device__ __forceinline__ int quad_test(const RaySetup& r, const QuadDev* q, co
                 *u_out = __fdiv_rn(e02 + e10, det);
                 *v_out = __fdiv_rn(e10, det);
             }
-            uncertain |= fabsf(tt - smin) <= r.eps_t || fabsf(tt - smax) <= r.eps_t;
+            uncertain |= fabsf(tt - smin) <= sh.eps_t || fabsf(tt - smax) <= sh.eps_t;
         }
         if (c1 == 1) {
             const float det = e32 + e03 - e02;
@@ -366,7 +372,7 @@ __device__ __forceinline__ int quad_test(const RaySetup& r, const QuadDev* q, co
                 *u_out = __fdiv_rn(e03, det);
                 *v_out = __fdiv_rn(e03 - e02, det);
             }
-            uncertain |= fabsf(tt - smin) <= r.eps_t || fabsf(tt - smax) <= r.eps_t;
+            uncertain |= fabsf(tt - smin) <= sh.eps_t || fabsf(tt - smax) <= sh.eps_t;
         }
     }
     if (uncertain) {
@@ -437,6 +443,7 @@ struct Traversal {
     float te;  // object-space parameter offset: t = s + te
     RaySetup r;
     uint64_t stack[STACK];
+    int cap;  // stack entries a ray may use (<= STACK); set once per kernel
     int sp, inst_sp;
     bool top, have;
     uint32_t node_base, quad_base, cur_inst, cur, steps, max_steps, err;
@@ -503,7 +510,7 @@ struct Traversal {
                 if (nh == 0) {
                     have = false;
                 } else {
-                    if (sp + nh - 1 > STACK) {
+                    if (sp + nh - 1 > cap) {
                         err |= kErrStackOverflow;
                         return false;
                     }
@@ -605,7 +612,7 @@ struct Traversal {
         if (nh == 0) {
             have = false;
         } else {
-            if (sp + nh - 1 > STACK) {
+            if (sp + nh - 1 > cap) {
                 stop(kErrStackOverflow);
                 return;
             }
@@ -675,7 +682,7 @@ struct Traversal {
         // of the slab and shear arithmetic, with a factor-two margin
         const float delta = __fmul_rn(2.384185791015625e-07f * (m3.w + 2.0f),
                                       maxabs3(rox, roy, roz) + m0.w);
-        setup_boxes(r, rox, roy, roz, fdx, fdy, fdz, delta);  // shear follows at the first leaf
+        setup_boxes(r, rox, roy, roz, fdx, fdy, fdz, delta);
         inst_sp = sp;
         top = false;
         ++st.insts;
@@ -701,7 +708,7 @@ struct Traversal {
     // query is answered.  Two candidates whose FP32 distances are within
     // their error bounds of each other are ordered by their FP64 distances.
     __device__ __forceinline__ bool leaf(const DevScene& S, TraceStats& st) {
-        if (!r.sheared) setup_shear(r);
+        const Shear sh = make_shear(r);
         const uint32_t first = cur & kRefIndexMask;
         const uint32_t cnt = ((cur >> 27) & 0xFu) + 1u;
         const float smin = __fsub_rn(tmin, te);
@@ -714,7 +721,7 @@ struct Traversal {
             double t64;
             int ex64;
             ++st.quads;
-            if (!quad_test(r, S.quads + slot, ip, ip64, wox, woy, woz, wdx, wdy, wdz, smin, smax, tmin,
+            if (!quad_test(r, sh, S.quads + slot, ip, ip64, wox, woy, woz, wdx, wdy, wdz, smin, smax, tmin,
                            &tt, &t64, &uu, &vv, &ex64, &st.fallbacks))
                 continue;
             if (!ex64) tt = __fadd_rn(tt, te);
@@ -726,7 +733,7 @@ struct Traversal {
                 h.slot = slot;
                 return true;
             }
-            const float eps = fmaxf(r.eps_t, h_eps);
+            const float eps = fmaxf(sh.eps_t, h_eps);
             if (h.inst != 0xFFFFFFFFu && fabsf(tt - h.t) <= eps &&
                 !(h.slot == slot && h.inst == cur_inst)) {
                 // near tie with the current best: decide on FP64 distances
@@ -744,7 +751,7 @@ struct Traversal {
                     h.u = uu;
                     h.v = vv;
                     h.slot = slot;
-                    h_eps = r.eps_t;
+                    h_eps = sh.eps_t;
                 }
                 continue;
             }
@@ -755,7 +762,7 @@ struct Traversal {
                 h.u = uu;
                 h.v = vv;
                 h.slot = slot;
-                h_eps = ex64 ? 0.f : r.eps_t;
+                h_eps = ex64 ? 0.f : sh.eps_t;
             } else if (tt == h.t) {
                 const uint32_t pr = __ldg(S.prim + slot);
                 if (cur_inst < h.inst || (cur_inst == h.inst && pr < h.prim)) {
@@ -764,7 +771,7 @@ struct Traversal {
                     h.u = uu;
                     h.v = vv;
                     h.slot = slot;
-                    h_eps = ex64 ? 0.f : r.eps_t;
+                    h_eps = ex64 ? 0.f : sh.eps_t;
                 }
             }
         }
@@ -823,6 +830,7 @@ __device__ __forceinline__ uint32_t trace_ray(const DevScene& S, float wox, floa
                                               float tmax, uint32_t max_steps, Hit& h,
                                               TraceStats& st) {
     Traversal<ANY, STACK, FETCH> T;
+    T.cap = STACK;
     T.init(S, wox, woy, woz, wdx, wdy, wdz, tmin, tmax, max_steps, st);
     while (T.step(S, st)) {
     }

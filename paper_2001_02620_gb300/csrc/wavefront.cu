@@ -90,16 +90,20 @@ __global__ void __launch_bounds__(256) wave_gen(const __grid_constant__ WaveArgs
 
 // Persistent trace over a queue.  ANY = false: closest hit of ray_o/ray_d of
 // each queued path into hit[].  ANY = true: shadow ray from sray_o toward the
-// sun; an unoccluded ray adds pend[] into L[].
-template <bool ANY, int STACK, int FETCH, int MINB>
-__global__ void __launch_bounds__(256, MINB) wave_trace(const __grid_constant__ WaveArgs A, int depth) {
+// sun; an unoccluded ray adds pend[] into L[].  Rays use at most stack_cap
+// stack entries.  Work counters are kept only in the STATS variant: in the
+// others they are dead code, which saves a dozen registers per thread.
+template <bool ANY, int FETCH, int OCC, bool STATS>
+__global__ void __maxnreg__(occupancy_regs(OCC)) wave_trace(const __grid_constant__ WaveArgs A, int depth,
+                                                        int stack_cap) {
     const uint32_t* ctr = A.B.ctr + kCtrStride * depth;
     const uint32_t count = ANY ? ctr[kCtrShadow] : ctr[kCtrClosest];
     uint32_t* fetch = A.B.ctr + kCtrStride * depth + (ANY ? kCtrFetchShadow : kCtrFetchClosest);
     const uint32_t* queue = ANY ? A.B.qs : A.B.q[depth & 1];
     const uint32_t batch = A.batch;
     TraceStats st{0, 0, 0, 0, 0, 0};
-    Traversal<ANY, STACK, FETCH> T;
+    Traversal<ANY, kMaxStack, FETCH> T;
+    T.cap = stack_cap;
     uint32_t next = 0, end = 0, j = 0;
     uint32_t err = 0;
     auto fetch_ray = [&]() -> bool {
@@ -138,9 +142,9 @@ __global__ void __launch_bounds__(256, MINB) wave_trace(const __grid_constant__ 
             A.B.hit[j] = make_uint4(__float_as_uint(T.h.t), T.h.inst, T.h.prim, T.h.slot);
         }
     };
-    persistent_trace<ANY, STACK, FETCH>(A.S, T, st, fetch_ray, finish_ray);
+    persistent_trace<ANY, kMaxStack, FETCH>(A.S, T, st, fetch_ray, finish_ray);
     if (err) atomicOr(A.S.err, err);
-    if (A.stats) add_stats(A.stats + (ANY ? 6 : 0), st);
+    if constexpr (STATS) add_stats(A.stats + (ANY ? 6 : 0), st);
 }
 
 // Shade stage of depth i (1-based).  replay = false: primal; true: replay
@@ -247,33 +251,37 @@ __global__ void __launch_bounds__(256) wave_accumulate(const __grid_constant__ W
     out[2] = __fdiv_rn(s2, (float)V.spp);
 }
 
-template <bool ANY, int STACK, int FETCH, int MINB>
+template <bool ANY, int FETCH, int OCC, bool STATS>
 static cudaError_t launch_wave_trace_v(const WaveArgs& A, int depth, const Tune& t, int sm_count,
                                        cudaStream_t s) {
     int per_sm = t.blocks_per_sm;
     if (per_sm <= 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wave_trace<ANY, STACK, FETCH, MINB>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wave_trace<ANY, FETCH, OCC, STATS>,
                                                       t.block, 0);
         if (per_sm < 1) per_sm = 1;
     }
-    wave_trace<ANY, STACK, FETCH, MINB><<<(unsigned)(sm_count * per_sm), t.block, 0, s>>>(A, depth);
+    wave_trace<ANY, FETCH, OCC, STATS><<<(unsigned)(sm_count * per_sm), t.block, 0, s>>>(A, depth,
+                                                                                         t.stack);
     return cudaGetLastError();
 }
 
 template <bool ANY>
 static cudaError_t launch_wave_trace(const WaveArgs& A, int depth, const Tune& t, int sm_count,
                                      cudaStream_t s) {
-    const bool s32 = t.stack <= 32, f32 = t.fetch == 32, o24 = t.occupancy == 24;
-#define QRT_WT(ST, FE, MB) return launch_wave_trace_v<ANY, ST, FE, MB>(A, depth, t, sm_count, s)
-    if (o24) {
-        if (s32) { if (f32) QRT_WT(32, 32, 3); QRT_WT(32, 16, 3); }
-        if (f32) QRT_WT(64, 32, 3);
-        QRT_WT(64, 16, 3);
+    const bool st = A.stats != nullptr, f32 = t.fetch == 32;
+#define QRT_WT(FE, OC, ST) return launch_wave_trace_v<ANY, FE, OC, ST>(A, depth, t, sm_count, s)
+#define QRT_WT_OCC(OC)                                          \
+    if (t.occupancy == OC) {                                    \
+        if (st) { if (f32) QRT_WT(32, OC, true); QRT_WT(16, OC, true); } \
+        if (f32) QRT_WT(32, OC, false);                         \
+        QRT_WT(16, OC, false);                                  \
     }
-    if (s32) { if (f32) QRT_WT(32, 32, 2); QRT_WT(32, 16, 2); }
-    if (f32) QRT_WT(64, 32, 2);
-    QRT_WT(64, 16, 2);
+    QRT_WT_OCC(32)
+    QRT_WT_OCC(24)
+    QRT_WT_OCC(16)
+#undef QRT_WT_OCC
 #undef QRT_WT
+    return cudaErrorInvalidValue;
 }
 
 void wave_carve(void* base, uint64_t C, bool adjoint, WaveBufs& B) {

@@ -289,6 +289,25 @@ def test_l2_loss(api):
     np.testing.assert_allclose(dimg.cpu().numpy(), 2 * (a.astype(np.float64) - b) / a.size, rtol=1e-6)
 
 
+def test_read_bandwidth_helper(api):
+    """The L2 read-bandwidth helper: argument checks, and a sweep of an
+    L2-resident buffer reads faster than any HBM copy could."""
+    import ctypes as C
+    L = api.N.lib()
+    buf = torch.zeros(1 << 20, dtype=torch.int32, device="cuda")
+    sink = torch.zeros(1, dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    assert L.qrt_read_bandwidth(buf.data_ptr(), 0, 3, sink.data_ptr(), s) == api.N.QRT_OK
+    assert L.qrt_read_bandwidth(buf.data_ptr() + 4, 1024, 1, sink.data_ptr(), s) == api.N.QRT_ERR_ALIGN
+    assert L.qrt_read_bandwidth(buf.data_ptr(), 1000, 1, sink.data_ptr(), s) == api.N.QRT_ERR_ALIGN
+    assert L.qrt_read_bandwidth(None, 1024, 1, sink.data_ptr(), s) == api.N.QRT_ERR_INVALID_ARG
+    # all-zero data folds to zero
+    api.N.check(L.qrt_read_bandwidth(buf.data_ptr(), buf.numel() * 4, 2, sink.data_ptr(), s))
+    assert int(sink.item()) == 0
+    gbs = api.read_bandwidth_gbs(32 << 20, 20)
+    assert 8000.0 < gbs < 200000.0
+
+
 def test_stack_overflow_is_reported(api):
     """A chain-shaped BLAS over coincident quads needs about three stack
     entries per level: a 32-entry stack overflows, the kernel stops that ray

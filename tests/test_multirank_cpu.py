@@ -78,8 +78,8 @@ def test_two_rank_gloo_render_matches_single_rank():
 
 def test_autotune_candidates_and_cache(tmp_path):
     c = autotune.candidates()
-    assert len(c) == 24 and all(set(x) == {"batch", "block", "fetch", "occupancy"} for x in c)
-    assert len({tuple(sorted(x.items())) for x in c}) == 24
+    assert len(c) == 36 and all(set(x) == {"batch", "block", "fetch", "occupancy"} for x in c)
+    assert len({tuple(sorted(x.items())) for x in c}) == 36
     k, t = autotune.pick_best({'{"a": 1}': 0.5, '{"a": 2}': None, '{"a": 3}': 0.25})
     assert k == '{"a": 3}' and t == 0.25
     with pytest.raises(RuntimeError):
@@ -93,4 +93,6 @@ def test_autotune_candidates_and_cache(tmp_path):
     sc = I.tiny_scene()
     assert autotune.scene_class(sc).startswith("tiny:q1e3:i1e2")
     v = autotune.proxy_view(I.mid_view())
-    assert (v.w, v.h, v.spp) == (384, 384, 4)
+    assert (v.w, v.h, v.spp) == (1024, 1024, 4)
+    v = autotune.proxy_view(I.moana_view())
+    assert v.spp == 16 and v.w * v.h * v.spp <= 1 << 22 and abs(v.w / v.h - 16 / 9) < 0.01
