@@ -212,12 +212,14 @@ def bench_trace(scene, sc, dev, tuning=None, eye=(2048.0, -300.0, 450.0)):
     return out
 
 
-def bench_batched(api, scene, d_alb, dev, tuning=None):
-    """32 uneven views of the mid scene: one graph-captured persistent launch
-    versus 32 plain launches on one stream; images must be bit-identical."""
+def bench_batched(api, scene, d_alb, dev, tuning=None, views=None):
+    """Uneven views of the mid scene (default: the 32 views of the batched
+    workload): one graph-captured launch sequence over all views versus one
+    plain launch sequence per view on one stream; images must be
+    bit-identical."""
     import torch
     from paper_2001_02620_gb300 import inputs as I
-    views = I.batched_views()
+    views = views or I.batched_views()
     params = I.mid_params()
     paths = sum(v.w * v.h * v.spp for v in views)
     outs_b = [torch.empty((v.h, v.w, 3), device=dev) for v in views]
@@ -463,6 +465,11 @@ def main():
         line["trace"] = bench_trace(scene, sc, dev, tuning, eye=view.eye)
     if "batched" in extras:
         line["batched_vs_plain"] = bench_batched(api, scene, d_alb, dev, tuning)
+        # many small views (32-128 px, 1-4 spp): where one launch per view
+        # leaves the GPU idle between launches and in each launch's tail
+        line["batched_small_vs_plain"] = bench_batched(
+            api, scene, d_alb, dev, tuning,
+            views=I.batched_views(n_views=64, min_log2=5.0, max_log2=7.0, max_spp=4))
     if "adjoint" in extras:
         line["adjoint_vs_primal"] = bench_adjoint(api, scene, sc, dev, tuning)
     if rank == 0 and not args.no_cpu_baseline and world == 1:

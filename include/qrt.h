@@ -170,12 +170,20 @@ typedef struct {
  *   sah_bins   binned-SAH bins (4..64, default 16)
  *   threads    host threads for the build (0 = all cores)
  *   degenerate 1 = build a deliberately deep chain-shaped BLAS (test aid for
- *              the stack-overflow path); 0 = normal SAH build */
+ *              the stack-overflow path); 0 = normal SAH build
+ *   inst_boxes how tightly the TLAS bounds each instance: 1 = the world box of
+ *              its BLAS's transformed root box; k = 2..6 = the union of the
+ *              world boxes of the BLAS nodes k-1 levels below the root
+ *              (smaller boxes of a rotated object overlap fewer rays; the
+ *              result is intersected with the root-box bound); 0 = default
+ *              (6: up to 1024 boxes per instance, fewer for small meshes,
+ *              whose cut stops at their leaves) */
 typedef struct {
     uint32_t max_leaf;
     uint32_t sah_bins;
     uint32_t threads;
     uint32_t degenerate;
+    uint32_t inst_boxes;
 } qrt_build_opts;
 
 /* Scene statistics (host). */

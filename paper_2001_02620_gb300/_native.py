@@ -58,7 +58,7 @@ class qrt_params(C.Structure):
 
 class qrt_build_opts(C.Structure):
     _fields_ = [("max_leaf", C.c_uint32), ("sah_bins", C.c_uint32), ("threads", C.c_uint32),
-                ("degenerate", C.c_uint32)]
+                ("degenerate", C.c_uint32), ("inst_boxes", C.c_uint32)]
 
 
 class qrt_scene_stats(C.Structure):

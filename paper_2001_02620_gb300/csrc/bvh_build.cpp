@@ -337,29 +337,55 @@ float dequant(uint8_t q, int8_t e, float origin) {
 }
 
 FBox transform_box(const FBox& b, const float* x) {
-    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int k = 0; k < 8; ++k) {
-        double p[3] = {(k & 1) ? b.hi[0] : b.lo[0], (k & 2) ? b.hi[1] : b.lo[1],
-                       (k & 4) ? b.hi[2] : b.lo[2]};
-        for (int r = 0; r < 3; ++r) {
-            double w = (double)x[4 * r] * p[0] + (double)x[4 * r + 1] * p[1] +
-                       (double)x[4 * r + 2] * p[2] + (double)x[4 * r + 3];
-            lo[r] = std::min(lo[r], w);
-            hi[r] = std::max(hi[r], w);
-        }
-    }
     FBox out;
     for (int r = 0; r < 3; ++r) {
-        // widen by a relative 1e-12 to cover the FP64 rounding above, then
-        // round outward to float
-        double pad = 1e-12 * (std::fabs(lo[r]) + std::fabs(hi[r]) + 1e-30);
-        double l = lo[r] - pad, h = hi[r] + pad;
+        double wc = (double)x[4 * r + 3], wh = 0.0, mag = std::fabs(wc);
+        for (int c = 0; c < 3; ++c) {
+            const double ctr = 0.5 * ((double)b.lo[c] + (double)b.hi[c]);
+            const double half = 0.5 * ((double)b.hi[c] - (double)b.lo[c]);
+            const double a = (double)x[4 * r + c];
+            wc += a * ctr;
+            wh += std::fabs(a) * half;
+            mag += std::fabs(a * ctr) + std::fabs(a) * half;
+        }
+        // every product and sum above is exact to within 2^-52 of mag;
+        // 1e-12 mag covers their accumulated rounding many times over
+        const double pad = 1e-12 * mag + 1e-300;
+        const double l = wc - wh - pad, h = wc + wh + pad;
         float fl = (float)l, fh = (float)h;
         if ((double)fl > l) fl = std::nextafter(fl, -kFInf);
         if ((double)fh < h) fh = std::nextafter(fh, kFInf);
         out.lo[r] = fl;
         out.hi[r] = fh;
     }
+    return out;
+}
+
+static void level_boxes_rec(const std::vector<QNode>& nodes, uint32_t n, uint32_t level,
+                            std::vector<FBox>& out) {
+    const QNode& q = nodes[n];
+    const float o[3] = {q.ox, q.oy, q.oz};
+    const int8_t e[3] = {q.ex, q.ey, q.ez};
+    for (int i = 0; i < 4; ++i) {
+        const uint8_t m = q.meta[i];
+        if (m == 0) continue;
+        if (m == kMetaInner && level > 1) {
+            level_boxes_rec(nodes, q.child[i], level - 1, out);
+            continue;
+        }
+        FBox b;
+        for (int a = 0; a < 3; ++a) {
+            b.lo[a] = dequant(q.qlo[a][i], e[a], o[a]);
+            b.hi[a] = dequant(q.qhi[a][i], e[a], o[a]);
+        }
+        out.push_back(b);
+    }
+}
+
+std::vector<FBox> level_boxes(const std::vector<QNode>& nodes, uint32_t level) {
+    std::vector<FBox> out;
+    if (level == 0 || nodes.empty()) return out;
+    level_boxes_rec(nodes, 0, level, out);
     return out;
 }
 

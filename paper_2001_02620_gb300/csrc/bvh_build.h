@@ -17,6 +17,7 @@ struct BuildOpts {
     uint32_t sah_bins = 16;
     uint32_t threads = 0;
     uint32_t degenerate = 0;
+    uint32_t inst_box_level = 5;  // BLAS level whose node boxes bound an instance (0 = root box)
 };
 
 struct FBox {
@@ -48,9 +49,17 @@ bool build_tlas(const std::vector<FBox>& inst_boxes, const BuildOpts& opts, Tlas
 bool check_wide(const std::vector<QNode>& nodes, const std::vector<FBox>& item_boxes,
                 std::string& err, uint32_t* depth);
 
-// World box of an object box under an object->world float 3x4 transform,
-// computed in FP64 and rounded outward to float.
+// World box of an object box under an object->world float 3x4 transform:
+// centre and half extent mapped in FP64 (the exact box of the eight
+// transformed corners), widened by a bound on that arithmetic's rounding and
+// rounded outward to float.
 FBox transform_box(const FBox& b, const float* xform);
+
+// Dequantised boxes of the BLAS nodes `level` levels below the root (level 1
+// = the root's children) together with the leaves above that level; every
+// quad of the BLAS lies in one of them.  level 0 returns nothing (use the
+// root box).
+std::vector<FBox> level_boxes(const std::vector<QNode>& nodes, uint32_t level);
 
 // Dequantised bound used by both the builder and the checker.
 float dequant(uint8_t q, int8_t e, float origin);

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -246,6 +247,8 @@ bool inverse3(const double* m, double* r) {
     return true;
 }
 
+const float kFInfHost = std::numeric_limits<float>::infinity();
+
 BuildOpts resolve_build(const qrt_build_opts* o) {
     BuildOpts b;
     if (!o) return b;
@@ -253,6 +256,7 @@ BuildOpts resolve_build(const qrt_build_opts* o) {
     if (o->sah_bins) b.sah_bins = o->sah_bins;
     b.threads = o->threads;
     b.degenerate = o->degenerate;
+    if (o->inst_boxes) b.inst_box_level = o->inst_boxes - 1;
     return b;
 }
 
@@ -290,6 +294,7 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
         if (mesh_ids[i] >= n_mesh)
             return fail(QRT_ERR_INVALID_ARG, "instance " + std::to_string(i) + " names mesh " +
                                                  std::to_string(mesh_ids[i]) + " out of range");
+    if (opts && opts->inst_boxes > 6) return fail(QRT_ERR_INVALID_ARG, "build_opts.inst_boxes must be 0..6");
     const BuildOpts bo = resolve_build(opts);
     auto t0 = std::chrono::steady_clock::now();
 
@@ -369,22 +374,25 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
     std::vector<InstDev64> inst64(n_inst);
     std::vector<FBox> wbox(n_inst);
     std::vector<float> meshR(n_mesh);
+    std::vector<std::vector<FBox>> mesh_cut(n_mesh);
     for (uint32_t m = 0; m < n_mesh; ++m) {
         float r = 0.f;
         for (int a = 0; a < 3; ++a)
             r = std::max(r, std::max(std::fabs(blas[m].box.lo[a]), std::fabs(blas[m].box.hi[a])));
         meshR[m] = r;
+        mesh_cut[m] = level_boxes(blas[m].nodes, bo.inst_box_level);
     }
-    for (uint64_t i = 0; i < n_inst; ++i) {
+    // per instance: FP64 inverse, float records, world box (threads over
+    // ranges of instances; the first bad instance is reported)
+    std::atomic<uint64_t> bad_inst{~0ull};
+    auto setup_instance = [&](uint64_t i) -> bool {
         const float* x = xforms + 12 * i;
         double A[9], Ai[9];
         for (int r = 0; r < 3; ++r)
             for (int c = 0; c < 3; ++c) A[3 * r + c] = x[4 * r + c];
         bool finite = true;
         for (int k = 0; k < 12; ++k) finite = finite && std::isfinite(x[k]);
-        if (!finite || !inverse3(A, Ai))
-            return fail(QRT_ERR_INVALID_ARG,
-                        "instance " + std::to_string(i) + " has a non-finite or singular transform");
+        if (!finite || !inverse3(A, Ai)) return false;
         InstDev& I = inst[i];
         std::memset(&I, 0, sizeof(I));
         std::memset(&inst64[i], 0, sizeof(InstDev64));
@@ -405,7 +413,82 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
         I.quad_base = (uint32_t)quad_base[m];
         I.R = meshR[m];
         I.kappa = (float)(na * ni);
-        wbox[i] = transform_box(blas[m].box, x);
+        // the transformed root box and the union of the transformed cut
+        // boxes both contain the instance's geometry, so their intersection
+        // does too
+        FBox wb = transform_box(blas[m].box, x);
+        if (!mesh_cut[m].empty()) {
+            FBox u;
+            for (int a = 0; a < 3; ++a) {
+                u.lo[a] = kFInfHost;
+                u.hi[a] = -kFInfHost;
+            }
+            for (const FBox& cb : mesh_cut[m]) {
+                const FBox t = transform_box(cb, x);
+                for (int a = 0; a < 3; ++a) {
+                    u.lo[a] = std::min(u.lo[a], t.lo[a]);
+                    u.hi[a] = std::max(u.hi[a], t.hi[a]);
+                }
+            }
+            for (int a = 0; a < 3; ++a) {
+                wb.lo[a] = std::max(wb.lo[a], u.lo[a]);
+                wb.hi[a] = std::min(wb.hi[a], u.hi[a]);
+            }
+        }
+        wbox[i] = wb;
+        return true;
+    };
+    {
+        unsigned nt = bo.threads ? bo.threads : std::max(1u, std::thread::hardware_concurrency());
+        const uint64_t chunk = 4096;
+        const uint64_t n_chunks = (n_inst + chunk - 1) / chunk;
+        nt = (unsigned)std::min<uint64_t>(nt, std::max<uint64_t>(1, n_chunks));
+        std::atomic<uint64_t> next{0};
+        auto work = [&]() {
+            for (;;) {
+                const uint64_t c = next.fetch_add(1);
+                if (c >= n_chunks) break;
+                const uint64_t end = std::min(n_inst, (c + 1) * chunk);
+                for (uint64_t i = c * chunk; i < end; ++i) {
+                    if (!setup_instance(i)) {
+                        uint64_t cur = bad_inst.load();
+                        while (i < cur && !bad_inst.compare_exchange_weak(cur, i)) {
+                        }
+                    }
+                }
+            }
+        };
+        std::vector<std::thread> th;
+        for (unsigned k = 1; k < nt; ++k) th.emplace_back(work);
+        work();
+        for (auto& t : th) t.join();
+    }
+    if (bad_inst.load() != ~0ull)
+        return fail(QRT_ERR_INVALID_ARG, "instance " + std::to_string(bad_inst.load()) +
+                                             " has a non-finite or singular transform");
+    // Spot check of the instance bounds: for up to 256 evenly spaced
+    // instances (at most 2^23 vertices in all), every vertex of every quad,
+    // mapped to world space in FP64, lies inside the instance's TLAS box.
+    {
+        const uint64_t samples = std::min<uint64_t>(n_inst, 256);
+        uint64_t budget = 1ull << 23;
+        for (uint64_t k = 0; k < samples; ++k) {
+            const uint64_t i = k * n_inst / samples;
+            const uint32_t m = mesh_ids[i];
+            const uint64_t nv = 4ull * blas[m].quads.size();
+            if (nv > budget) continue;
+            budget -= nv;
+            const float* x = xforms + 12 * i;
+            for (const QuadDev& q : blas[m].quads)
+                for (int v = 0; v < 4; ++v)
+                    for (int r = 0; r < 3; ++r) {
+                        const double w = (double)x[4 * r] * q.v[3 * v] + (double)x[4 * r + 1] * q.v[3 * v + 1] +
+                                         (double)x[4 * r + 2] * q.v[3 * v + 2] + (double)x[4 * r + 3];
+                        if (!(w >= (double)wbox[i].lo[r] && w <= (double)wbox[i].hi[r]))
+                            return fail(QRT_ERR_INVALID_ARG, "internal: instance " + std::to_string(i) +
+                                                                 " lies outside its TLAS box");
+                    }
+        }
     }
     TlasResult tlas;
     std::string terr;

@@ -782,9 +782,9 @@ struct Traversal {
 // Persistent warp-synchronous traversal loop.  Each lane holds one ray;
 // fetch(ray) claims the next ray (returns false when none is left) and
 // calls T.init; done() consumes the finished ray in T.  Per outer iteration
-// the warp first tests inner nodes together until no lane has one left
-// (lanes that reach a BLAS leaf postpone it and keep traversing), then lanes
-// enter instances or test one leaf each.  Finished lanes refill
+// the warp first tests inner nodes together (lanes that reach a BLAS leaf
+// postpone it and keep traversing) until few lanes are left with one, then
+// lanes enter instances or test one leaf each.  Finished lanes refill
 // immediately, so no lane waits for the slowest ray of its warp.
 template <bool ANY, int STACK, int FETCH, class Fetch, class Done>
 __device__ __forceinline__ void persistent_trace(const DevScene& S, Traversal<ANY, STACK, FETCH>& T,
@@ -801,7 +801,16 @@ __device__ __forceinline__ void persistent_trace(const DevScene& S, Traversal<AN
         if (__all_sync(FULL, !busy)) break;
         for (;;) {
             const bool w = busy && T.wants_inner();
-            if (!__any_sync(FULL, w)) break;
+            const unsigned bw = __ballot_sync(FULL, w);
+            if (!bw) break;
+            // Leave the inner-node phase early once the lanes still in it are
+            // at most half as many as the lanes waiting at an instance or a
+            // leaf (or finished): those then move on together instead of
+            // idling until the warp's longest run of inner nodes ends.
+            // bo != 0 keeps a lane that the next phase moves on, so every
+            // outer iteration makes progress.
+            const unsigned bo = __ballot_sync(FULL, busy && !w);
+            if (bo && 2 * __popc(bw) <= __popc(bo)) break;
             if (w) T.inner_step(S, st);
         }
         if (busy) {

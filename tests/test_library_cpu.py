@@ -73,6 +73,20 @@ def test_host_side_argument_errors(native):
     rc = L.qrt_scene_create(m, 1, xf.ctypes.data_as(C.POINTER(C.c_float)),
                             ids.ctypes.data_as(C.POINTER(C.c_uint32)), 2, None, C.byref(out))
     assert rc == native.QRT_ERR_INVALID_ARG and b"out of range" in L.qrt_last_error()
+    # build options out of range
+    ids = np.array([0, 0], dtype=np.uint32)
+    o = native.qrt_build_opts()
+    o.inst_boxes = 7
+    rc = L.qrt_scene_create(m, 1, xf.ctypes.data_as(C.POINTER(C.c_float)),
+                            ids.ctypes.data_as(C.POINTER(C.c_uint32)), 2, C.byref(o), C.byref(out))
+    assert rc == native.QRT_ERR_INVALID_ARG and b"inst_boxes" in L.qrt_last_error()
+    # a singular instance transform is found by the host build (no GPU needed)
+    xs = xf.copy()
+    xs[12:24] = [1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0]
+    rc = L.qrt_scene_create(m, 1, xs.ctypes.data_as(C.POINTER(C.c_float)),
+                            ids.ctypes.data_as(C.POINTER(C.c_uint32)), 2, None, C.byref(out))
+    assert rc == native.QRT_ERR_INVALID_ARG and b"instance 1" in L.qrt_last_error()
+    assert b"singular" in L.qrt_last_error()
 
 
 def _check_mesh(native, v, q, **opts):
