@@ -28,8 +28,10 @@ METRIC = "Mrays/s closest-hit & path samples/s, batched vs plain launch; adjoint
 # per kernel kind (closest-hit, then shadow): rays, nodes, quads, instance
 # entries, fp64 re-tests, shaded vertices
 STAT_WORDS = 12
+# the closest-hit kernel's code and the scene build that shapes its traffic
 KERNEL_SOURCES = ["paper_2001_02620_gb300/csrc/traverse.cuh", "paper_2001_02620_gb300/csrc/wavefront.cu",
-                  "paper_2001_02620_gb300/csrc/qrt_layout.h", "paper_2001_02620_gb300/csrc/shading.cuh"]
+                  "paper_2001_02620_gb300/csrc/qrt_layout.h", "paper_2001_02620_gb300/csrc/shading.cuh",
+                  "paper_2001_02620_gb300/csrc/bvh_build.cpp", "paper_2001_02620_gb300/csrc/capi.cpp"]
 
 
 def kernel_source_hash() -> str:
