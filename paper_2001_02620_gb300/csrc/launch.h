@@ -2,21 +2,54 @@
 // translation units (trace.cu, render.cu).  Plain C++ types only.
 #pragma once
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <stdint.h>
 
 #include "qrt_layout.h"
 
 namespace qrt {
 
-// Resolved launch configuration.
+// Resident blocks per SM of one kernel at a given block size (no dynamic
+// shared memory), queried once per device and block size and then reused:
+// the query costs more host time than launching a trace kernel on a short
+// queue, and the persistent kernels size their grid from it on every launch.
+// Each kernel variant owns one (a static in its launcher).
+struct ResidentBlocks {
+    std::atomic<int> cached[16][5];  // [device][block / 64], 0 = not queried yet
+
+    template <class Kernel>
+    int get(Kernel kernel, int block) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16 || block % 64 != 0 ||
+            block / 64 > 4)
+            return query(kernel, block);
+        std::atomic<int>& c = cached[dev][block / 64];
+        int n = c.load(std::memory_order_relaxed);
+        if (n == 0) {
+            n = query(kernel, block);
+            c.store(n, std::memory_order_relaxed);
+        }
+        return n;
+    }
+
+    template <class Kernel>
+    static int query(Kernel kernel, int block) {
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, 0);
+        return n < 1 ? 1 : n;
+    }
+};
+
 // Register budget per thread that lets `warps` warps reside on one SM
 // (65,536 registers per SM, allocated in multiples of 8 per thread).
 constexpr int occupancy_regs(int warps) { return (65536 / (32 * warps)) & ~7; }
 
+// Resolved launch configuration.
 struct Tune {
     int block = 128;
     int blocks_per_sm = 0;  // 0 = occupancy maximum
-    int batch = 1;          // 32-item groups a warp claims per fetch
+    int batch = 1;          // single kernel: 32-pixel groups a warp claims; trace kernels: rays a lane claims
     int stack = 64;         // 32 or 64
     int fetch = 32;         // node fetch bytes per load: 16 or 32
     int occupancy = 32;     // trace kernels: target resident warps per SM (16, 24 or 32)

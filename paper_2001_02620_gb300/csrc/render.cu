@@ -212,9 +212,8 @@ __global__ void __launch_bounds__(256) render_kernel(const __grid_constant__ Ren
 
 template <int STACK, int FETCH, bool ADJ>
 static int occupancy_of(int block) {
-    int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_kernel<STACK, FETCH, ADJ>, block, 0);
-    return n;
+    static ResidentBlocks resident;
+    return resident.get(render_kernel<STACK, FETCH, ADJ>, block);
 }
 
 int render_occupancy(const Tune& t, bool adjoint) {

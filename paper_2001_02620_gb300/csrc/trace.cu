@@ -17,19 +17,13 @@ __global__ void __maxnreg__(occupancy_regs(OCC)) trace_kernel(const DevScene S, 
     TraceStats st{0, 0, 0, 0, 0, 0};
     Traversal<ANY, kMaxStack, FETCH> T;
     T.cap = stack_cap;
-    uint64_t next = 0, end = 0, i = 0;
+    uint64_t i = 0;
     uint32_t err = 0;
     uint64_t bad = ~0ull;
-    auto fetch_ray = [&]() -> bool {
-        if (next >= end) {
-            next = atomicAdd(cursor, (unsigned long long)batch);
-            end = min(next + batch, n);
-            if (next >= n) return false;
-        }
-        i = next++;
+    auto start_ray = [&](unsigned long long k) {
+        i = k;
         const float4 a = __ldg(rays + 2 * i), b = __ldg(rays + 2 * i + 1);
         T.init(S, a.x, a.y, a.z, b.x, b.y, b.z, a.w, b.w, max_steps, st);
-        return true;
     };
     auto finish_ray = [&]() {
         if (T.err) {
@@ -45,7 +39,8 @@ __global__ void __maxnreg__(occupancy_regs(OCC)) trace_kernel(const DevScene S, 
             hits[i] = make_uint4(__float_as_uint(T.h.t), T.h.inst, T.h.prim, uv);
         }
     };
-    persistent_trace<ANY, kMaxStack, FETCH>(S, T, st, fetch_ray, finish_ray);
+    persistent_trace<ANY, kMaxStack, FETCH>(S, T, st, cursor, (unsigned long long)n, batch, start_ray,
+                                            finish_ray);
     if (err) {
         atomicOr(S.err, err);
         atomicMin(S.err + 1, (uint32_t)min(bad, (uint64_t)0xFFFFFFFEu));
@@ -58,12 +53,9 @@ static cudaError_t launch_variant(const DevScene& S, const float4* rays, uint64_
                                   uint32_t* occ, uint32_t max_steps, unsigned long long* cursor,
                                   unsigned long long* stats, const Tune& t, int sm_count,
                                   cudaStream_t s) {
-    int per_sm = t.blocks_per_sm;
-    if (per_sm <= 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel<ANY, FETCH, OCC, STATS>,
-                                                      t.block, 0);
-        if (per_sm < 1) per_sm = 1;
-    }
+    static ResidentBlocks resident;
+    const int per_sm = t.blocks_per_sm > 0 ? t.blocks_per_sm
+                                           : resident.get(trace_kernel<ANY, FETCH, OCC, STATS>, t.block);
     uint64_t grid = (uint64_t)sm_count * per_sm;
     const uint64_t want = (n + (uint64_t)t.block - 1) / (uint64_t)t.block;
     if (want < grid) grid = want;

@@ -779,24 +779,41 @@ struct Traversal {
     }
 };
 
-// Persistent warp-synchronous traversal loop.  Each lane holds one ray;
-// fetch(ray) claims the next ray (returns false when none is left) and
-// calls T.init; done() consumes the finished ray in T.  Per outer iteration
+// Persistent warp-synchronous traversal loop over work items [0, count)
+// claimed from *cursor.  Each lane holds one ray; start(k) sets item k up in
+// T (T.init), done() consumes the finished ray in T.  A lane claims `batch`
+// items at a time; the idle lanes of a warp claim theirs with one atomic
+// (warp-aggregated), so a launch costs about one atomic per warp and
+// refill round instead of one per thread.  Per outer iteration
 // the warp first tests inner nodes together (lanes that reach a BLAS leaf
 // postpone it and keep traversing) until few lanes are left with one, then
 // lanes enter instances or test one leaf each.  Finished lanes refill
 // immediately, so no lane waits for the slowest ray of its warp.
-template <bool ANY, int STACK, int FETCH, class Fetch, class Done>
+template <bool ANY, int STACK, int FETCH, class Idx, class Start, class Done>
 __device__ __forceinline__ void persistent_trace(const DevScene& S, Traversal<ANY, STACK, FETCH>& T,
-                                                 TraceStats& st, Fetch fetch, Done done) {
+                                                 TraceStats& st, Idx* cursor, Idx count,
+                                                 uint32_t batch, Start start, Done done) {
     const unsigned FULL = 0xFFFFFFFFu;
+    const unsigned lane = threadIdx.x & 31u;
     bool busy = false, exhausted = false;
+    Idx next = 0, end = 0;
     for (;;) {
+        const bool need = !busy && !exhausted && next >= end;
+        const unsigned want = __ballot_sync(FULL, need);
+        if (want) {
+            const int leader = __ffs(want) - 1;
+            Idx base = 0;
+            if ((int)lane == leader) base = atomicAdd(cursor, (Idx)batch * (Idx)__popc(want));
+            base = __shfl_sync(FULL, base, leader);
+            if (need) {
+                next = base + (Idx)batch * (Idx)__popc(want & ((1u << lane) - 1u));
+                end = min(next + (Idx)batch, count);
+                exhausted = next >= count;
+            }
+        }
         if (!busy && !exhausted) {
-            if (fetch())
-                busy = true;
-            else
-                exhausted = true;
+            start(next++);
+            busy = true;
         }
         if (__all_sync(FULL, !busy)) break;
         for (;;) {

@@ -104,15 +104,10 @@ __global__ void __maxnreg__(occupancy_regs(OCC)) wave_trace(const __grid_constan
     TraceStats st{0, 0, 0, 0, 0, 0};
     Traversal<ANY, kMaxStack, FETCH> T;
     T.cap = stack_cap;
-    uint32_t next = 0, end = 0, j = 0;
+    uint32_t j = 0;
     uint32_t err = 0;
-    auto fetch_ray = [&]() -> bool {
-        if (next >= end) {
-            next = atomicAdd(fetch, batch);
-            end = min(next + batch, count);
-            if (next >= count) return false;
-        }
-        j = queue[next++];
+    auto start_ray = [&](uint32_t k) {
+        j = queue[k];
         if (ANY) {
             const float4 o = A.B.sray_o[j];
             T.init(A.S, o.x, o.y, o.z, A.P.sun_l[0], A.P.sun_l[1], A.P.sun_l[2], 0.f, kInfF,
@@ -121,7 +116,6 @@ __global__ void __maxnreg__(occupancy_regs(OCC)) wave_trace(const __grid_constan
             const float4 o = A.B.ray_o[j], d = A.B.ray_d[j];
             T.init(A.S, o.x, o.y, o.z, d.x, d.y, d.z, o.w, d.w, A.P.max_steps, st);
         }
-        return true;
     };
     auto finish_ray = [&]() {
         err |= T.err;
@@ -142,7 +136,7 @@ __global__ void __maxnreg__(occupancy_regs(OCC)) wave_trace(const __grid_constan
             A.B.hit[j] = make_uint4(__float_as_uint(T.h.t), T.h.inst, T.h.prim, T.h.slot);
         }
     };
-    persistent_trace<ANY, kMaxStack, FETCH>(A.S, T, st, fetch_ray, finish_ray);
+    persistent_trace<ANY, kMaxStack, FETCH>(A.S, T, st, fetch, count, batch, start_ray, finish_ray);
     if (err) atomicOr(A.S.err, err);
     if constexpr (STATS) add_stats(A.stats + (ANY ? 6 : 0), st);
 }
@@ -254,12 +248,9 @@ __global__ void __launch_bounds__(256) wave_accumulate(const __grid_constant__ W
 template <bool ANY, int FETCH, int OCC, bool STATS>
 static cudaError_t launch_wave_trace_v(const WaveArgs& A, int depth, const Tune& t, int sm_count,
                                        cudaStream_t s) {
-    int per_sm = t.blocks_per_sm;
-    if (per_sm <= 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wave_trace<ANY, FETCH, OCC, STATS>,
-                                                      t.block, 0);
-        if (per_sm < 1) per_sm = 1;
-    }
+    static ResidentBlocks resident;
+    const int per_sm = t.blocks_per_sm > 0 ? t.blocks_per_sm
+                                           : resident.get(wave_trace<ANY, FETCH, OCC, STATS>, t.block);
     wave_trace<ANY, FETCH, OCC, STATS><<<(unsigned)(sm_count * per_sm), t.block, 0, s>>>(A, depth,
                                                                                          t.stack);
     return cudaGetLastError();
