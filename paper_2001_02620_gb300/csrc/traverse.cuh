@@ -786,8 +786,9 @@ struct Traversal {
 // (warp-aggregated), so a launch costs about one atomic per warp and
 // refill round instead of one per thread.  Per outer iteration
 // the warp first tests inner nodes together (lanes that reach a BLAS leaf
-// postpone it and keep traversing) until few lanes are left with one, then
-// lanes enter instances or test one leaf each.  Finished lanes refill
+// postpone it and keep traversing; lanes waiting at instances enter them in
+// groups) until few lanes are left with an inner node, then lanes enter
+// instances or test one leaf each.  Finished lanes refill
 // immediately, so no lane waits for the slowest ray of its warp.
 template <bool ANY, int STACK, int FETCH, class Idx, class Start, class Done>
 __device__ __forceinline__ void persistent_trace(const DevScene& S, Traversal<ANY, STACK, FETCH>& T,
@@ -817,6 +818,16 @@ __device__ __forceinline__ void persistent_trace(const DevScene& S, Traversal<AN
         }
         if (__all_sync(FULL, !busy)) break;
         for (;;) {
+            // Once eight or more lanes wait at an instance (TLAS leaf), they
+            // enter it together and go on with the inner nodes of its BLAS
+            // in this phase, instead of idling until the next outer
+            // iteration.  Each such step enters at least eight instances.
+            const bool wt = busy && T.at_instance();
+            const unsigned bt = __ballot_sync(FULL, wt);
+            if (__popc(bt) >= 8) {
+                if (wt) T.instance_step(S, st);
+                continue;
+            }
             const bool w = busy && T.wants_inner();
             const unsigned bw = __ballot_sync(FULL, w);
             if (!bw) break;
