@@ -78,8 +78,8 @@ def test_two_rank_gloo_render_matches_single_rank():
 
 def test_autotune_candidates_and_cache(tmp_path):
     c = autotune.candidates()
-    assert len(c) == 36 and all(set(x) == {"batch", "block", "fetch", "occupancy"} for x in c)
-    assert len({tuple(sorted(x.items())) for x in c}) == 36
+    assert len(c) == 18 and all(set(x) == {"block", "fetch", "occupancy"} for x in c)
+    assert len({tuple(sorted(x.items())) for x in c}) == 18
     k, t = autotune.pick_best({'{"a": 1}': 0.5, '{"a": 2}': None, '{"a": 3}': 0.25})
     assert k == '{"a": 3}' and t == 0.25
     with pytest.raises(RuntimeError):
