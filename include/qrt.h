@@ -227,7 +227,10 @@ int qrt_trace_any(qrt_scene scene, const qrt_ray* d_rays, uint64_t n, uint32_t* 
  * launch covers every (view, pixel) and all of each pixel's spp samples).
  * d_albedo: DEVICE float [n_quads*3], per unique quad RGB albedo.  Each
  * view's out_rgb receives the mean over its spp samples; results do not
- * depend on n_views, on the tuning or on other views in the same call. */
+ * depend on n_views, on the tuning or on other views in the same call.
+ * The wavefront renderer enqueues its work on `stream` and on a second
+ * stream that the library keeps per (scene, stream) and joins back before
+ * returning control of the stream's order: the call stays stream-ordered. */
 int qrt_render_spp(qrt_scene scene, const qrt_view* views, uint32_t n_views,
                    const float* d_albedo, const qrt_params* params, qrt_stream stream);
 
@@ -296,7 +299,9 @@ int qrt_trace_stats(qrt_scene scene, int any, const qrt_ray* d_rays, uint64_t n,
  * stages 0 camera-ray generation, 1 closest-hit tracing, 2 shading,
  * 3 shadow-ray tracing, 4 accumulation (ms[5], launches[5]); reset != 0
  * starts a new accumulation.  Timers are per scene: time one stream at a
- * time. */
+ * time.  A timed render runs its stages one after another; an untimed one
+ * runs the shadow rays of each depth on a second stream beside the next
+ * depth's closest-hit rays. */
 int qrt_stage_times(qrt_scene scene, qrt_stream stream, double* ms, uint32_t* launches, int reset);
 
 /* Measurement helper with no counterpart in the paper: reads the DEVICE

@@ -115,7 +115,23 @@ struct StreamSlot {
     unsigned long long* counter = nullptr;
     void* ws = nullptr;
     size_t ws_bytes = 0;
+    WaveStreams ov;  // second stream for overlapping shadow and closest-hit launches
 };
+
+void destroy_streams(WaveStreams& w) {
+    if (w.fork) cudaEventDestroy(w.fork);
+    if (w.join) cudaEventDestroy(w.join);
+    if (w.aux) cudaStreamDestroy(w.aux);
+    w = WaveStreams{};
+}
+
+cudaError_t create_streams(WaveStreams& w) {
+    cudaError_t e = cudaStreamCreateWithFlags(&w.aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.join, cudaEventDisableTiming);
+    if (e != cudaSuccess) destroy_streams(w);
+    return e;
+}
 
 struct qrt_scene_s {
     int device = -1;
@@ -174,7 +190,10 @@ void free_scene(qrt_scene_s* s) {
     cudaFree(s->d_inst64);
     cudaFree(s->d_err);
     cudaFree(s->d_counters);
-    for (StreamSlot& sl : s->slots) cudaFree(sl.ws);
+    for (StreamSlot& sl : s->slots) {
+        cudaFree(sl.ws);
+        destroy_streams(sl.ov);
+    }
     delete s;
 }
 
@@ -727,7 +746,7 @@ int ensure_workspace(StreamSlot& sl, size_t bytes, cudaStream_t s) {
 int wave_enqueue(qrt_scene scene, const qrt_view* views, uint32_t n_views, const float* d_albedo,
                  const float* const* d_dimage, float* d_grad, const qrt_params* params,
                  const Tune& t, void* workspace, size_t ws_bytes, unsigned long long* stats,
-                 cudaStream_t s, WaveArgs& W, RenderArgs& R) {
+                 cudaStream_t s, WaveArgs& W, RenderArgs& R, const WaveStreams* ov) {
     static_assert(sizeof(WaveArgs) < 32000, "kernel parameter block too large");
     const bool adjoint = d_grad != nullptr;
     const uint64_t cap = 1ull << t.chunk_log2;
@@ -756,7 +775,8 @@ int wave_enqueue(qrt_scene scene, const qrt_view* views, uint32_t n_views, const
         }
         W.n_views = cnt;
         StageHook* hook = (params && (params->flags & QRT_FLAG_STAGE_TIMES)) ? &scene->timer : nullptr;
-        cudaError_t e = launch_wave(W, t, scene->sm_count, s, hook);
+        // timed stages run in order: overlapping kernels would blur their times
+        cudaError_t e = launch_wave(W, t, scene->sm_count, s, hook, hook ? nullptr : ov);
         if (e != cudaSuccess) rc = cuda_fail(e, "wavefront launch");
     }
     return rc;
@@ -767,7 +787,7 @@ int wave_enqueue(qrt_scene scene, const qrt_view* views, uint32_t n_views, const
 int render_enqueue(qrt_scene scene, const qrt_view* views, uint32_t n_views, const float* d_albedo,
                    const float* const* d_dimage, float* d_grad, const qrt_params* params,
                    unsigned long long* counter, void* workspace, size_t ws_bytes,
-                   unsigned long long* stats, cudaStream_t s) {
+                   unsigned long long* stats, cudaStream_t s, const WaveStreams* ov) {
     Tune t = resolve_tuning(params ? &params->tuning : nullptr);
     int rc = validate_tuning(t);
     if (rc) return rc;
@@ -801,7 +821,7 @@ int render_enqueue(qrt_scene scene, const qrt_view* views, uint32_t n_views, con
     WaveArgs* W = new WaveArgs();
     RenderArgs* R = new RenderArgs();
     rc = wave_enqueue(scene, views, n_views, d_albedo, d_dimage, d_grad, params, t, workspace,
-                      ws_bytes, stats, s, *W, *R);
+                      ws_bytes, stats, s, *W, *R, ov);
     delete R;
     delete W;
     return rc;
@@ -809,9 +829,11 @@ int render_enqueue(qrt_scene scene, const qrt_view* views, uint32_t n_views, con
 
 // Scratch for a plain (non-graph) call on stream s.
 int stream_scratch(qrt_scene scene, const qrt_params* params, bool adjoint, cudaStream_t s,
-                   unsigned long long** counter, void** ws, size_t* ws_bytes) {
+                   unsigned long long** counter, void** ws, size_t* ws_bytes,
+                   const WaveStreams** ov) {
     StreamSlot& sl = scene->slot_for(s);
     *counter = sl.counter;
+    *ov = nullptr;
     Tune t = resolve_tuning(params ? &params->tuning : nullptr);
     int rc = validate_tuning(t);
     if (rc) return rc;
@@ -819,6 +841,16 @@ int stream_scratch(qrt_scene scene, const qrt_params* params, bool adjoint, cuda
         // one workspace per stream, sized for the adjoint so both fit
         rc = ensure_workspace(sl, wave_workspace_bytes(1ull << t.chunk_log2, true), s);
         if (rc) return rc;
+        // the second stream is made outside capture; a capture started
+        // before the first render on this stream runs the stages in order
+        if (!sl.ov.aux) {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+                cudaError_t e = create_streams(sl.ov);
+                if (e != cudaSuccess) return cuda_fail(e, "overlap stream");
+            }
+        }
+        if (sl.ov.aux) *ov = &sl.ov;
     }
     (void)adjoint;
     *ws = sl.ws;
@@ -847,10 +879,11 @@ int qrt_render_spp(qrt_scene scene, const qrt_view* views, uint32_t n_views, con
     unsigned long long* ctr;
     void* ws;
     size_t wsb;
-    rc = stream_scratch(scene, params, false, s, &ctr, &ws, &wsb);
+    const WaveStreams* ov = nullptr;
+    rc = stream_scratch(scene, params, false, s, &ctr, &ws, &wsb, &ov);
     if (rc) return rc;
     return render_enqueue(scene, views, n_views, d_albedo, nullptr, nullptr, params, ctr, ws, wsb,
-                          nullptr, s);
+                          nullptr, s, ov);
 }
 
 // qrt_render_spp without any allocation: the wavefront renderer with its
@@ -879,7 +912,8 @@ int qrt_render_spp_static(qrt_scene scene, const qrt_view* views, uint32_t n_vie
     WaveArgs W;  // parameter blocks on the stack: nothing is allocated
     RenderArgs R;
     return wave_enqueue(scene, views, n_views, d_albedo, nullptr, nullptr, params, t, ws,
-                        kStaticWorkspaceBytes, nullptr, reinterpret_cast<cudaStream_t>(stream), W, R);
+                        kStaticWorkspaceBytes, nullptr, reinterpret_cast<cudaStream_t>(stream), W, R,
+                        nullptr);
 }
 
 // Same as qrt_render_spp with traversal counters added into d_stats (device
@@ -896,10 +930,11 @@ int qrt_render_spp_stats(qrt_scene scene, const qrt_view* views, uint32_t n_view
     unsigned long long* ctr;
     void* ws;
     size_t wsb;
-    rc = stream_scratch(scene, params, false, s, &ctr, &ws, &wsb);
+    const WaveStreams* ov = nullptr;
+    rc = stream_scratch(scene, params, false, s, &ctr, &ws, &wsb, &ov);
     if (rc) return rc;
     return render_enqueue(scene, views, n_views, d_albedo, nullptr, nullptr, params, ctr, ws, wsb,
-                          d_stats, s);
+                          d_stats, s, ov);
 }
 
 int qrt_trace_stats(qrt_scene scene, int any, const qrt_ray* d_rays, uint64_t n, void* d_out,
@@ -935,10 +970,11 @@ int qrt_render_adjoint(qrt_scene scene, const qrt_view* views, uint32_t n_views,
     unsigned long long* ctr;
     void* ws;
     size_t wsb;
-    rc = stream_scratch(scene, params, true, s, &ctr, &ws, &wsb);
+    const WaveStreams* ov = nullptr;
+    rc = stream_scratch(scene, params, true, s, &ctr, &ws, &wsb, &ov);
     if (rc) return rc;
     return render_enqueue(scene, views, n_views, d_albedo, d_dimage, d_grad_albedo, params, ctr, ws,
-                          wsb, nullptr, s);
+                          wsb, nullptr, s, ov);
 }
 
 int qrt_l2_loss(const float* d_img, const float* d_target, uint64_t n, double* d_loss,
@@ -990,9 +1026,12 @@ int qrt_render_graph_create(qrt_scene scene, const qrt_view* views, uint32_t n_v
         return cuda_fail(e, "graph scratch");
     }
     cudaStream_t cs = nullptr;
+    WaveStreams ov;  // joins the capture through its fork event, so the graph keeps the overlap
     e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess && tg.mode == 2) e = create_streams(ov);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) {
+        destroy_streams(ov);
         if (cs) cudaStreamDestroy(cs);
         cudaFree(g->d_counter);
         cudaFree(g->ws);
@@ -1000,10 +1039,11 @@ int qrt_render_graph_create(qrt_scene scene, const qrt_view* views, uint32_t n_v
         return cuda_fail(e, "graph capture");
     }
     rc = render_enqueue(scene, views, n_views, d_albedo, nullptr, nullptr, params, g->d_counter,
-                        g->ws, wsb, nullptr, cs);
+                        g->ws, wsb, nullptr, cs, ov.aux ? &ov : nullptr);
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
     cudaStreamDestroy(cs);
+    destroy_streams(ov);
     if (rc == QRT_OK && e2 != cudaSuccess) rc = cuda_fail(e2, "graph capture");
     if (rc == QRT_OK) {
         g->graph = graph;

@@ -322,7 +322,8 @@ cudaError_t static_workspace(void** ptr) {
 
 // One pass over paths [P0, P0 + n) of the launch.
 static cudaError_t wave_pass(WaveArgs& A, uint64_t P0, uint32_t n, int replay, const Tune& t,
-                             int sm_count, cudaStream_t s, StageHook* hook) {
+                             int sm_count, cudaStream_t s, StageHook* hook, const WaveStreams* ov) {
+    const bool overlap = ov && ov->aux && A.P.sun_on;
     A.P0 = P0;
     cudaError_t e = cudaMemsetAsync(A.B.ctr, 0, sizeof(uint32_t) * kCtrStride * (A.P.max_depth + 2), s);
     if (e != cudaSuccess) return e;
@@ -330,27 +331,42 @@ static cudaError_t wave_pass(WaveArgs& A, uint64_t P0, uint32_t n, int replay, c
     wave_gen<<<(n + 255) / 256, 256, 0, s>>>(A, P0, n);
     if (hook) hook->end(kStageGen, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    bool shadow_pending = false;
     for (uint32_t i = 1; i <= A.P.max_depth; ++i) {
         if (hook) hook->begin(kStageTrace, s);
         e = launch_wave_trace<false>(A, (int)i, t, sm_count, s);
         if (hook) hook->end(kStageTrace, s);
         if (e != cudaSuccess) return e;
+        // shade(i) adds into the radiance that shadow(i - 1) adds into
+        if (shadow_pending && (e = cudaStreamWaitEvent(s, ov->join, 0)) != cudaSuccess) return e;
+        shadow_pending = false;
         if (hook) hook->begin(kStageShade, s);
         wave_shade<<<(n + 255) / 256, 256, 0, s>>>(A, (int)i, replay);
         if (hook) hook->end(kStageShade, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (A.P.sun_on) {
-            if (hook) hook->begin(kStageShadow, s);
-            e = launch_wave_trace<true>(A, (int)i, t, sm_count, s);
-            if (hook) hook->end(kStageShadow, s);
+            cudaStream_t ss = s;
+            if (overlap) {
+                if ((e = cudaEventRecord(ov->fork, s)) != cudaSuccess) return e;
+                if ((e = cudaStreamWaitEvent(ov->aux, ov->fork, 0)) != cudaSuccess) return e;
+                ss = ov->aux;
+            }
+            if (hook) hook->begin(kStageShadow, ss);
+            e = launch_wave_trace<true>(A, (int)i, t, sm_count, ss);
+            if (hook) hook->end(kStageShadow, ss);
             if (e != cudaSuccess) return e;
+            if (overlap) {
+                if ((e = cudaEventRecord(ov->join, ss)) != cudaSuccess) return e;
+                shadow_pending = true;
+            }
         }
     }
+    if (shadow_pending && (e = cudaStreamWaitEvent(s, ov->join, 0)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
-cudaError_t launch_wave(WaveArgs& A, const Tune& t, int sm_count, cudaStream_t s,
-                        StageHook* hook) {
+cudaError_t launch_wave(WaveArgs& A, const Tune& t, int sm_count, cudaStream_t s, StageHook* hook,
+                        const WaveStreams* ov) {
     // chunks of at most A.capacity paths, cut at pixel boundaries
     uint64_t P_total = 0;
     for (uint32_t v = 0; v < A.n_views; ++v)
@@ -370,13 +386,13 @@ cudaError_t launch_wave(WaveArgs& A, const Tune& t, int sm_count, cudaStream_t s
         }
         const uint32_t n = (uint32_t)(P1 - P0);
         if (A.grad) {
-            if ((e = wave_pass(A, P0, n, 0, t, sm_count, s, hook)) != cudaSuccess) return e;
+            if ((e = wave_pass(A, P0, n, 0, t, sm_count, s, hook, ov)) != cudaSuccess) return e;
             // radiance of pass one becomes Ltot; L restarts at zero in the replay
             e = cudaMemcpyAsync(A.B.Ltot, A.B.L, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s);
             if (e != cudaSuccess) return e;
-            if ((e = wave_pass(A, P0, n, 1, t, sm_count, s, hook)) != cudaSuccess) return e;
+            if ((e = wave_pass(A, P0, n, 1, t, sm_count, s, hook, ov)) != cudaSuccess) return e;
         } else {
-            if ((e = wave_pass(A, P0, n, 0, t, sm_count, s, hook)) != cudaSuccess) return e;
+            if ((e = wave_pass(A, P0, n, 0, t, sm_count, s, hook, ov)) != cudaSuccess) return e;
             // pixels of this chunk: items whose paths lie in [P0, P1)
             int v0 = 0;
             for (int v = 0; v < (int)A.n_views; ++v)

@@ -34,6 +34,16 @@ struct WaveBufs {
 // Host-side hook around each stage launch (stage timers); may be null.
 enum Stage { kStageGen = 0, kStageTrace = 1, kStageShade = 2, kStageShadow = 3, kStageAccum = 4,
              kStages = 5 };
+// A second stream and two events that let the shadow rays of depth i run
+// beside the closest-hit rays of depth i + 1 (both read what shade(i)
+// wrote and write disjoint buffers), so each persistent launch's draining
+// tail is filled by the other.  aux == nullptr runs the stages in order on
+// one stream.  Results do not depend on it.
+struct WaveStreams {
+    cudaStream_t aux = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+
 struct StageHook {
     virtual void begin(int stage, cudaStream_t s) = 0;
     virtual void end(int stage, cudaStream_t s) = 0;
@@ -71,7 +81,7 @@ constexpr size_t kStaticWorkspaceBytes = wave_workspace_bytes(1ull << kStaticChu
 // device with cudaGetSymbolAddress; allocates nothing).
 cudaError_t static_workspace(void** ptr);
 void wave_carve(void* base, uint64_t capacity, bool adjoint, WaveBufs& B);
-cudaError_t launch_wave(WaveArgs& A, const Tune& t, int sm_count, cudaStream_t s,
-                        StageHook* hook = nullptr);
+cudaError_t launch_wave(WaveArgs& A, const Tune& t, int sm_count, cudaStream_t s, StageHook* hook,
+                        const WaveStreams* ov);
 
 }  // namespace qrt

@@ -160,6 +160,30 @@ def test_wavefront_equals_single_kernel(api, tiny, chunk_log2):
     assert torch.equal(log1, log2)
 
 
+def test_overlapped_stages_equal_ordered_stages(api, tiny):
+    """An untimed wavefront render runs each depth's shadow rays on a second
+    stream beside the next depth's closest-hit rays; a timed render and the
+    single-kernel renderer run everything in order.  A captured graph keeps
+    the overlap.  All give the same bits, on a stream of the caller's."""
+    sc, gs, osc = tiny
+    view = I.tiny_view()
+    view.w, view.h, view.spp = 160, 96, 3
+    params = I.Params(max_depth=5, sun_dir=I.MID_SUN_DIR, sun_E=(3.0, 2.0, 1.0))
+    alb = torch.from_numpy(I.albedo(sc.n_quads)).cuda()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        (a,) = gs.render([view], alb, params, tuning=dict(chunk_log2=12))
+        (b,) = gs.render([view], alb, params, tuning=dict(chunk_log2=12), stage_times=True)
+        (c,) = gs.render([view], alb, params, tuning=dict(mode=1))
+        g = api.RenderGraph(gs, [view], alb, params, tuning=dict(chunk_log2=12))
+        (d,) = g.launch()
+    s.synchronize()
+    gs.check()
+    gs.stage_times(reset=True)
+    assert torch.equal(a, b) and torch.equal(a, c) and torch.equal(a, d)
+    g.close()
+
+
 def test_adjoint_modes_agree(api, tiny):
     sc, gs, osc = tiny
     view = I.tiny_view()
