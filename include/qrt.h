@@ -122,8 +122,10 @@ typedef struct {
  *                  gen / trace / shade / shadow / accumulate over queues; a
  *                  lane of a trace kernel takes a new ray as soon as its own
  *                  is done).  Both give bit-identical images.
- *   chunk_log2     wavefront: paths per chunk = 2^chunk_log2 (10..26,
- *                  default 21); sets the size of the per-stream workspace */
+ *   chunk_log2     wavefront: paths per chunk = 2^chunk_log2 (10..26); 0 =
+ *                  fit the call: the smallest 2^k >= its paths, k in
+ *                  10..24.  Sets the size of the per-stream workspace
+ *                  (about 164 B per path; it grows when a call needs more) */
 typedef struct {
     uint32_t block;
     uint32_t blocks_per_sm;

@@ -54,7 +54,7 @@ struct Tune {
     int fetch = 32;         // node fetch bytes per load: 16 or 32
     int occupancy = 32;     // trace kernels: target resident warps per SM (16, 24 or 32)
     int mode = 2;           // 1 = single persistent kernel, 2 = wavefront
-    int chunk_log2 = 21;    // wavefront paths per chunk = 2^chunk_log2
+    int chunk_log2 = 0;     // wavefront paths per chunk = 2^chunk_log2; 0 = fit the call
 };
 
 // A view with its camera basis precomputed on the host (FP64 -> FP32).
