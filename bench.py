@@ -461,6 +461,10 @@ def main():
                      "algorithmic_bytes_per_launch": closest_bytes / max(1.0, launches_step),
                      "peak_kind": f"{peak_kind} hbm_gbs ({'of measured' if peak_kind == 'measured' else 'of fallback'})",
                      "l2_read_gbs": l2_gbs, "l2_frac": achieved / l2_gbs if achieved else None,
+                     # loose upper bound: 48 compulsory bytes per ray (32 B ray in,
+                     # 16 B hit out) against the HBM copy bandwidth
+                     "compulsory_bound_grays_s": hbm / 48.0,
+                     "compulsory_frac": (value / 1e3) / (hbm / 48.0),
                      "l2_kind": "measured here: qrt_read_bandwidth over a 64 MB buffer, 40 sweeps",
                      "frame_algorithmic_gbs": frame_bytes / (ms * 1e-3) / 1e9},
         "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
