@@ -11,6 +11,7 @@ torch = pytest.importorskip("torch")
 import oracle as O
 from paper_2001_02620_gb300 import inputs as I
 
+from golden_data import table1
 from parity import NONE, classify_closest, path_agreement, split_log
 
 pytestmark = pytest.mark.gpu
@@ -86,6 +87,24 @@ def test_mid_trace_closest_and_any(api, mid):
         occ = ((bits[np.arange(len(rays)) // 32] >> (np.arange(len(rays)) % 32)) & 1).astype(bool)
         assert (occ != (o_i != NONE)).sum() <= acc, name
     assert acc_all / total < 1e-5, f"{acc_all} near-tie mismatches in {total} rays"
+
+
+def test_mid_frame_time_is_dominated_by_traversal(api, mid):
+    """The paper's Table 1 finds 67-75 % of a frame in ray traversal and
+    intersection with full shading; with its plain diffuse shading this
+    renderer must spend at least the paper's smallest share there."""
+    sc, gs, osc = mid
+    view, params = I.mid_view(), I.mid_params()
+    alb = torch.from_numpy(I.albedo(sc.n_quads)).cuda()
+    gs.render([view], alb, params)
+    gs.stage_times(reset=True)
+    for _ in range(2):
+        gs.render([view], alb, params, stage_times=True)
+    st = gs.stage_times(reset=True)
+    total = sum(v[0] for v in st.values())
+    traversal = st["trace_closest"][0] + st["trace_shadow"][0]
+    assert st["trace_closest"][1] == 2 * params.max_depth
+    assert traversal / total >= min(table1()["traversal_and_intersection"]) / 100.0
 
 
 def test_mid_batched_equals_plain(api, mid):
