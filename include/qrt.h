@@ -124,7 +124,7 @@ typedef struct {
  *                  is done).  Both give bit-identical images.
  *   chunk_log2     wavefront: paths per chunk = 2^chunk_log2 (10..26); 0 =
  *                  fit the call: the smallest 2^k >= its paths, k in
- *                  10..24.  Sets the size of the per-stream workspace
+ *                  10..25.  Sets the size of the per-stream workspace
  *                  (about 164 B per path; it grows when a call needs more) */
 typedef struct {
     uint32_t block;

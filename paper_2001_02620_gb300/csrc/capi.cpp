@@ -226,9 +226,10 @@ Tune resolve_tuning(const qrt_tuning* t) {
 // Default wavefront chunk: the smallest 2^k >= the call's paths, k in
 // [10, kFitChunkMax].  One chunk per call where it fits: every chunk pays
 // its own run of draining launches, and a whole mid frame (2^22 paths) in
-// one chunk renders 1.12x faster than in two.  2^24 paths of workspace is
-// about 2.8 GB (adjoint included) per stream.
-constexpr int kFitChunkMax = 24;
+// one chunk renders 1.12x faster than in two (a Moana-scale frame of 2^25
+// paths: 1.03x faster than in two).  2^25 paths of workspace is about 5.5 GB
+// (adjoint included) per stream, 2 % of GB300's memory.
+constexpr int kFitChunkMax = 25;
 
 void fit_chunk(Tune& t, const qrt_view* views, uint32_t n_views) {
     if (t.chunk_log2 != 0) return;
