@@ -106,10 +106,12 @@ typedef struct {
 } qrt_view;
 
 /* Launch tuning; 0 in any field selects the library default.
- *   block          threads per block (64..1024, multiple of 32)
- *   blocks_per_sm  resident blocks per SM for persistent kernels
+ *   block          threads per block: 64, 128 (default), 192 or 256
+ *   blocks_per_sm  resident blocks per SM for persistent kernels (default:
+ *                  as many as the register budget allows)
  *   batch          single kernel: pixels a warp claims per fetch, in units
- *                  of 32; wavefront: rays a lane claims per fetch
+ *                  of 32; wavefront and ray queries: rays a lane claims per
+ *                  fetch (1..64, default 1)
  *   stack          traversal stack entries per ray (32 or 64)
  *   fetch          node fetch width in bytes (16: 4x128-bit, 32: 2x256-bit
  *                  loads, default)

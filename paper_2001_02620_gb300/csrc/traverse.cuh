@@ -18,11 +18,19 @@
 // number of the transform), so a node is never culled
 // that the exact ray enters.  The quad test is the watertight test of Woop,
 // Benthin and Wald (JCGT 2013) applied to both triangles of the quad with the
-// diagonal v0-v2 shared; an edge function within the same error bound of zero
+// diagonal v0-v2 shared; an edge function within the same error bound of zero,
+// or a hit distance within its error bound of either end of the interval,
 // makes the decision uncertain, and only then the quad is re-tested in FP64
-// from the world ray and the FP64 transform.  Hit/miss decisions therefore
-// agree with exact arithmetic on the given FP32 ray except when a hit lies
-// within FP64 rounding of an edge.
+// from the world ray and the FP64 transform; two hits whose FP32 distances
+// lie within their error bounds of each other are ordered by FP64 distances.
+// Hit/miss decisions and the closest-hit choice therefore agree with exact
+// arithmetic on the given FP32 ray except when a hit lies within FP64
+// rounding of an edge or of another hit.
+//
+// Execution.  Persistent kernels run persistent_trace: each lane of a warp
+// holds one ray; the warp tests inner nodes together, enters instances in
+// groups, then lets every other lane enter its instance or test one leaf;
+// finished lanes take the next ray at once (claimed one atomic per warp).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>

@@ -11,7 +11,9 @@
 //              shadow ray toward the sun (pending term beta*a/pi*E*cos),
 //              multiply beta by a and queue the bounce ray for depth i+1
 //     shadow   persistent any-hit kernel over the shadow queue; an
-//              unoccluded ray adds its pending term to the path
+//              unoccluded ray adds its pending term to the path (on a second
+//              stream, beside the trace of depth i+1, unless the render is
+//              timed stage by stage; shade i+1 waits for it)
 //   accumulate mean over each pixel's samples, summed in sample order
 // The adjoint runs the chunk twice: a primal pass that leaves each path's
 // radiance in Ltot, then a replay pass whose shade stage adds
