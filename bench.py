@@ -277,8 +277,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mrays/s", "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "mid: 64 prototypes + 2048^2-quad terrain, 100k instances, "
-                                   "1024x1024, 4 spp, depth 5, env + sun"},
+            "config": {"workload": WORKLOADS["mid"],
+                       "parallelism": f"{base['cores']} host threads (FP64 oracle)"},
             "cpu_baseline": {"value": v, "unit": "Mrays/s", "cores": base["cores"], "kind": "oracle",
                              "sample": base["sample"]},
             "e2e": {"value": v, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
