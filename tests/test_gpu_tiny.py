@@ -66,6 +66,33 @@ def test_trace_closest_matches_oracle(api, tiny, tuning):
     assert np.all(gt[miss] == rays[miss, 7])
 
 
+def test_trace_closest_interval_windows(api, tiny):
+    """Rays with a window tmin < t < tmax cut out of their path (the open
+    interval of the ray queries): hits before tmin or after tmax must not be
+    reported, and the object-space re-centring at max(tmin, box entry) must
+    keep the hits inside the window exact."""
+    sc, gs, osc = tiny
+    rays = _rays(sc)
+    rng = np.random.default_rng(77)
+    half = rng.random(len(rays)) < 0.5
+    t0 = rng.uniform(0.0, 120.0, size=len(rays)).astype(np.float32)
+    rays[half, 3] = t0[half]
+    rays[half, 7] = t0[half] + rng.uniform(2.0, 60.0, size=half.sum()).astype(np.float32)
+    d_rays = torch.from_numpy(rays).cuda()
+    hits = gs.trace_closest(d_rays)
+    gs.check()
+    h = hits.cpu().numpy().view(np.uint32)
+    o_t, o_i, o_p, _, _ = osc.trace_closest(rays)
+    n, acc, bad = classify_closest(sc, rays, h[:, 1], h[:, 2], o_t, o_i, o_p)
+    assert not bad, f"{len(bad)} unexplained mismatches, e.g. ray {bad[:5]}"
+    assert acc / len(rays) < 1e-5
+    hit = o_i != NONE
+    assert hit[half].mean() > 0.05 and (~hit[half]).mean() > 0.05
+    gt = h[:, 0].view(np.float32).astype(np.float64)
+    got = h[:, 1] != NONE
+    assert np.all(gt[got] > rays[got, 3]) and np.all(gt[got] < rays[got, 7])
+
+
 @pytest.mark.parametrize("tuning", SETTINGS[:3])
 def test_trace_any_matches_oracle(api, tiny, tuning):
     sc, gs, osc = tiny
