@@ -241,6 +241,45 @@ def bench_batched(api, scene, d_alb, dev, tuning=None, views=None):
             "batched_ms": tb * 1e3, "plain_ms": tp * 1e3}
 
 
+def bench_progressive(api, scene, view, d_alb, params, dev, tuning=None, warm=64, frames=64):
+    """Progressive rendering as the paper runs it (Section 5.4: one sample
+    per pixel per frame, accumulated; Section 6: 64 warm-up frames, then 64
+    measured): each frame renders spp = 1 at sample_base = frame number and
+    adds into a device sum (qrt_accumulate), which also writes the mean."""
+    import dataclasses
+    import torch
+    img = torch.empty((view.h, view.w, 3), device=dev)
+    acc = torch.zeros_like(img)
+    mean = torch.empty_like(img)
+
+    def frame(f):
+        fv = dataclasses.replace(view, spp=1, sample_base=f)
+        scene.render([fv], d_alb, params, outs=[img], tuning=tuning)
+        api.accumulate(acc, img, f + 1, mean)
+
+    for f in range(warm):
+        frame(f)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for f in range(warm, warm + frames):
+        frame(f)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / frames
+    # rays of the measured frames: one counting render of the same samples
+    stats = torch.zeros(12, dtype=torch.int64, device=dev)
+    scene.render([dataclasses.replace(view, spp=frames, sample_base=warm)], d_alb, params,
+                 outs=[torch.empty_like(img)], stats=stats, tuning=tuning)
+    st = stats.cpu().numpy()
+    rays = int(st[0] + st[6]) / frames
+    scene.check()
+    return {"frames": frames, "warmup_frames": warm, "spp_per_frame": 1,
+            "resolution": [view.w, view.h], "ms_per_frame": ms, "fps": 1e3 / ms,
+            "rays_per_frame": rays, "mrays_s": rays / (ms * 1e-3) / 1e6}
+
+
 def bench_adjoint(api, scene, sc, dev, tuning=None):
     """Adjoint workload (512x512, 8 spp, depth 4): replay adjoint vs primal."""
     import torch
@@ -293,7 +332,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--extras", default="trace,batched,adjoint",
+    ap.add_argument("--extras", default="trace,batched,adjoint,progressive",
                     help="comma list of sub-measurements to add (or 'none')")
     ap.add_argument("--res", type=int, default=0,
                     help="override the view side (small profiling captures only)")
@@ -505,7 +544,7 @@ def main():
     }
     extras = [] if args.extras == "none" else args.extras.split(",")
     if args.workload != "mid":
-        extras = [e for e in extras if e == "trace"]
+        extras = [e for e in extras if e in ("trace", "progressive")]
     if "trace" in extras:
         line["trace"] = bench_trace(scene, sc, dev, tuning, eye=view.eye)
     if "batched" in extras:
@@ -517,6 +556,8 @@ def main():
             views=I.batched_views(n_views=64, min_log2=5.0, max_log2=7.0, max_spp=4))
     if "adjoint" in extras:
         line["adjoint_vs_primal"] = bench_adjoint(api, scene, sc, dev, tuning)
+    if "progressive" in extras:
+        line["progressive"] = bench_progressive(api, scene, view, d_alb, params, dev, tuning)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = oracle_sample(sc, view, params, alb, budget_s=12.0,
                                              frame=f"{view.w}x{view.h} {args.workload}")

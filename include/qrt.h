@@ -92,15 +92,19 @@ typedef struct {
  * (x + xi1, y + xi2); vfov is the vertical field of view in degrees.
  * pixel_base gives the first global pixel index of this view: the random
  * stream of a sample is keyed by (pixel_base + y*w + x, sample, bounce), so
- * distinct views should use disjoint ranges.  out_rgb: DEVICE float [h*w*3],
- * row-major, receives the mean radiance over spp samples (overwritten). */
+ * distinct views should use disjoint ranges.  The call draws samples
+ * sample_base .. sample_base + spp - 1 of every pixel: progressive rendering
+ * (Section 5.4, one sample per pixel per frame) passes the frame number with
+ * spp = 1 and sums the frames with qrt_accumulate.  out_rgb: DEVICE float
+ * [h*w*3], row-major, receives the mean radiance over the call's spp samples
+ * (overwritten). */
 typedef struct {
     float eye[3];
     float look[3];
     float up[3];
     float vfov_deg;
     uint32_t w, h, spp;
-    uint32_t reserved0;
+    uint32_t sample_base;
     uint64_t pixel_base;
     float* out_rgb;
 } qrt_view;
@@ -269,6 +273,16 @@ int qrt_render_spp_static(qrt_scene scene, const qrt_view* views, uint32_t n_vie
 int qrt_render_adjoint(qrt_scene scene, const qrt_view* views, uint32_t n_views,
                        const float* d_albedo, const float* const* d_dimage,
                        float* d_grad_albedo, const qrt_params* params, qrt_stream stream);
+
+/* Progressive accumulation on the device: d_sum[i] += d_frame[i] for i < n
+ * (FP32, in call order) and, if d_mean is not NULL, d_mean[i] = d_sum[i] /
+ * frames, where frames counts the frames summed so far (including this
+ * one, >= 1).  Frames rendered with spp = 1 and sample_base = 0, 1, 2, ...
+ * summed from a zeroed d_sum give exactly the image of one call with
+ * spp = frames: the renderer sums a pixel's samples in the same order.
+ * All pointers DEVICE float [n]; d_mean may alias d_frame. */
+int qrt_accumulate(float* d_sum, const float* d_frame, float* d_mean, uint64_t n, uint32_t frames,
+                   qrt_stream stream);
 
 /* Mean-squared image loss and its gradient on the device:
  * *d_loss = sum_i (img_i - target_i)^2 / n and d_dimage_i = 2 (img_i - target_i) / n

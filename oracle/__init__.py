@@ -40,7 +40,7 @@ def build(force: bool = False) -> str:
 class _View(C.Structure):
     _fields_ = [("eye", C.c_float * 3), ("look", C.c_float * 3), ("up", C.c_float * 3),
                 ("vfov_deg", C.c_float), ("w", C.c_uint32), ("h", C.c_uint32),
-                ("spp", C.c_uint32), ("pixel_base", C.c_uint64)]
+                ("spp", C.c_uint32), ("sample_base", C.c_uint32), ("pixel_base", C.c_uint64)]
 
 
 class _Params(C.Structure):
@@ -119,6 +119,7 @@ def _view(v) -> _View:
     cv.up[:] = [float(x) for x in v.up]
     cv.vfov_deg = float(v.vfov_deg)
     cv.w, cv.h, cv.spp, cv.pixel_base = int(v.w), int(v.h), int(v.spp), int(v.pixel_base)
+    cv.sample_base = int(getattr(v, "sample_base", 0))
     return cv
 
 

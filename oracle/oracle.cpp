@@ -520,11 +520,13 @@ struct PathRecord {
     bool escaped = false;  // the ray after the last vertex left the scene
 };
 
-// One path sample; returns radiance (with the given albedo) and its record.
+// One path sample (the view's sample sample_base + k); returns radiance
+// (with the given albedo) and its record.
 void trace_path(const ora_scene& s, const ora_view& view, const float* albedo,
-                const ora_params& p, uint32_t x, uint32_t y, uint32_t smp, double L[3],
+                const ora_params& p, uint32_t x, uint32_t y, uint32_t k, double L[3],
                 PathRecord* rec, uint32_t* log_inst, uint32_t* log_prim, uint32_t* log_shadow) {
     const uint64_t pix = view.pixel_base + (uint64_t)y * view.w + x;
+    const uint32_t smp = view.sample_base + k;  // Philox counter: (pixel, sample, bounce)
     double xi[4];
     draw4(p.seed, pix, smp, 0, xi);
     V3 o, d;

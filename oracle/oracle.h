@@ -47,6 +47,7 @@ typedef struct {
     float eye[3], look[3], up[3];
     float vfov_deg;
     uint32_t w, h, spp;
+    uint32_t sample_base;  // samples sample_base .. sample_base + spp - 1 are drawn
     uint64_t pixel_base;
 } ora_view;
 

@@ -40,7 +40,7 @@ class qrt_mesh(C.Structure):
 class qrt_view(C.Structure):
     _fields_ = [("eye", C.c_float * 3), ("look", C.c_float * 3), ("up", C.c_float * 3),
                 ("vfov_deg", C.c_float), ("w", C.c_uint32), ("h", C.c_uint32),
-                ("spp", C.c_uint32), ("reserved0", C.c_uint32), ("pixel_base", C.c_uint64),
+                ("spp", C.c_uint32), ("sample_base", C.c_uint32), ("pixel_base", C.c_uint64),
                 ("out_rgb", C.c_void_p)]
 
 
@@ -88,6 +88,7 @@ SIGNATURES = {
     "qrt_render_spp_static": (_i, [_vp, C.POINTER(qrt_view), _u32, _vp, C.POINTER(qrt_params), _vp]),
     "qrt_render_adjoint": (_i, [_vp, C.POINTER(qrt_view), _u32, _vp, C.POINTER(_vp), _vp,
                                 C.POINTER(qrt_params), _vp]),
+    "qrt_accumulate": (_i, [_vp, _vp, _vp, _u64, _u32, _vp]),
     "qrt_l2_loss": (_i, [_vp, _vp, _u64, _vp, _vp, _vp]),
     "qrt_read_bandwidth": (_i, [_vp, _u64, _u32, _vp, _vp]),
     "qrt_render_graph_create": (_i, [_vp, C.POINTER(qrt_view), _u32, _vp, C.POINTER(qrt_params),

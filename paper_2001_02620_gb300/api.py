@@ -53,6 +53,7 @@ def make_views(views, outs) -> C.Array:
         cv.vfov_deg = float(v.vfov_deg)
         cv.w, cv.h, cv.spp = int(v.w), int(v.h), int(v.spp)
         cv.pixel_base = int(v.pixel_base)
+        cv.sample_base = int(getattr(v, "sample_base", 0))
         cv.out_rgb = _ptr(o)
     return arr
 
@@ -233,6 +234,15 @@ def read_bandwidth_gbs(nbytes: int, reps: int, stream=None) -> float:
     e1.record(s)
     e1.synchronize()
     return buf.numel() * 4 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
+
+def accumulate(frame_sum: torch.Tensor, frame: torch.Tensor, frames: int,
+               mean: torch.Tensor | None = None, stream=None) -> torch.Tensor | None:
+    """Progressive accumulation (qrt_accumulate): frame_sum += frame, and
+    mean = frame_sum / frames when given (frames = frames summed so far)."""
+    N.check(N.lib().qrt_accumulate(_ptr(frame_sum), _ptr(frame), _ptr(mean), frame.numel(),
+                                   int(frames), _stream(stream)))
+    return mean
 
 
 def l2_loss(img: torch.Tensor, target: torch.Tensor, dimage: torch.Tensor | None = None,

@@ -695,7 +695,7 @@ int make_views(const qrt_view* views, uint32_t first, uint32_t count, const floa
         d.w = v.w;
         d.h = v.h;
         d.spp = v.spp;
-        d.pad = 0;
+        d.sample_base = v.sample_base;
         d.pixel_base = v.pixel_base;
         d.item_begin = items;
         d.path_begin = paths;
@@ -994,6 +994,19 @@ int qrt_render_adjoint(qrt_scene scene, const qrt_view* views, uint32_t n_views,
     if (rc) return rc;
     return render_enqueue(scene, views, n_views, d_albedo, d_dimage, d_grad_albedo, params, ctr, ws,
                           wsb, nullptr, s, ov);
+}
+
+int qrt_accumulate(float* d_sum, const float* d_frame, float* d_mean, uint64_t n, uint32_t frames,
+                   qrt_stream stream) {
+    if (n == 0) return QRT_OK;
+    if (!d_sum || !d_frame) return fail(QRT_ERR_INVALID_ARG, "NULL image pointer");
+    if (frames == 0) return fail(QRT_ERR_INVALID_ARG, "frames must be at least 1");
+    if (!aligned(d_sum, 4) || !aligned(d_frame, 4) || (d_mean && !aligned(d_mean, 4)))
+        return fail(QRT_ERR_ALIGN, "image pointers must be 4-byte aligned");
+    cudaError_t e = launch_accumulate(d_sum, d_frame, d_mean, n, frames,
+                                      reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "accumulate launch");
+    return QRT_OK;
 }
 
 int qrt_l2_loss(const float* d_img, const float* d_target, uint64_t n, double* d_loss,

@@ -62,7 +62,7 @@ struct ViewDev {
     float eye[3];
     float f[3], r[3], u[3];
     float sx0, sxs, sy0, sys;  // sx = sx0 + px*sxs, sy = sy0 + py*sys
-    uint32_t w, h, spp, pad;
+    uint32_t w, h, spp, sample_base;
     uint64_t pixel_base;
     uint64_t item_begin;  // first work item (pixel) of this view in the launch
     uint64_t path_begin;  // first path index of this view (for the path log)
@@ -109,6 +109,8 @@ cudaError_t launch_render(const RenderArgs& A, const Tune& t, int sm_count, cuda
 
 cudaError_t launch_read_sweep(const void* buf, uint64_t bytes, uint32_t reps, uint32_t* sink,
                               int sm_count, cudaStream_t s);
+cudaError_t launch_accumulate(float* sum, const float* frame, float* mean, uint64_t n,
+                              uint32_t frames, cudaStream_t s);
 cudaError_t launch_l2_loss(const float* img, const float* target, uint64_t n, double* loss,
                            float* dimage, cudaStream_t s);
 

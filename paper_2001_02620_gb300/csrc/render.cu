@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(256) render_kernel(const __grid_constant__ Ren
                     uint32_t* log = A.P.path_log
                                         ? A.P.path_log + (V.path_begin + pix * V.spp + s) * (2ull * D + 1)
                                         : nullptr;
-                    const uint32_t e = path_sample<STACK, FETCH>(A, V, x, y, gpix, s, 0, L, nullptr,
+                    const uint32_t e = path_sample<STACK, FETCH>(A, V, x, y, gpix, V.sample_base + s, 0, L, nullptr,
                                                                  nullptr, log, &st);
                     if (e) {
                         err |= e;
@@ -192,9 +192,9 @@ __global__ void __launch_bounds__(256) render_kernel(const __grid_constant__ Ren
                 if (w[0] == 0.f && w[1] == 0.f && w[2] == 0.f) continue;
                 for (uint32_t s = 0; s < V.spp; ++s) {
                     float L[3], L2[3];
-                    uint32_t e = path_sample<STACK, FETCH>(A, V, x, y, gpix, s, 0, L, nullptr,
+                    uint32_t e = path_sample<STACK, FETCH>(A, V, x, y, gpix, V.sample_base + s, 0, L, nullptr,
                                                            nullptr, nullptr, &st);
-                    e |= path_sample<STACK, FETCH>(A, V, x, y, gpix, s, 1, L2, L, w, nullptr, &st);
+                    e |= path_sample<STACK, FETCH>(A, V, x, y, gpix, V.sample_base + s, 1, L2, L, w, nullptr, &st);
                     if (e) {
                         err |= e;
                         bad = min(bad, item);
@@ -290,6 +290,29 @@ cudaError_t launch_l2_loss(const float* img, const float* target, uint64_t n, do
     uint64_t grid = (n + 255) / 256;
     if (grid > 4096) grid = 4096;
     l2_loss_kernel<<<(unsigned)grid, 256, 0, s>>>(img, target, n, loss, dimage);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Progressive accumulation: sum += frame; mean = sum / frames
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) accumulate_kernel(float* __restrict__ sum,
+                                                         const float* frame, float* mean,
+                                                         uint64_t n, float frames) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const float s = __fadd_rn(sum[i], frame[i]);
+        sum[i] = s;
+        if (mean) mean[i] = __fdiv_rn(s, frames);
+    }
+}
+
+cudaError_t launch_accumulate(float* sum, const float* frame, float* mean, uint64_t n,
+                              uint32_t frames, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    uint64_t grid = (n + 255) / 256;
+    if (grid > 8192) grid = 8192;
+    accumulate_kernel<<<(unsigned)grid, 256, 0, s>>>(sum, frame, mean, n, (float)frames);
     return cudaGetLastError();
 }
 

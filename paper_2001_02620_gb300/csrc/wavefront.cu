@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256) wave_gen(const __grid_constant__ WaveArgs
     const ViewDev& V = A.views[find_view_by_path(A, g)];
     const uint64_t local = g - V.path_begin;
     const uint64_t pix = local / V.spp;
-    const uint32_t smp = (uint32_t)(local - pix * V.spp);
+    const uint32_t smp = V.sample_base + (uint32_t)(local - pix * V.spp);  // global sample index
     const uint32_t x = (uint32_t)(pix % V.w), y = (uint32_t)(pix / V.w);
     const uint4 xi = draw(A.P.seed, V.pixel_base + pix, smp, 0);
     const F3 d = camera_dir(V, x, y, u01(xi.x), u01(xi.y));

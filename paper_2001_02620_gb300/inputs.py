@@ -74,6 +74,7 @@ class View:
     h: int
     spp: int
     pixel_base: int = 0
+    sample_base: int = 0  # first sample index drawn (progressive frames)
 
 
 @dataclass

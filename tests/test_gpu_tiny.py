@@ -211,6 +211,42 @@ def test_overlapped_stages_equal_ordered_stages(api, tiny):
     g.close()
 
 
+@pytest.mark.parametrize("mode", [2, 1])
+def test_progressive_frames_equal_one_render(api, tiny, mode):
+    """One sample per pixel per frame (sample_base = frame number), summed
+    with qrt_accumulate, gives exactly the image of one render with spp =
+    frames; each frame matches the oracle's sample of that index."""
+    import dataclasses
+    sc, gs, osc = tiny
+    view = I.tiny_view()
+    view.w, view.h, view.spp = 96, 64, 6
+    params = I.Params(max_depth=4, sun_dir=I.MID_SUN_DIR, sun_E=(3.0, 2.0, 1.0))
+    alb = torch.from_numpy(I.albedo(sc.n_quads)).cuda()
+    (ref,) = gs.render([view], alb, params, tuning=dict(mode=mode))
+    acc = torch.zeros_like(ref)
+    mean = torch.empty_like(ref)
+    for f in range(view.spp):
+        fv = dataclasses.replace(view, spp=1, sample_base=f)
+        (frame,) = gs.render([fv], alb, params, tuning=dict(mode=mode))
+        api.accumulate(acc, frame, f + 1, mean)
+        if f == 3:
+            pix_ok, err, r, g, _ = _render_compare(api, gs, osc, fv, I.albedo(sc.n_quads), params)
+            assert pix_ok.mean() > 0.99
+            assert (err <= 1e-4 * np.abs(r) + 1e-6).all()
+    gs.check()
+    assert torch.equal(mean, ref)
+
+
+def test_accumulate_rejects_bad_arguments(api):
+    L = api.N.lib()
+    x = torch.zeros(16, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    assert L.qrt_accumulate(x.data_ptr(), x.data_ptr(), None, 16, 0, s) == api.N.QRT_ERR_INVALID_ARG
+    assert L.qrt_accumulate(None, x.data_ptr(), None, 16, 1, s) == api.N.QRT_ERR_INVALID_ARG
+    assert L.qrt_accumulate(x.data_ptr() + 2, x.data_ptr(), None, 4, 1, s) == api.N.QRT_ERR_ALIGN
+    assert L.qrt_accumulate(None, None, None, 0, 1, s) == api.N.QRT_OK
+
+
 def test_adjoint_modes_agree(api, tiny):
     sc, gs, osc = tiny
     view = I.tiny_view()

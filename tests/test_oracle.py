@@ -424,6 +424,31 @@ def test_render_pixel_subset_matches_full_image():
     np.testing.assert_array_equal(sub, full[px])
 
 
+def test_progressive_samples_compose_to_one_render():
+    """Section 5.4 renders one sample per pixel per frame.  A view's samples
+    are drawn at sample_base + k: the mean of frames with spp = 1 and
+    sample_base = 0, 1, 2 is the 3-spp render, and a frame is the matching
+    sample of it (its path log rows)."""
+    import dataclasses
+    sc = I.tiny_scene()
+    osc = O.OracleScene(sc)
+    view = I.tiny_view()
+    view.w = view.h = 32
+    view.spp = 3
+    alb = I.albedo(sc.n_quads)
+    p = I.Params(max_depth=3, sun_dir=I.MID_SUN_DIR, sun_E=(3.0, 3.0, 3.0))
+    full = osc.render(view, alb, p, log=True)
+    frames = [osc.render(dataclasses.replace(view, spp=1, sample_base=k), alb, p, log=True)
+              for k in range(3)]
+    acc = (frames[0]["rgb"] + frames[1]["rgb"]) + frames[2]["rgb"]
+    np.testing.assert_array_equal(acc / 3.0, full["rgb"])
+    for k in range(3):
+        np.testing.assert_array_equal(frames[k]["inst"], full["inst"][k::3])
+        np.testing.assert_array_equal(frames[k]["prim"], full["prim"][k::3])
+    # a different sample index draws a different path somewhere
+    assert not np.array_equal(frames[0]["inst"], frames[1]["inst"])
+
+
 # ---------------------------------------------------------------------------
 # Gradient
 # ---------------------------------------------------------------------------
