@@ -280,6 +280,20 @@ def bench_progressive(api, scene, view, d_alb, params, dev, tuning=None, warm=64
             "rays_per_frame": rays, "mrays_s": rays / (ms * 1e-3) / 1e6}
 
 
+def bench_cost_map(api, scene, view, d_alb, params, dev, tuning=None):
+    """Per-pixel traversal cost of the frame (the paper's cost heat map):
+    mean inner BVH nodes visited per sample, summarised."""
+    import torch
+    stats = torch.zeros(12, dtype=torch.int64, device=dev)
+    (cost,) = scene.cost_maps([view], d_alb, params, stats, tuning=tuning)
+    c = cost.flatten().double()
+    q = torch.quantile(c[torch.randperm(c.numel(), device=c.device)[:1 << 20]],
+                       torch.tensor([0.5, 0.9, 0.99], dtype=torch.float64, device=c.device))
+    return {"unit": "inner BVH nodes visited per path sample (closest-hit and shadow rays)",
+            "mean": float(c.mean()), "p50": float(q[0]), "p90": float(q[1]), "p99": float(q[2]),
+            "max": float(c.max()), "pixels": int(c.numel())}
+
+
 def bench_adjoint(api, scene, sc, dev, tuning=None):
     """Adjoint workload (512x512, 8 spp, depth 4): replay adjoint vs primal."""
     import torch
@@ -332,7 +346,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--extras", default="trace,batched,adjoint,progressive",
+    ap.add_argument("--extras", default="trace,batched,adjoint,progressive,costmap",
                     help="comma list of sub-measurements to add (or 'none')")
     ap.add_argument("--res", type=int, default=0,
                     help="override the view side (small profiling captures only)")
@@ -540,11 +554,13 @@ def main():
         "scene_build_s": build_s, "scene_gen_s": gen_s,
         "scene": {k: scene.stats[k] for k in ("n_quads", "n_instances", "blas_nodes", "tlas_nodes",
                                               "device_bytes", "max_blas_depth", "tlas_depth")},
+        "build_phase_s": dict(zip(("blas_build", "blas_check", "instances", "tlas", "concat", "upload"),
+                                  scene.stats["phase_seconds"])),
         "tuning": tuning, "tune_s": tune_s,
     }
     extras = [] if args.extras == "none" else args.extras.split(",")
     if args.workload != "mid":
-        extras = [e for e in extras if e in ("trace", "progressive")]
+        extras = [e for e in extras if e in ("trace", "progressive", "costmap")]
     if "trace" in extras:
         line["trace"] = bench_trace(scene, sc, dev, tuning, eye=view.eye)
     if "batched" in extras:
@@ -556,6 +572,8 @@ def main():
             views=I.batched_views(n_views=64, min_log2=5.0, max_log2=7.0, max_spp=4))
     if "adjoint" in extras:
         line["adjoint_vs_primal"] = bench_adjoint(api, scene, sc, dev, tuning)
+    if "costmap" in extras:
+        line["cost_map"] = bench_cost_map(api, scene, view, d_alb, params, dev, tuning)
     if "progressive" in extras:
         line["progressive"] = bench_progressive(api, scene, view, d_alb, params, dev, tuning)
     if rank == 0 and not args.no_cpu_baseline and world == 1:

@@ -194,13 +194,16 @@ typedef struct {
     uint32_t inst_boxes;
 } qrt_build_opts;
 
-/* Scene statistics (host). */
+/* Scene statistics (host).  build_seconds covers the host build (phases
+ * 0-4); phase_seconds: 0 BLAS builds, 1 BLAS checks, 2 instance records and
+ * bounds, 3 TLAS build and check, 4 concatenation, 5 upload. */
 typedef struct {
     uint64_t n_meshes, n_instances, n_quads;
     uint64_t blas_nodes, tlas_nodes;
     uint64_t device_bytes;
     uint32_t max_blas_depth, tlas_depth;
     double build_seconds;
+    double phase_seconds[6];
 } qrt_scene_stats;
 
 const char* qrt_last_error(void);
@@ -310,6 +313,16 @@ int qrt_render_spp_stats(qrt_scene scene, const qrt_view* views, uint32_t n_view
                          unsigned long long* d_stats, qrt_stream stream);
 int qrt_trace_stats(qrt_scene scene, int any, const qrt_ray* d_rays, uint64_t n, void* d_out,
                     const qrt_tuning* tuning, unsigned long long* d_stats, qrt_stream stream);
+
+/* Cost map (the paper's per-pixel cost heat map, Section 6): as
+ * qrt_render_spp_stats, and additionally writes for every pixel of view v
+ * the mean over its samples of the inner BVH nodes (both levels) visited by
+ * all rays of the path, closest-hit and shadow, into d_cost[v] (host array
+ * of n_views DEVICE pointers, each float [h*w], row-major).  Wavefront
+ * renderer only (tuning.mode 0 or 2). */
+int qrt_render_cost(qrt_scene scene, const qrt_view* views, uint32_t n_views, const float* d_albedo,
+                    const qrt_params* params, float* const* d_cost, unsigned long long* d_stats,
+                    qrt_stream stream);
 
 /* Per-stage GPU time of wavefront renders made with QRT_FLAG_STAGE_TIMES (the
  * breakdown of the paper's Table 1): after waiting for the stream, writes the

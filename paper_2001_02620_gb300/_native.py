@@ -65,7 +65,8 @@ class qrt_scene_stats(C.Structure):
     _fields_ = [("n_meshes", C.c_uint64), ("n_instances", C.c_uint64), ("n_quads", C.c_uint64),
                 ("blas_nodes", C.c_uint64), ("tlas_nodes", C.c_uint64),
                 ("device_bytes", C.c_uint64), ("max_blas_depth", C.c_uint32),
-                ("tlas_depth", C.c_uint32), ("build_seconds", C.c_double)]
+                ("tlas_depth", C.c_uint32), ("build_seconds", C.c_double),
+                ("phase_seconds", C.c_double * 6)]
 
 
 _vp = C.c_void_p
@@ -97,6 +98,7 @@ SIGNATURES = {
     "qrt_graph_destroy": (_i, [_vp]),
     "qrt_render_spp_stats": (_i, [_vp, C.POINTER(qrt_view), _u32, _vp, C.POINTER(qrt_params),
                                   _vp, _vp]),
+    "qrt_render_cost": (_i, [_vp, C.POINTER(qrt_view), _u32, _vp, C.POINTER(qrt_params), _vp, _vp, _vp]),
     "qrt_trace_stats": (_i, [_vp, _i, _vp, _u64, _vp, C.POINTER(qrt_tuning), _vp, _vp]),
     "qrt_stage_times": (_i, [_vp, _vp, C.POINTER(C.c_double), C.POINTER(C.c_uint32), _i]),
     "qrt_check": (_i, [_vp, _vp]),

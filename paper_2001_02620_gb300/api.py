@@ -94,6 +94,7 @@ class Scene:
         st = N.qrt_scene_stats()
         N.check(L.qrt_scene_stats_get(h, C.byref(st)))
         self.stats = {f: getattr(st, f) for f, _ in N.qrt_scene_stats._fields_}
+        self.stats["phase_seconds"] = list(st.phase_seconds)
         self.n_quads = int(st.n_quads)
         self.n_instances = int(st.n_instances)
 
@@ -158,6 +159,24 @@ class Scene:
             N.check(L.qrt_render_spp_stats(self.handle, cv, len(views), _ptr(albedo), C.byref(cp),
                                            _ptr(stats), _stream(stream)))
         return outs
+
+    def cost_maps(self, views, albedo: torch.Tensor, params: Params, stats: torch.Tensor,
+                  outs=None, tuning: dict | None = None, stream=None):
+        """Renders views and returns float [h, w] maps of the mean inner BVH
+        nodes visited per sample (qrt_render_cost); traversal counters are
+        added into stats (int64 [12])."""
+        if isinstance(views, View):
+            views = [views]
+        if outs is None:
+            outs = [torch.empty((v.h, v.w, 3), dtype=torch.float32, device=albedo.device)
+                    for v in views]
+        costs = [torch.empty((v.h, v.w), dtype=torch.float32, device=albedo.device) for v in views]
+        cv = make_views(views, outs)
+        cp = make_params(params, tuning)
+        cptr = (C.c_void_p * len(views))(*[_ptr(c) for c in costs])
+        N.check(N.lib().qrt_render_cost(self.handle, cv, len(views), _ptr(albedo), C.byref(cp), cptr,
+                                        _ptr(stats), _stream(stream)))
+        return costs
 
     def adjoint(self, views, albedo: torch.Tensor, dimages, grad: torch.Tensor, params: Params,
                 tuning: dict | None = None, stream=None) -> torch.Tensor:
@@ -234,6 +253,24 @@ def read_bandwidth_gbs(nbytes: int, reps: int, stream=None) -> float:
     e1.record(s)
     e1.synchronize()
     return buf.numel() * 4 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
+
+def save_heat_map(cost: torch.Tensor, path: str, scale: float | None = None) -> float:
+    """Writes a cost map (float [h, w], e.g. from Scene.cost_maps) as a binary
+    PPM heat map, dark (cheap) -> red -> yellow -> white (expensive), the
+    way the paper shows per-pixel cost.  scale: the cost drawn white
+    (default: the 99th percentile).  Returns the scale used."""
+    import numpy as np
+    c = cost.detach().float().cpu().numpy()
+    if scale is None:
+        scale = float(np.percentile(c, 99.0)) or 1.0
+    x = np.clip(c / scale, 0.0, 1.0)
+    rgb = np.stack([np.clip(3 * x, 0, 1), np.clip(3 * x - 1, 0, 1), np.clip(3 * x - 2, 0, 1)], -1)
+    img = (rgb * 255.0 + 0.5).astype(np.uint8)
+    with open(path, "wb") as f:
+        f.write(b"P6\n%d %d\n255\n" % (img.shape[1], img.shape[0]))
+        f.write(img.tobytes())
+    return scale
 
 
 def accumulate(frame_sum: torch.Tensor, frame: torch.Tensor, frames: int,

@@ -333,6 +333,14 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
     if (opts && opts->inst_boxes > 6) return fail(QRT_ERR_INVALID_ARG, "build_opts.inst_boxes must be 0..6");
     const BuildOpts bo = resolve_build(opts);
     auto t0 = std::chrono::steady_clock::now();
+    // wall time of each build phase (reported in qrt_scene_stats)
+    double phase[6] = {0, 0, 0, 0, 0, 0};
+    auto lap_t = t0;
+    auto lap = [&](int k) {
+        const auto now = std::chrono::steady_clock::now();
+        phase[k] += std::chrono::duration<double>(now - lap_t).count();
+        lap_t = now;
+    };
 
     // 1. one BLAS per mesh, largest first, on a pool of host threads
     std::vector<BlasResult> blas(n_mesh);
@@ -361,6 +369,7 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
     }
     for (uint32_t m = 0; m < n_mesh; ++m)
         if (!errs[m].empty()) return fail(QRT_ERR_INVALID_ARG, "mesh " + std::to_string(m) + ": " + errs[m]);
+    lap(0);
     // Verify every BLAS before anything reaches the device: all child and
     // item indices in range, each quad referenced once, boxes conservative.
     {
@@ -391,6 +400,7 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
     for (uint32_t m = 0; m < n_mesh; ++m)
         if (!errs[m].empty()) return fail(QRT_ERR_INVALID_ARG, "mesh " + std::to_string(m) + ": " + errs[m]);
 
+    lap(1);
     // 2. global layout: BLAS nodes mesh by mesh, then the TLAS
     std::vector<uint64_t> node_base(n_mesh), quad_base(n_mesh);
     uint64_t nn = 0, nq = 0;
@@ -526,6 +536,7 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
                     }
         }
     }
+    lap(2);
     TlasResult tlas;
     std::string terr;
     if (!build_tlas(wbox, bo, tlas, terr)) return fail(QRT_ERR_INVALID_ARG, "TLAS: " + terr);
@@ -539,6 +550,7 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
     for (const FBox& b : wbox)
         for (int a = 0; a < 3; ++a) R_top = std::max(R_top, std::max(std::fabs(b.lo[a]), std::fabs(b.hi[a])));
 
+    lap(3);
     // 4. concatenate: inner node references stay local to their structure
     std::vector<QNode> nodes;
     nodes.reserve(nn + tlas.nodes.size());
@@ -557,6 +569,7 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
     nodes.insert(nodes.end(), tlas.nodes.begin(), tlas.nodes.end());
     const double build_s =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    lap(4);
 
     // 5. upload
     qrt_scene_s* s = new qrt_scene_s();
@@ -601,6 +614,8 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
     s->stats.max_blas_depth = max_blas_depth;
     s->stats.tlas_depth = tlas.depth;
     s->stats.build_seconds = build_s;
+    lap(5);
+    for (int k = 0; k < 6; ++k) s->stats.phase_seconds[k] = phase[k];
     *out = s;
     return QRT_OK;
 }
@@ -700,6 +715,7 @@ int make_views(const qrt_view* views, uint32_t first, uint32_t count, const floa
         d.item_begin = items;
         d.path_begin = paths;
         d.out = v.out_rgb;
+        d.cost_out = nullptr;
         d.dimage = d_dimage ? d_dimage[first + k] : nullptr;
         if (d_dimage && !d.dimage) {
             std::snprintf(g_err, sizeof(g_err), "d_dimage[%u] is NULL", first + k);
@@ -763,7 +779,8 @@ int ensure_workspace(StreamSlot& sl, size_t bytes, cudaStream_t s) {
 int wave_enqueue(qrt_scene scene, const qrt_view* views, uint32_t n_views, const float* d_albedo,
                  const float* const* d_dimage, float* d_grad, const qrt_params* params,
                  const Tune& t, void* workspace, size_t ws_bytes, unsigned long long* stats,
-                 cudaStream_t s, WaveArgs& W, RenderArgs& R, const WaveStreams* ov) {
+                 cudaStream_t s, WaveArgs& W, RenderArgs& R, const WaveStreams* ov,
+                 float* const* d_cost = nullptr) {
     static_assert(sizeof(WaveArgs) < 32000, "kernel parameter block too large");
     const bool adjoint = d_grad != nullptr;
     const uint64_t cap = 1ull << t.chunk_log2;
@@ -777,6 +794,7 @@ int wave_enqueue(qrt_scene scene, const qrt_view* views, uint32_t n_views, const
     W.stats = stats;
     W.capacity = cap;
     W.batch = (uint32_t)t.batch;
+    W.cost_on = d_cost != nullptr;
     wave_carve(workspace, cap, adjoint, W.B);
     int rc = make_params(params, W.P);
     if (adjoint) W.P.path_log = nullptr;
@@ -788,6 +806,7 @@ int wave_enqueue(qrt_scene scene, const qrt_view* views, uint32_t n_views, const
         if (rc) break;
         for (uint32_t k = 0; k < cnt; ++k) {
             W.views[k] = R.views[k];
+            if (d_cost) W.views[k].cost_out = d_cost[first + k];
             paths += (uint64_t)views[first + k].w * views[first + k].h * views[first + k].spp;
         }
         W.n_views = cnt;
@@ -804,7 +823,8 @@ int wave_enqueue(qrt_scene scene, const qrt_view* views, uint32_t n_views, const
 int render_enqueue(qrt_scene scene, const qrt_view* views, uint32_t n_views, const float* d_albedo,
                    const float* const* d_dimage, float* d_grad, const qrt_params* params,
                    unsigned long long* counter, void* workspace, size_t ws_bytes,
-                   unsigned long long* stats, cudaStream_t s, const WaveStreams* ov) {
+                   unsigned long long* stats, cudaStream_t s, const WaveStreams* ov,
+                   float* const* d_cost = nullptr) {
     Tune t = resolve_tuning(params ? &params->tuning : nullptr);
     fit_chunk(t, views, n_views);
     int rc = validate_tuning(t);
@@ -839,7 +859,7 @@ int render_enqueue(qrt_scene scene, const qrt_view* views, uint32_t n_views, con
     WaveArgs* W = new WaveArgs();
     RenderArgs* R = new RenderArgs();
     rc = wave_enqueue(scene, views, n_views, d_albedo, d_dimage, d_grad, params, t, workspace,
-                      ws_bytes, stats, s, *W, *R, ov);
+                      ws_bytes, stats, s, *W, *R, ov, d_cost);
     delete R;
     delete W;
     return rc;
@@ -954,6 +974,32 @@ int qrt_render_spp_stats(qrt_scene scene, const qrt_view* views, uint32_t n_view
     if (rc) return rc;
     return render_enqueue(scene, views, n_views, d_albedo, nullptr, nullptr, params, ctr, ws, wsb,
                           d_stats, s, ov);
+}
+
+int qrt_render_cost(qrt_scene scene, const qrt_view* views, uint32_t n_views, const float* d_albedo,
+                    const qrt_params* params, float* const* d_cost, unsigned long long* d_stats,
+                    qrt_stream stream) {
+    int rc = render_args_check(scene, views, n_views, d_albedo);
+    if (rc) return rc;
+    if (!d_stats || !aligned(d_stats, 8)) return fail(QRT_ERR_INVALID_ARG, "d_stats NULL or unaligned");
+    if (n_views == 0) return QRT_OK;
+    if (!d_cost) return fail(QRT_ERR_INVALID_ARG, "d_cost is NULL");
+    for (uint32_t v = 0; v < n_views; ++v)
+        if (!d_cost[v] || !aligned(d_cost[v], 4)) {
+            std::snprintf(g_err, sizeof(g_err), "d_cost[%u] is NULL or unaligned", v);
+            return QRT_ERR_INVALID_ARG;
+        }
+    if (params && params->tuning.mode == 1)
+        return fail(QRT_ERR_INVALID_ARG, "cost maps come from the wavefront renderer (tuning.mode 0 or 2)");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned long long* ctr;
+    void* ws;
+    size_t wsb;
+    const WaveStreams* ov = nullptr;
+    rc = stream_scratch(scene, params, views, n_views, false, s, &ctr, &ws, &wsb, &ov);
+    if (rc) return rc;
+    return render_enqueue(scene, views, n_views, d_albedo, nullptr, nullptr, params, ctr, ws, wsb,
+                          d_stats, s, ov, d_cost);
 }
 
 int qrt_trace_stats(qrt_scene scene, int any, const qrt_ray* d_rays, uint64_t n, void* d_out,

@@ -67,6 +67,7 @@ struct ViewDev {
     uint64_t item_begin;  // first work item (pixel) of this view in the launch
     uint64_t path_begin;  // first path index of this view (for the path log)
     float* out;           // float [h*w*3]
+    float* cost_out;      // cost map float [h*w] (mean inner nodes visited per sample) or null
     const float* dimage;  // adjoint input, float [h*w*3]
 };
 

@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(256) wave_gen(const __grid_constant__ WaveArgs
     A.B.L[j] = make_float4(0.f, 0.f, 0.f, 0.f);
     A.B.meta[j] = make_uint2((uint32_t)(V.item_begin + pix), smp);
     A.B.q[1][j] = j;  // depth 1 uses queue 1 & 1
+    if (A.cost_on) A.B.cost[j] = 0;
     if (A.P.path_log) {
         uint32_t* log = A.P.path_log + g * (2ull * A.P.max_depth + 1);
         for (uint32_t k = 0; k < 2 * A.P.max_depth + 1; ++k) log[k] = k == 2 * A.P.max_depth ? 0u : 0xFFFFFFFFu;
@@ -121,6 +122,9 @@ __global__ void __maxnreg__(occupancy_regs(OCC)) wave_trace(const __grid_constan
     };
     auto finish_ray = [&]() {
         err |= T.err;
+        if constexpr (STATS) {
+            if (A.cost_on) atomicAdd(A.B.cost + j, T.steps);
+        }
         if (ANY) {
             if (T.h.inst == 0xFFFFFFFFu) {
                 const float4 p = A.B.pend[j];
@@ -245,6 +249,11 @@ __global__ void __launch_bounds__(256) wave_accumulate(const __grid_constant__ W
     out[0] = __fdiv_rn(s0, (float)V.spp);
     out[1] = __fdiv_rn(s1, (float)V.spp);
     out[2] = __fdiv_rn(s2, (float)V.spp);
+    if (V.cost_out) {
+        uint32_t c = 0;
+        for (uint32_t s = 0; s < V.spp; ++s) c += A.B.cost[j0 + s];
+        V.cost_out[pix] = (float)c / (float)V.spp;
+    }
 }
 
 template <bool ANY, int FETCH, int OCC, bool STATS>
@@ -295,6 +304,7 @@ void wave_carve(void* base, uint64_t C, bool adjoint, WaveBufs& B) {
     B.q[0] = reinterpret_cast<uint32_t*>(take(4 * C));
     B.q[1] = reinterpret_cast<uint32_t*>(take(4 * C));
     B.qs = reinterpret_cast<uint32_t*>(take(4 * C));
+    B.cost = reinterpret_cast<uint32_t*>(take(4 * C));
     B.Ltot = adjoint ? reinterpret_cast<float4*>(take(16 * C)) : nullptr;
     B.ctr = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * kCtrStride * 258));
 }

@@ -27,6 +27,7 @@ struct WaveBufs {
     uint2* meta;     // (pixel item, sample)
     uint32_t* q[2];  // closest-ray queues, ping-pong by depth parity
     uint32_t* qs;    // shadow-ray queue
+    uint32_t* cost;  // cost maps: inner BVH nodes visited by each path's rays
     float4* Ltot;    // adjoint: radiance of the first pass
     uint32_t* ctr;   // kCtrStride words per depth 0..max_depth+1
 };
@@ -61,13 +62,14 @@ struct WaveArgs {
     uint64_t capacity;  // paths per chunk
     uint32_t n_views;
     uint32_t batch;     // rays a lane claims per fetch
+    uint32_t cost_on;   // record per-path traversal cost (counting launches only)
     ViewDev views[kMaxViewsPerLaunch];
 };
 
 // Bytes wave_carve() takes for `capacity` paths (each piece 256-B aligned).
 constexpr size_t wave_workspace_bytes(uint64_t capacity, bool adjoint) {
     return 7 * (((16 * capacity) + 255) & ~uint64_t(255)) + (((8 * capacity) + 255) & ~uint64_t(255)) +
-           3 * (((4 * capacity) + 255) & ~uint64_t(255)) +
+           4 * (((4 * capacity) + 255) & ~uint64_t(255)) +
            ((sizeof(uint32_t) * kCtrStride * 258 + 255) & ~uint64_t(255)) +
            (adjoint ? (((16 * capacity) + 255) & ~uint64_t(255)) : 0);
 }

@@ -237,6 +237,31 @@ def test_progressive_frames_equal_one_render(api, tiny, mode):
     assert torch.equal(mean, ref)
 
 
+def test_cost_maps_count_every_node_visit(api, tiny):
+    """qrt_render_cost: per-pixel mean inner-node visits over the pixel's
+    samples; summed over the image they give back the launch's node counters
+    exactly, and the image equals qrt_render_spp's."""
+    sc, gs, osc = tiny
+    views = [I.tiny_view(), I.tiny_view()]
+    views[0].w, views[0].h, views[0].spp = 80, 48, 3
+    views[1].w, views[1].h, views[1].spp, views[1].pixel_base = 40, 40, 2, 80 * 48
+    params = I.Params(max_depth=4, sun_dir=I.MID_SUN_DIR, sun_E=(3.0, 2.0, 1.0))
+    alb = torch.from_numpy(I.albedo(sc.n_quads)).cuda()
+    stats = torch.zeros(12, dtype=torch.int64, device="cuda")
+    imgs = [torch.empty((v.h, v.w, 3), device="cuda") for v in views]
+    costs = gs.cost_maps(views, alb, params, stats, outs=imgs)
+    refs = gs.render(views, alb, params)
+    gs.check()
+    for a, b in zip(imgs, refs):
+        assert torch.equal(a, b)
+    st = stats.cpu().numpy()
+    total = sum(int(torch.round(c.double() * v.spp).sum().item()) for c, v in zip(costs, views))
+    assert total == int(st[1] + st[7])
+    assert all(float(c.min()) >= 1.0 for c in costs)   # every camera ray tests the TLAS root
+    with pytest.raises(api.N.QrtError):
+        gs.cost_maps(views, alb, params, stats, tuning=dict(mode=1))
+
+
 def test_accumulate_rejects_bad_arguments(api):
     L = api.N.lib()
     x = torch.zeros(16, device="cuda")

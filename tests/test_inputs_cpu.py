@@ -33,3 +33,15 @@ def test_table1_columns_sum_to_one_hundred_percent():
     cols = np.array(list(t.values())).sum(axis=0)
     np.testing.assert_allclose(cols, 100.0, atol=0.02)
     assert min(t["traversal_and_intersection"]) == 67.28
+
+
+def test_heat_map_writer(tmp_path):
+    import torch
+    from paper_2001_02620_gb300 import api
+    c = torch.arange(12, dtype=torch.float32).reshape(3, 4)
+    p = str(tmp_path / "cost.ppm")
+    scale = api.save_heat_map(c, p, scale=11.0)
+    data = open(p, "rb").read()
+    assert data.startswith(b"P6\n4 3\n255\n") and len(data) == len(b"P6\n4 3\n255\n") + 36
+    px = np.frombuffer(data[-36:], dtype=np.uint8).reshape(3, 4, 3)
+    assert scale == 11.0 and px[0, 0].tolist() == [0, 0, 0] and px[2, 3].tolist() == [255, 255, 255]
