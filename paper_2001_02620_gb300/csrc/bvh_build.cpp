@@ -6,9 +6,11 @@
 #include "bvh_build.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <thread>
 
 namespace qrt {
 namespace {
@@ -44,111 +46,171 @@ struct Centroid {
     float c[3];
 };
 
+// Helper threads that binary builds may start, shared by all builds running
+// at once (the BLAS builds of one scene run concurrently, one per core).
+std::atomic<int> g_helpers{0};
+
 // Binned-SAH binary build over items [0, n); ids receives the leaf order.
-void build_binary(const std::vector<FBox>& boxes, std::vector<uint32_t>& ids, uint32_t max_leaf,
-                  uint32_t bins, std::vector<BinNode>& nodes) {
-    const uint32_t n = (uint32_t)boxes.size();
-    ids.resize(n);
-    std::vector<Centroid> cen(n);
-    for (uint32_t i = 0; i < n; ++i) {
-        ids[i] = i;
-        for (int a = 0; a < 3; ++a) cen[i].c[a] = 0.5f * boxes[i].lo[a] + 0.5f * boxes[i].hi[a];
+// Subtrees of at least kForkItems items may be handed to a helper thread
+// while fewer than max_helpers helpers run.  Node slots are allocated
+// atomically, so their numbering depends on thread timing, but the tree --
+// every split, and the four-wide tree collapsed from it by following child
+// links from the root -- does not.
+class BinaryBuilder {
+  public:
+    static constexpr uint32_t kForkItems = 1u << 15;
+
+    BinaryBuilder(const std::vector<FBox>& boxes, std::vector<uint32_t>& ids, uint32_t max_leaf,
+                  uint32_t bins, std::vector<BinNode>& nodes, int max_helpers)
+        : boxes_(boxes), ids_(ids), max_leaf_(max_leaf), bins_(bins), nodes_(nodes),
+          max_helpers_(max_helpers) {}
+
+    void build() {
+        const uint32_t n = (uint32_t)boxes_.size();
+        ids_.resize(n);
+        cen_.resize(n);
+        for (uint32_t i = 0; i < n; ++i) {
+            ids_[i] = i;
+            for (int a = 0; a < 3; ++a) cen_[i].c[a] = 0.5f * boxes_[i].lo[a] + 0.5f * boxes_[i].hi[a];
+        }
+        nodes_.assign(2 * (size_t)std::max(1u, n), BinNode{});  // a binary tree has < 2n nodes
+        next_.store(1);
+        run(Task{0, 0, n});
+        nodes_.resize(next_.load());
     }
-    nodes.clear();
-    nodes.reserve(2 * (size_t)n / std::max(1u, max_leaf) + 8);
-    nodes.emplace_back();
+
+  private:
     struct Task {
         int32_t node;
         uint32_t first, count;
     };
-    std::vector<Task> work;
-    work.push_back(Task{0, 0, n});
-    std::vector<uint32_t> bcnt(bins);
-    std::vector<FBox> bbox(bins);
-    std::vector<double> right_area(bins);
-    std::vector<uint32_t> right_cnt(bins);
-    while (!work.empty()) {
-        Task tk = work.back();
-        work.pop_back();
-        FBox b, cb;
-        box_empty(b);
-        box_empty(cb);
-        for (uint32_t k = tk.first; k < tk.first + tk.count; ++k) {
-            box_grow(b, boxes[ids[k]]);
-            const Centroid& c = cen[ids[k]];
-            FBox p{{c.c[0], c.c[1], c.c[2]}, {c.c[0], c.c[1], c.c[2]}};
-            box_grow(cb, p);
-        }
-        nodes[tk.node].box = b;
-        if (tk.count <= max_leaf) {
-            nodes[tk.node].first = tk.first;
-            nodes[tk.node].count = tk.count;
-            continue;
-        }
-        int best_axis = -1;
-        uint32_t best_split = 0;
-        double best_cost = std::numeric_limits<double>::infinity();
-        for (int a = 0; a < 3; ++a) {
-            double ext = (double)cb.hi[a] - cb.lo[a];
-            if (!(ext > 0.0)) continue;
-            double scale = (double)bins / ext;
-            std::fill(bcnt.begin(), bcnt.end(), 0u);
-            for (auto& x : bbox) box_empty(x);
+
+    void run(Task root) {
+        std::vector<Task> work{root};
+        std::vector<std::thread> helpers;
+        std::vector<uint32_t> bcnt(bins_);
+        std::vector<FBox> bbox(bins_);
+        std::vector<double> right_area(bins_);
+        std::vector<uint32_t> right_cnt(bins_);
+        while (!work.empty()) {
+            Task tk = work.back();
+            work.pop_back();
+            FBox b, cb;
+            box_empty(b);
+            box_empty(cb);
             for (uint32_t k = tk.first; k < tk.first + tk.count; ++k) {
-                uint32_t i = ids[k];
-                int bi = (int)(((double)cen[i].c[a] - cb.lo[a]) * scale);
-                bi = std::min(std::max(bi, 0), (int)bins - 1);
-                bcnt[bi]++;
-                box_grow(bbox[bi], boxes[i]);
+                box_grow(b, boxes_[ids_[k]]);
+                const Centroid& c = cen_[ids_[k]];
+                FBox p{{c.c[0], c.c[1], c.c[2]}, {c.c[0], c.c[1], c.c[2]}};
+                box_grow(cb, p);
             }
-            FBox acc;
-            box_empty(acc);
-            uint32_t cnt = 0;
-            for (int bi = (int)bins - 1; bi >= 1; --bi) {
-                box_grow(acc, bbox[bi]);
-                cnt += bcnt[bi];
-                right_area[bi] = box_area(acc);
-                right_cnt[bi] = cnt;
+            nodes_[tk.node].box = b;
+            if (tk.count <= max_leaf_) {
+                nodes_[tk.node].first = tk.first;
+                nodes_[tk.node].count = tk.count;
+                continue;
             }
-            box_empty(acc);
-            cnt = 0;
-            for (uint32_t s = 0; s + 1 < bins; ++s) {  // left = bins [0, s]
-                box_grow(acc, bbox[s]);
-                cnt += bcnt[s];
-                uint32_t rc = right_cnt[s + 1];
-                if (cnt == 0 || rc == 0) continue;
-                double cost = box_area(acc) * cnt + right_area[s + 1] * rc;
-                if (cost < best_cost) {
-                    best_cost = cost;
-                    best_axis = a;
-                    best_split = s;
+            int best_axis = -1;
+            uint32_t best_split = 0;
+            double best_cost = std::numeric_limits<double>::infinity();
+            for (int a = 0; a < 3; ++a) {
+                double ext = (double)cb.hi[a] - cb.lo[a];
+                if (!(ext > 0.0)) continue;
+                double scale = (double)bins_ / ext;
+                std::fill(bcnt.begin(), bcnt.end(), 0u);
+                for (auto& x : bbox) box_empty(x);
+                for (uint32_t k = tk.first; k < tk.first + tk.count; ++k) {
+                    uint32_t i = ids_[k];
+                    int bi = (int)(((double)cen_[i].c[a] - cb.lo[a]) * scale);
+                    bi = std::min(std::max(bi, 0), (int)bins_ - 1);
+                    bcnt[bi]++;
+                    box_grow(bbox[bi], boxes_[i]);
+                }
+                FBox acc;
+                box_empty(acc);
+                uint32_t cnt = 0;
+                for (int bi = (int)bins_ - 1; bi >= 1; --bi) {
+                    box_grow(acc, bbox[bi]);
+                    cnt += bcnt[bi];
+                    right_area[bi] = box_area(acc);
+                    right_cnt[bi] = cnt;
+                }
+                box_empty(acc);
+                cnt = 0;
+                for (uint32_t sp = 0; sp + 1 < bins_; ++sp) {  // left = bins [0, sp]
+                    box_grow(acc, bbox[sp]);
+                    cnt += bcnt[sp];
+                    uint32_t rc = right_cnt[sp + 1];
+                    if (cnt == 0 || rc == 0) continue;
+                    double cost = box_area(acc) * cnt + right_area[sp + 1] * rc;
+                    if (cost < best_cost) {
+                        best_cost = cost;
+                        best_axis = a;
+                        best_split = sp;
+                    }
+                }
+            }
+            uint32_t mid;
+            if (best_axis < 0) {
+                mid = tk.first + tk.count / 2;  // all centroids coincide: split by count
+            } else {
+                double ext = (double)cb.hi[best_axis] - cb.lo[best_axis];
+                double scale = (double)bins_ / ext;
+                float lo = cb.lo[best_axis];
+                auto it = std::partition(ids_.begin() + tk.first, ids_.begin() + tk.first + tk.count,
+                                         [&](uint32_t i) {
+                                             int bi = (int)(((double)cen_[i].c[best_axis] - lo) * scale);
+                                             bi = std::min(std::max(bi, 0), (int)bins_ - 1);
+                                             return (uint32_t)bi <= best_split;
+                                         });
+                mid = (uint32_t)(it - ids_.begin());
+                if (mid == tk.first || mid == tk.first + tk.count) mid = tk.first + tk.count / 2;
+            }
+            const int32_t l = (int32_t)next_.fetch_add(2);
+            nodes_[tk.node].left = l;
+            nodes_[tk.node].right = l + 1;
+            const Task kids[2] = {Task{l + 1, mid, tk.first + tk.count - mid},
+                                  Task{l, tk.first, mid - tk.first}};
+            for (const Task& c : kids) {
+                if (c.count >= kForkItems && take_helper()) {
+                    helpers.emplace_back([this, c] {
+                        run(c);
+                        g_helpers.fetch_sub(1);
+                    });
+                } else {
+                    work.push_back(c);
                 }
             }
         }
-        uint32_t mid;
-        if (best_axis < 0) {
-            mid = tk.first + tk.count / 2;  // all centroids coincide: split by count
-        } else {
-            double ext = (double)cb.hi[best_axis] - cb.lo[best_axis];
-            double scale = (double)bins / ext;
-            float lo = cb.lo[best_axis];
-            auto it = std::partition(ids.begin() + tk.first, ids.begin() + tk.first + tk.count,
-                                     [&](uint32_t i) {
-                                         int bi = (int)(((double)cen[i].c[best_axis] - lo) * scale);
-                                         bi = std::min(std::max(bi, 0), (int)bins - 1);
-                                         return (uint32_t)bi <= best_split;
-                                     });
-            mid = (uint32_t)(it - ids.begin());
-            if (mid == tk.first || mid == tk.first + tk.count) mid = tk.first + tk.count / 2;
-        }
-        int32_t l = (int32_t)nodes.size();
-        nodes.emplace_back();
-        nodes.emplace_back();
-        nodes[tk.node].left = l;
-        nodes[tk.node].right = l + 1;
-        work.push_back(Task{l + 1, mid, tk.first + tk.count - mid});
-        work.push_back(Task{l, tk.first, mid - tk.first});
+        for (std::thread& t : helpers) t.join();
     }
+
+    bool take_helper() {
+        int h = g_helpers.load();
+        while (h < max_helpers_)
+            if (g_helpers.compare_exchange_weak(h, h + 1)) return true;
+        return false;
+    }
+
+    const std::vector<FBox>& boxes_;
+    std::vector<uint32_t>& ids_;
+    uint32_t max_leaf_, bins_;
+    std::vector<BinNode>& nodes_;
+    int max_helpers_;
+    std::vector<Centroid> cen_;
+    std::atomic<uint32_t> next_{1};
+};
+
+void build_binary(const std::vector<FBox>& boxes, std::vector<uint32_t>& ids, uint32_t max_leaf,
+                  uint32_t bins, std::vector<BinNode>& nodes, int max_helpers) {
+    BinaryBuilder b(boxes, ids, max_leaf, bins, nodes, max_helpers);
+    b.build();
+}
+
+// Helper threads a build may start: one per core (opts.threads, 0 = all).
+int helper_budget(const BuildOpts& opts) {
+    const unsigned hw = opts.threads ? opts.threads : std::max(1u, std::thread::hardware_concurrency());
+    return (int)hw;
 }
 
 // Chain-shaped binary tree (test aid): every inner node has one leaf of one
@@ -429,7 +491,7 @@ bool build_blas(const float* verts, uint32_t n_verts, const uint32_t* quads, uin
         build_chain(boxes, ids, bn);
     else
         build_binary(boxes, ids, std::max(1u, std::min(opts.max_leaf, 8u)),
-                     std::max(4u, std::min(opts.sah_bins, 64u)), bn);
+                     std::max(4u, std::min(opts.sah_bins, 64u)), bn, helper_budget(opts));
     out.nodes.clear();
     Collapser col{bn, ids, false, out.nodes};
     if (col.emit(0, 1) < 0) {
@@ -469,7 +531,8 @@ bool build_tlas(const std::vector<FBox>& inst_boxes, const BuildOpts& opts, Tlas
         }
     std::vector<BinNode> bn;
     std::vector<uint32_t> ids;
-    build_binary(inst_boxes, ids, 1, std::max(4u, std::min(opts.sah_bins, 64u)), bn);
+    build_binary(inst_boxes, ids, 1, std::max(4u, std::min(opts.sah_bins, 64u)), bn,
+                 helper_budget(opts));
     Collapser col{bn, ids, true, out.nodes};
     if (col.emit(0, 1) < 0) {
         err = col.err;

@@ -132,6 +132,18 @@ def test_blas_invariants_varied_meshes(native):
         assert rc == 0, msg
 
 
+def test_parallel_build_gives_the_same_tree(native):
+    """Large subtrees are built by helper threads; the tree must not depend
+    on how many: node count and depth (and the invariant check) agree for 1
+    and 8 threads on meshes large enough to fork."""
+    rng = np.random.default_rng(5)
+    for v, q in [I.displaced_grid(rng, 300_000), I.noisy_blob(rng, 200_000)]:
+        r1 = _check_mesh(native, v, q, threads=1)
+        r8 = _check_mesh(native, v, q, threads=8)
+        assert r1[0] == 0 and r8[0] == 0, (r1[3], r8[3])
+        assert r1[1:3] == r8[1:3]
+
+
 def test_blas_degenerate_chain_is_deep(native):
     vv = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0]], dtype=np.float32)
     q = np.tile(np.array([[0, 1, 2, 3]], dtype=np.uint32), (300, 1))
