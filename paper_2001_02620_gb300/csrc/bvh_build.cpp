@@ -6,6 +6,7 @@
 #include "bvh_build.h"
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -92,18 +93,13 @@ class BinaryBuilder {
         std::vector<FBox> bbox(bins_);
         std::vector<double> right_area(bins_);
         std::vector<uint32_t> right_cnt(bins_);
+        std::vector<uint32_t> bcnt3(3 * bins_);
+        std::vector<FBox> bbox3(3 * bins_);
         while (!work.empty()) {
             Task tk = work.back();
             work.pop_back();
             FBox b, cb;
-            box_empty(b);
-            box_empty(cb);
-            for (uint32_t k = tk.first; k < tk.first + tk.count; ++k) {
-                box_grow(b, boxes_[ids_[k]]);
-                const Centroid& c = cen_[ids_[k]];
-                FBox p{{c.c[0], c.c[1], c.c[2]}, {c.c[0], c.c[1], c.c[2]}};
-                box_grow(cb, p);
-            }
+            bounds(tk.first, tk.first + tk.count, b, cb);
             nodes_[tk.node].box = b;
             if (tk.count <= max_leaf_) {
                 nodes_[tk.node].first = tk.first;
@@ -113,19 +109,16 @@ class BinaryBuilder {
             int best_axis = -1;
             uint32_t best_split = 0;
             double best_cost = std::numeric_limits<double>::infinity();
+            double scale3[3];
             for (int a = 0; a < 3; ++a) {
-                double ext = (double)cb.hi[a] - cb.lo[a];
-                if (!(ext > 0.0)) continue;
-                double scale = (double)bins_ / ext;
-                std::fill(bcnt.begin(), bcnt.end(), 0u);
-                for (auto& x : bbox) box_empty(x);
-                for (uint32_t k = tk.first; k < tk.first + tk.count; ++k) {
-                    uint32_t i = ids_[k];
-                    int bi = (int)(((double)cen_[i].c[a] - cb.lo[a]) * scale);
-                    bi = std::min(std::max(bi, 0), (int)bins_ - 1);
-                    bcnt[bi]++;
-                    box_grow(bbox[bi], boxes_[i]);
-                }
+                const double ext = (double)cb.hi[a] - cb.lo[a];
+                scale3[a] = ext > 0.0 ? (double)bins_ / ext : 0.0;
+            }
+            bin3(tk.first, tk.first + tk.count, cb, scale3, bcnt3, bbox3);
+            for (int a = 0; a < 3; ++a) {
+                if (!(scale3[a] > 0.0)) continue;
+                std::copy(bcnt3.begin() + a * bins_, bcnt3.begin() + (a + 1) * bins_, bcnt.begin());
+                std::copy(bbox3.begin() + a * bins_, bbox3.begin() + (a + 1) * bins_, bbox.begin());
                 FBox acc;
                 box_empty(acc);
                 uint32_t cnt = 0;
@@ -183,6 +176,88 @@ class BinaryBuilder {
             }
         }
         for (std::thread& t : helpers) t.join();
+    }
+
+    // Items [k0, k1) split into chunks processed on threads when the range is
+    // large (the first splits of a big tree would otherwise be one long
+    // sequential pass each); merging counts and min/max boxes is exact, so
+    // the result does not depend on the chunking.
+    static constexpr uint32_t kParItems = 1u << 20;
+
+    template <class F>
+    void chunks(uint32_t k0, uint32_t k1, F f) {
+        const uint32_t n = k1 - k0;
+        const int nt = n >= kParItems ? std::max(1, max_helpers_) : 1;
+        if (nt == 1) {
+            f(0, k0, k1);
+            return;
+        }
+        std::vector<std::thread> th;
+        const uint32_t step = (n + nt - 1) / nt;
+        for (int t = 1; t < nt; ++t) {
+            const uint32_t a = k0 + std::min(n, t * step), b = k0 + std::min(n, (t + 1) * step);
+            th.emplace_back([&f, t, a, b] { f(t, a, b); });
+        }
+        f(0, k0, k0 + std::min(n, step));
+        for (std::thread& x : th) x.join();
+    }
+
+    void bounds(uint32_t k0, uint32_t k1, FBox& b, FBox& cb) {
+        const int nt = (k1 - k0) >= kParItems ? std::max(1, max_helpers_) : 1;
+        std::vector<FBox> pb(nt), pc(nt);
+        for (int t = 0; t < nt; ++t) {
+            box_empty(pb[t]);
+            box_empty(pc[t]);
+        }
+        chunks(k0, k1, [&](int t, uint32_t a, uint32_t e) {
+            for (uint32_t k = a; k < e; ++k) {
+                box_grow(pb[t], boxes_[ids_[k]]);
+                const Centroid& c = cen_[ids_[k]];
+                FBox p{{c.c[0], c.c[1], c.c[2]}, {c.c[0], c.c[1], c.c[2]}};
+                box_grow(pc[t], p);
+            }
+        });
+        box_empty(b);
+        box_empty(cb);
+        for (int t = 0; t < nt; ++t) {
+            box_grow(b, pb[t]);
+            box_grow(cb, pc[t]);
+        }
+    }
+
+    // Bins every item once for all three axes (axes with scale 0 are
+    // skipped): one gather of its box and centroid per item and pass.
+    void bin3(uint32_t k0, uint32_t k1, const FBox& cb, const double* scale, std::vector<uint32_t>& bcnt,
+              std::vector<FBox>& bbox) {
+        const int nt = (k1 - k0) >= kParItems ? std::max(1, max_helpers_) : 1;
+        const uint32_t nb = 3 * bins_;
+        std::vector<std::vector<uint32_t>> pc(nt, std::vector<uint32_t>(nb, 0u));
+        std::vector<std::vector<FBox>> pb(nt, std::vector<FBox>(nb));
+        for (auto& v : pb)
+            for (auto& x : v) box_empty(x);
+        chunks(k0, k1, [&](int t, uint32_t s, uint32_t e) {
+            uint32_t* cnt = pc[t].data();
+            FBox* bx = pb[t].data();
+            for (uint32_t k = s; k < e; ++k) {
+                const uint32_t i = ids_[k];
+                const FBox& box = boxes_[i];
+                const Centroid& c = cen_[i];
+                for (int a = 0; a < 3; ++a) {
+                    if (!(scale[a] > 0.0)) continue;
+                    int bi = (int)(((double)c.c[a] - cb.lo[a]) * scale[a]);
+                    bi = std::min(std::max(bi, 0), (int)bins_ - 1);
+                    cnt[a * bins_ + bi]++;
+                    box_grow(bx[a * bins_ + bi], box);
+                }
+            }
+        });
+        std::fill(bcnt.begin(), bcnt.end(), 0u);
+        for (auto& x : bbox) box_empty(x);
+        for (int t = 0; t < nt; ++t)
+            for (uint32_t bi = 0; bi < nb; ++bi) {
+                bcnt[bi] += pc[t][bi];
+                box_grow(bbox[bi], pb[t][bi]);
+            }
     }
 
     bool take_helper() {
@@ -302,6 +377,10 @@ bool quantize(QNode& q, const FBox* cb, int nc) {
     return true;
 }
 
+// Collapses the binary tree to four-wide nodes in two passes: emit() lays
+// the wide nodes out depth first (children and leaf references; it fixes
+// every index), then quantise() fills in the child boxes of all nodes in
+// parallel (each node's quantisation depends only on its own child boxes).
 struct Collapser {
     const std::vector<BinNode>& bn;
     const std::vector<uint32_t>& ids;
@@ -309,6 +388,36 @@ struct Collapser {
     std::vector<QNode>& out;
     uint32_t max_depth = 0;
     std::string err;
+    std::vector<std::array<int32_t, 4>> kids;  // binary node of each child slot
+
+    bool quantise(int threads) {
+        const size_t n = out.size();
+        const size_t chunk = 4096;
+        std::atomic<size_t> next{0};
+        std::atomic<bool> bad{false};
+        auto work = [&]() {
+            for (;;) {
+                const size_t c0 = next.fetch_add(chunk);
+                if (c0 >= n || bad.load()) break;
+                for (size_t k = c0; k < std::min(n, c0 + chunk); ++k) {
+                    FBox cb[4];
+                    const int nc = out[k].nchild;
+                    for (int i = 0; i < nc; ++i) cb[i] = bn[kids[k][i]].box;
+                    if (!quantize(out[k], cb, nc)) bad.store(true);
+                }
+            }
+        };
+        const int nt = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::max(1, threads), n / chunk + 1));
+        std::vector<std::thread> th;
+        for (int t = 1; t < nt; ++t) th.emplace_back(work);
+        work();
+        for (std::thread& t : th) t.join();
+        if (bad.load()) {
+            err = "box quantisation failed (coordinates out of range)";
+            return false;
+        }
+        return true;
+    }
 
     // Emits the wide node for binary node b; returns its local index or -1.
     int64_t emit(int32_t b, uint32_t depth) {
@@ -319,6 +428,7 @@ struct Collapser {
             return -1;
         }
         out.emplace_back();
+        kids.emplace_back();
         int32_t ch[4];
         int nc = 0;
         if (bn[b].left < 0) {
@@ -347,12 +457,12 @@ struct Collapser {
         }
         QNode q;
         std::memset(&q, 0, sizeof(q));
-        FBox cb[4];
         uint32_t childv[4] = {0, 0, 0, 0};
         uint8_t meta[4] = {0, 0, 0, 0};
+        std::array<int32_t, 4> kb = {-1, -1, -1, -1};
         for (int i = 0; i < nc; ++i) {
             const BinNode& c = bn[ch[i]];
-            cb[i] = c.box;
+            kb[i] = ch[i];
             if (c.left < 0) {
                 if (c.count == 0 || c.count > kMaxLeaf) {
                     err = "leaf size out of range";
@@ -372,16 +482,13 @@ struct Collapser {
                 meta[i] = kMetaInner;
             }
         }
-        if (!quantize(q, cb, nc)) {
-            err = "box quantisation failed (coordinates out of range)";
-            return -1;
-        }
         for (int i = 0; i < 4; ++i) {
             q.child[i] = childv[i];
             q.meta[i] = meta[i];
         }
         q.nchild = (uint8_t)nc;
         out[idx] = q;
+        kids[idx] = kb;
         return idx;
     }
 };
@@ -494,7 +601,7 @@ bool build_blas(const float* verts, uint32_t n_verts, const uint32_t* quads, uin
                      std::max(4u, std::min(opts.sah_bins, 64u)), bn, helper_budget(opts));
     out.nodes.clear();
     Collapser col{bn, ids, false, out.nodes};
-    if (col.emit(0, 1) < 0) {
+    if (col.emit(0, 1) < 0 || !col.quantise(1)) {
         err = col.err;
         return false;
     }
@@ -534,7 +641,7 @@ bool build_tlas(const std::vector<FBox>& inst_boxes, const BuildOpts& opts, Tlas
     build_binary(inst_boxes, ids, 1, std::max(4u, std::min(opts.sah_bins, 64u)), bn,
                  helper_budget(opts));
     Collapser col{bn, ids, true, out.nodes};
-    if (col.emit(0, 1) < 0) {
+    if (col.emit(0, 1) < 0 || !col.quantise(helper_budget(opts))) {
         err = col.err;
         return false;
     }
@@ -543,15 +650,20 @@ bool build_tlas(const std::vector<FBox>& inst_boxes, const BuildOpts& opts, Tlas
 }
 
 namespace {
+// Checks subtrees recursively; the subtrees two levels below the root of a
+// large tree are checked on their own threads (items are marked seen with
+// atomic increments, so an item referenced from two subtrees is still found).
 struct Checker {
     const std::vector<QNode>& nodes;
     const std::vector<FBox>& items;
-    std::vector<uint8_t> seen;
+    std::vector<uint8_t>& seen;
     std::string err;
     uint32_t depth = 0;
+    uint32_t fork_depth = 0;  // nodes at depths < fork_depth check inner children on threads
 
     bool rec(uint32_t idx, uint32_t d, FBox& box) {
         depth = std::max(depth, d);
+        if (d < fork_depth && idx < nodes.size()) return rec_forked(idx, d, box);
         if (idx >= nodes.size()) {
             err = "child node index out of range";
             return false;
@@ -579,7 +691,95 @@ struct Checker {
                         err = "leaf item out of range";
                         return false;
                     }
-                    if (seen[it]++) {
+                    if (__atomic_fetch_add(&seen[it], (uint8_t)1, __ATOMIC_RELAXED)) {
+                        err = "item referenced twice";
+                        return false;
+                    }
+                    box_grow(cb, items[it]);
+                }
+            }
+            for (int a = 0; a < 3; ++a) {
+                float lo = dequant(n.qlo[a][i], ex[a], org[a]);
+                float hi = dequant(n.qhi[a][i], ex[a], org[a]);
+                if (!(lo <= cb.lo[a] && hi >= cb.hi[a])) {
+                    err = "quantised child box does not contain its subtree";
+                    return false;
+                }
+            }
+            box_grow(box, cb);
+        }
+        if (valid == 0 || valid != n.nchild) {
+            err = "node child count inconsistent";
+            return false;
+        }
+        return true;
+    }
+
+    // As rec(), with each inner child checked by its own Checker on a thread.
+    bool rec_forked(uint32_t idx, uint32_t d, FBox& box) {
+        const QNode& n = nodes[idx];
+        std::vector<Checker> sub;
+        sub.reserve(4);
+        FBox cbs[4];
+        bool ok[4] = {true, true, true, true};
+        std::vector<std::thread> th;
+        for (int i = 0; i < 4; ++i)
+            if (n.meta[i] == kMetaInner) sub.push_back(Checker{nodes, items, seen, {}, 0, fork_depth});
+        int s = 0;
+        for (int i = 0; i < 4; ++i) {
+            if (n.meta[i] != kMetaInner) continue;
+            Checker* c = &sub[s++];
+            th.emplace_back([c, &n, i, d, &cbs, &ok] { ok[i] = c->rec(n.child[i], d + 1, cbs[i]); });
+        }
+        for (std::thread& t : th) t.join();
+        s = 0;
+        for (int i = 0; i < 4; ++i) {
+            if (n.meta[i] != kMetaInner) continue;
+            Checker& c = sub[s++];
+            depth = std::max(depth, c.depth);
+            if (!ok[i]) {
+                err = c.err;
+                return false;
+            }
+        }
+        // the node itself, with the children's boxes already known
+        Checker self{nodes, items, seen, {}, 0, 0};
+        if (!self.node(idx, d, box, cbs)) {
+            err = self.err;
+            return false;
+        }
+        depth = std::max(depth, self.depth);
+        return true;
+    }
+
+    // Checks node idx given the boxes of its inner children (leaves are
+    // checked here).
+    bool node(uint32_t idx, uint32_t d, FBox& box, const FBox* inner_boxes) {
+        depth = std::max(depth, d);
+        const QNode& n = nodes[idx];
+        box_empty(box);
+        const float org[3] = {n.ox, n.oy, n.oz};
+        const int8_t ex[3] = {n.ex, n.ey, n.ez};
+        int valid = 0;
+        for (int i = 0; i < 4; ++i) {
+            if (n.meta[i] == 0) continue;
+            ++valid;
+            FBox cb;
+            if (n.meta[i] == kMetaInner) {
+                cb = inner_boxes[i];
+            } else {
+                if (n.meta[i] > kMaxLeaf) {
+                    err = "leaf count too large";
+                    return false;
+                }
+                box_empty(cb);
+                for (uint32_t k = 0; k < n.meta[i]; ++k) {
+                    uint32_t it = n.child[i] + k;
+                    if (it >= items.size()) {
+                        err = "leaf item out of range";
+                        return false;
+                    }
+                    if (__atomic_fetch_add(&seen[it], (uint8_t)1, __ATOMIC_RELAXED)) {
                         err = "item referenced twice";
                         return false;
                     }
@@ -614,14 +814,16 @@ bool check_wide(const std::vector<QNode>& nodes, const std::vector<FBox>& item_b
         }
         return true;
     }
-    Checker c{nodes, item_boxes, std::vector<uint8_t>(item_boxes.size(), 0), {}, 0};
+    std::vector<uint8_t> seen(item_boxes.size(), 0);
+    // large trees: the root's and its children's inner subtrees on threads
+    Checker c{nodes, item_boxes, seen, {}, 0, nodes.size() > (1u << 16) ? 3u : 0u};
     FBox b;
     if (!c.rec(0, 1, b)) {
         err = c.err;
         return false;
     }
-    for (size_t i = 0; i < c.seen.size(); ++i)
-        if (c.seen[i] != 1) {
+    for (size_t i = 0; i < seen.size(); ++i)
+        if (seen[i] != 1) {
             err = "item not referenced";
             return false;
         }
