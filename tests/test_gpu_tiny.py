@@ -258,6 +258,13 @@ def test_cost_maps_count_every_node_visit(api, tiny):
     total = sum(int(torch.round(c.double() * v.spp).sum().item()) for c, v in zip(costs, views))
     assert total == int(st[1] + st[7])
     assert all(float(c.min()) >= 1.0 for c in costs)   # every camera ray tests the TLAS root
+    # small chunks cut the views (and pixels' sample runs) into many chunks:
+    # the per-path counters are chunk-local, the maps must not change
+    stats2 = torch.zeros(12, dtype=torch.int64, device="cuda")
+    costs2 = gs.cost_maps(views, alb, params, stats2, tuning=dict(chunk_log2=10))
+    for a, b in zip(costs, costs2):
+        assert torch.equal(a, b)
+    assert torch.equal(stats, stats2)
     with pytest.raises(api.N.QrtError):
         gs.cost_maps(views, alb, params, stats, tuning=dict(mode=1))
 
