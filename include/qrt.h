@@ -271,8 +271,11 @@ int qrt_render_spp_static(qrt_scene scene, const qrt_view* views, uint32_t n_vie
  * sum_v sum_pixel sum_c d_dimage[v][pixel*3+c] * dI_v[pixel,c]/d albedo[q,c]
  * into d_grad_albedo (DEVICE float [n_quads*3], accumulated, not cleared).
  * Paths are recomputed from their random streams instead of being stored
- * (path replay); contributions are added with FP32 atomics.  d_dimage: host
- * array of n_views DEVICE pointers, each float [h*w*3]. */
+ * (path replay); contributions are added with FP32 atomics.  Per path the
+ * wavefront renderer keeps only its radiance and one visibility bit per
+ * shadow ray of depths 1..32, so its replay traces the closest-hit rays again
+ * but not those shadow rays.  d_dimage: host array of n_views DEVICE
+ * pointers, each float [h*w*3]. */
 int qrt_render_adjoint(qrt_scene scene, const qrt_view* views, uint32_t n_views,
                        const float* d_albedo, const float* const* d_dimage,
                        float* d_grad_albedo, const qrt_params* params, qrt_stream stream);
@@ -307,7 +310,12 @@ int qrt_graph_destroy(qrt_graph graph);
  * launch into d_stats (DEVICE uint64 [6], 8-byte aligned, accumulated):
  * rays traced, inner nodes visited, quads tested, instances entered, quad
  * tests re-done in FP64, path vertices shaded.  These counts give the algorithmic bytes of a
- * launch (64 B per node, 48 B per quad, 64 B per instance entry). */
+ * launch (64 B per node, 48 B per quad, 64 B per instance entry).  Rays,
+ * shaded vertices and every result are reproducible; node, quad and instance
+ * counts may vary slightly from launch to launch, because a lane defers a
+ * BLAS leaf while its warp tests inner nodes, so the moment its hit distance
+ * tightens (and which stack entries are culled) depends on the rays that
+ * share its warp. */
 int qrt_render_spp_stats(qrt_scene scene, const qrt_view* views, uint32_t n_views,
                          const float* d_albedo, const qrt_params* params,
                          unsigned long long* d_stats, qrt_stream stream);
@@ -318,8 +326,10 @@ int qrt_trace_stats(qrt_scene scene, int any, const qrt_ray* d_rays, uint64_t n,
  * qrt_render_spp_stats, and additionally writes for every pixel of view v
  * the mean over its samples of the inner BVH nodes (both levels) visited by
  * all rays of the path, closest-hit and shadow, into d_cost[v] (host array
- * of n_views DEVICE pointers, each float [h*w], row-major).  Wavefront
- * renderer only (tuning.mode 0 or 2). */
+ * of n_views DEVICE pointers, each float [h*w], row-major).  Summed over the
+ * image (times spp) the maps equal the launch's node counters; like them they
+ * may vary slightly between launches.  Wavefront renderer only (tuning.mode 0
+ * or 2). */
 int qrt_render_cost(qrt_scene scene, const qrt_view* views, uint32_t n_views, const float* d_albedo,
                     const qrt_params* params, float* const* d_cost, unsigned long long* d_stats,
                     qrt_stream stream);

@@ -1,11 +1,16 @@
 // Device-side traversal of the two-level quad BVH (qrt_layout.h).
 //
 // Top level: four-wide TLAS over instance world boxes.  At a TLAS leaf the ray
-// is re-centred at the point where it enters the instance's box, formed
-// exactly with error-free FP32 transformations, and moved into the
-// instance's object space (the direction is not renormalised, so t is shared
-// by both levels); the object's BLAS is traversed on the same stack with a
-// parameter s = t - t_e.
+// is re-centred at a point t_e on it near the object, formed exactly with
+// error-free FP32 transformations, and moved into the instance's object space
+// (the direction is not renormalised, so t is shared by both levels); the
+// object's BLAS is traversed on the same stack with a parameter s = t - t_e.
+// Closest-hit rays take t_e where they enter the instance's box: their stack
+// entries keep each box's entry distance (64 bits: distance, reference), which
+// also culls entries beyond the best hit.  Any-hit rays never cull (tmax is
+// fixed until the ray ends), so their entries are the 32-bit reference alone
+// (half the local-memory traffic) and t_e is where the ray passes closest to
+// the object origin.
 // When the stack drains back to the level where the instance was entered,
 // the world ray is restored.  Leaves of a BLAS hold up to 16 quads stored
 // contiguously.
@@ -35,6 +40,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "qrt_layout.h"
 
 namespace qrt {
@@ -52,8 +59,6 @@ struct Hit {
 struct RaySetup {
     float ox, oy, oz;     // origin
     float ix, iy, iz;     // reciprocal direction, |d| clamped away from 0
-    float oix, oiy, oiz;  // o * inv
-    float px, py, pz;     // box widening in t units (delta * |inv|)
     uint32_t neg;         // bit a: direction negative along axis a
     float delta;
     float dx, dy, dz;  // direction in the current space (for the shear)
@@ -82,12 +87,6 @@ __device__ __forceinline__ void setup_boxes(RaySetup& r, float ox, float oy, flo
     r.ix = __frcp_rn(clamp_dir(dx));
     r.iy = __frcp_rn(clamp_dir(dy));
     r.iz = __frcp_rn(clamp_dir(dz));
-    r.oix = __fmul_rn(ox, r.ix);
-    r.oiy = __fmul_rn(oy, r.iy);
-    r.oiz = __fmul_rn(oz, r.iz);
-    r.px = __fmul_rn(delta, fabsf(r.ix));
-    r.py = __fmul_rn(delta, fabsf(r.iy));
-    r.pz = __fmul_rn(delta, fabsf(r.iz));
     r.neg = (r.ix < 0.f ? 1u : 0u) | (r.iy < 0.f ? 2u : 0u) | (r.iz < 0.f ? 4u : 0u);
     r.delta = delta;
     r.dx = dx;
@@ -178,11 +177,17 @@ __device__ __forceinline__ int node_children(const QNode* node, const RaySetup& 
               ez = (int)(int8_t)((A.w >> 16) & 0xFF);
     const float ax = __fmul_rn(exp2i(ex), r.ix), ay = __fmul_rn(exp2i(ey), r.iy),
                 az = __fmul_rn(exp2i(ez), r.iz);
-    const float bx = __fmaf_rn(nox, r.ix, -r.oix), by = __fmaf_rn(noy, r.iy, -r.oiy),
-                bz = __fmaf_rn(noz, r.iz, -r.oiz);
-    const float bnx = bx - r.px, bfx = bx + r.px;
-    const float bny = by - r.py, bfy = by + r.py;
-    const float bnz = bz - r.pz, bfz = bz + r.pz;
+    // o * inv and the widening delta * |inv| are formed here, not kept in
+    // RaySetup: at 64 registers kept values are spilled, and six multiplies
+    // per node cost less than their local-memory round trips
+    const float bx = __fmaf_rn(nox, r.ix, -__fmul_rn(r.ox, r.ix)),
+                by = __fmaf_rn(noy, r.iy, -__fmul_rn(r.oy, r.iy)),
+                bz = __fmaf_rn(noz, r.iz, -__fmul_rn(r.oz, r.iz));
+    const float px = __fmul_rn(r.delta, fabsf(r.ix)), py = __fmul_rn(r.delta, fabsf(r.iy)),
+                pz = __fmul_rn(r.delta, fabsf(r.iz));
+    const float bnx = bx - px, bfx = bx + px;
+    const float bny = by - py, bfy = by + py;
+    const float bnz = bz - pz, bfz = bz + pz;
     // words: lo x,y,z = B.x, B.y, B.z ; hi x,y,z = B.w, C.x, C.y
     const uint32_t nwx = (r.neg & 1u) ? B.w : B.x, fwx = (r.neg & 1u) ? B.x : B.w;
     const uint32_t nwy = (r.neg & 2u) ? C.x : B.y, fwy = (r.neg & 2u) ? B.y : C.x;
@@ -449,7 +454,9 @@ struct Traversal {
     float wox, woy, woz, wdx, wdy, wdz, tmin, tmax;
     float te;  // object-space parameter offset: t = s + te
     RaySetup r;
-    uint64_t stack[STACK];
+    // any-hit rays never cull by distance (tmax stays put until the ray
+    // ends), so their entries hold the reference alone
+    std::conditional_t<ANY, uint32_t, uint64_t> stack[STACK];
     int cap;  // stack entries a ray may use (<= STACK); set once per kernel
     int sp, inst_sp;
     bool top, have;
@@ -532,7 +539,7 @@ struct Traversal {
                     }
 #pragma unroll
                     for (int k = 3; k >= 1; --k)
-                        if (k < nh) stack[sp++] = ((uint64_t)__float_as_uint(t[k]) << 32) | ref[k];
+                        if (k < nh) stack[sp++] = ANY ? ref[k] : (((uint64_t)__float_as_uint(t[k]) << 32) | ref[k]);
                     cur = ref[0];
                     cur_t = t[0];
                     return true;
@@ -554,8 +561,8 @@ struct Traversal {
         }
         if (sp == 0) return false;
         const uint64_t e = stack[--sp];
-        const float tn = __uint_as_float((uint32_t)(e >> 32));
-        if (tn <= limit()) {
+        const float tn = ANY ? tmin : __uint_as_float((uint32_t)(e >> 32));
+        if (ANY || tn <= limit()) {
             cur = (uint32_t)e;
             cur_t = tn;
             have = true;
@@ -605,8 +612,8 @@ struct Traversal {
             }
             if (sp == 0) return;
             const uint64_t e = stack[--sp];
-            const float tn = __uint_as_float((uint32_t)(e >> 32));
-            if (tn <= limit()) {
+            const float tn = ANY ? tmin : __uint_as_float((uint32_t)(e >> 32));
+            if (ANY || tn <= limit()) {
                 cur = (uint32_t)e;
                 cur_t = tn;
                 have = true;
@@ -634,7 +641,7 @@ struct Traversal {
             }
 #pragma unroll
             for (int k = 3; k >= 1; --k)
-                if (k < nh) stack[sp++] = ((uint64_t)__float_as_uint(t[k]) << 32) | ref[k];
+                if (k < nh) stack[sp++] = ANY ? ref[k] : (((uint64_t)__float_as_uint(t[k]) << 32) | ref[k]);
             cur = ref[0];
             cur_t = t[0];
         }
@@ -675,10 +682,21 @@ struct Traversal {
         const float4* ip = reinterpret_cast<const float4*>(S.inst + cur_inst);
         const float4 m0 = __ldg(ip), m1 = __ldg(ip + 1), m2 = __ldg(ip + 2), m3 = __ldg(ip + 3);
         // m0 = (c, R); m1 = (w0 w1 w2 w3); m2 = (w4 w5 w6 w7); m3 = (w8, node_base, quad_base, kappa)
-        // Re-centre where the ray enters the instance's world box (never
-        // before tmin): every hit lies beyond it, so s = t - te starts at 0 and
-        // keeps full precision near the origin of rays that start on a surface.
-        te = (cur_t < h.t) ? fmaxf(tmin, cur_t) : tmin;
+        if constexpr (ANY) {
+            // no box entry distance on a reference-only stack: re-centre
+            // where the ray passes closest to the object origin (never
+            // before tmin); hits before that point have s < 0
+            const float cx = __fsub_rn(m0.x, wox), cy = __fsub_rn(m0.y, woy), cz = __fsub_rn(m0.z, woz);
+            const float dd = __fmaf_rn(wdx, wdx, __fmaf_rn(wdy, wdy, __fmul_rn(wdz, wdz)));
+            const float tc = __fdiv_rn(__fmaf_rn(cx, wdx, __fmaf_rn(cy, wdy, __fmul_rn(cz, wdz))), dd);
+            te = (tc > tmin && tc < kInfF) ? tc : tmin;
+        } else {
+            // where the ray enters the instance's world box (never before
+            // tmin): every hit lies beyond it, so s = t - te starts at 0 and
+            // keeps full precision near the origin of rays that start on a
+            // surface
+            te = (cur_t < h.t) ? fmaxf(tmin, cur_t) : tmin;
+        }
         float exl, eyl, ezl;
         const float ex = exact_offset(wox, wdx, te, m0.x, &exl);
         const float ey = exact_offset(woy, wdy, te, m0.y, &eyl);

@@ -18,6 +18,10 @@
 // The adjoint runs the chunk twice: a primal pass that leaves each path's
 // radiance in Ltot, then a replay pass whose shade stage adds
 // w * (Ltot - sun terms before vertex i) / a_i into the albedo gradient.
+// The primal also records which of the path's shadow rays of depths 1..32
+// were unoccluded (bit i-1 in the spare w lane of its radiance), so the
+// replay adds those sun terms in its shade stage instead of tracing the
+// shadow rays again.
 // Radiance is accumulated in the same order as render.cu, so the two
 // renderers give bit-identical images.
 #include <algorithm>
@@ -132,6 +136,7 @@ __global__ void __maxnreg__(occupancy_regs(OCC)) wave_trace(const __grid_constan
                 l.x = __fadd_rn(l.x, p.x);
                 l.y = __fadd_rn(l.y, p.y);
                 l.z = __fadd_rn(l.z, p.z);
+                if (depth <= kVisDepths) l.w = __uint_as_float(__float_as_uint(l.w) | (1u << (depth - 1)));
                 A.B.L[j] = l;
             } else if (A.P.path_log && depth <= 16) {
                 const uint64_t g = A.P0 + j;
@@ -206,11 +211,25 @@ __global__ void __launch_bounds__(256) wave_shade(const __grid_constant__ WaveAr
         if (cl > 0.f) {
             if (log && depth <= 16) log[2 * D] |= 1u << (2 * (depth - 1));
             const float kk = __fmul_rn(cl, 0.318309886183790671538f);  // cos / pi
-            A.B.pend[j] = make_float4(__fmul_rn(__fmul_rn(b.x, a0), __fmul_rn(A.P.sun_E[0], kk)),
-                                      __fmul_rn(__fmul_rn(b.y, a1), __fmul_rn(A.P.sun_E[1], kk)),
-                                      __fmul_rn(__fmul_rn(b.z, a2), __fmul_rn(A.P.sun_E[2], kk)), 0.f);
-            A.B.sray_o[j] = make_float4(sp.x, sp.y, sp.z, 0.f);
-            push(A.B.qs, A.B.ctr + kCtrStride * depth + kCtrShadow, j);
+            const float4 p = make_float4(__fmul_rn(__fmul_rn(b.x, a0), __fmul_rn(A.P.sun_E[0], kk)),
+                                         __fmul_rn(__fmul_rn(b.y, a1), __fmul_rn(A.P.sun_E[1], kk)),
+                                         __fmul_rn(__fmul_rn(b.z, a2), __fmul_rn(A.P.sun_E[2], kk)), 0.f);
+            if (replay && depth <= kVisDepths) {
+                // the primal found this shadow ray unoccluded or not: add its
+                // term after the gradient of this vertex, as the shadow stage
+                // would have, without tracing it again
+                if (__float_as_uint(A.B.Ltot[j].w) & (1u << (depth - 1))) {
+                    float4 l = A.B.L[j];
+                    l.x = __fadd_rn(l.x, p.x);
+                    l.y = __fadd_rn(l.y, p.y);
+                    l.z = __fadd_rn(l.z, p.z);
+                    A.B.L[j] = l;
+                }
+            } else {
+                A.B.pend[j] = p;
+                A.B.sray_o[j] = make_float4(sp.x, sp.y, sp.z, 0.f);
+                push(A.B.qs, A.B.ctr + kCtrStride * depth + kCtrShadow, j);
+            }
         }
     }
     b.x = __fmul_rn(b.x, a0);
@@ -356,7 +375,9 @@ static cudaError_t wave_pass(WaveArgs& A, uint64_t P0, uint32_t n, int replay, c
         wave_shade<<<(n + 255) / 256, 256, 0, s>>>(A, (int)i, replay);
         if (hook) hook->end(kStageShade, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if (A.P.sun_on) {
+        // the replay traces shadow rays only beyond the depths whose
+        // visibility the primal recorded
+        if (A.P.sun_on && !(replay && i <= (uint32_t)kVisDepths)) {
             cudaStream_t ss = s;
             if (overlap) {
                 if ((e = cudaEventRecord(ov->fork, s)) != cudaSuccess) return e;

@@ -16,11 +16,16 @@ constexpr int kCtrShadow = 1;       // shadow-ray queue length of this depth
 constexpr int kCtrFetchClosest = 2;
 constexpr int kCtrFetchShadow = 3;
 
+// Depths whose shadow-ray visibility the primal pass of the adjoint records
+// (one bit each), so that the replay need not trace those shadow rays.
+constexpr int kVisDepths = 32;
+
 struct WaveBufs {
     float4* ray_o;   // origin.xyz, tmin
     float4* ray_d;   // direction.xyz, tmax
     float4* beta;    // throughput
-    float4* L;       // radiance (primal) / sun terms so far (replay)
+    float4* L;       // radiance (primal) / sun terms so far (replay); w: bits
+                     // of the path's unoccluded shadow rays, depths 1..32
     float4* pend;    // sun term waiting for its shadow ray
     float4* sray_o;  // shadow-ray origin
     uint4* hit;      // t bits, instance, quad, slot

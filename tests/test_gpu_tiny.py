@@ -258,13 +258,24 @@ def test_cost_maps_count_every_node_visit(api, tiny):
     total = sum(int(torch.round(c.double() * v.spp).sum().item()) for c, v in zip(costs, views))
     assert total == int(st[1] + st[7])
     assert all(float(c.min()) >= 1.0 for c in costs)   # every camera ray tests the TLAS root
-    # small chunks cut the views (and pixels' sample runs) into many chunks:
-    # the per-path counters are chunk-local, the maps must not change
+    # small chunks cut the views into many chunks, whose per-path counters
+    # are indexed chunk-locally.  Node-visit counts are not bit-reproducible
+    # across schedules: a lane postpones a BLAS leaf while its warp tests
+    # inner nodes, so when its hit distance tightens (and which stack entries
+    # are culled) depends on the rays sharing the warp.  Each chunked map must
+    # still add up to its own launch's counters, rays and hits must not
+    # change, and the visits may differ only a little in total.
     stats2 = torch.zeros(12, dtype=torch.int64, device="cuda")
-    costs2 = gs.cost_maps(views, alb, params, stats2, tuning=dict(chunk_log2=10))
-    for a, b in zip(costs, costs2):
+    imgs2 = [torch.empty_like(i) for i in imgs]
+    costs2 = gs.cost_maps(views, alb, params, stats2, outs=imgs2, tuning=dict(chunk_log2=10))
+    for a, b in zip(imgs, imgs2):
         assert torch.equal(a, b)
-    assert torch.equal(stats, stats2)
+    st2 = stats2.cpu().numpy()
+    total2 = sum(int(torch.round(c.double() * v.spp).sum().item()) for c, v in zip(costs2, views))
+    assert total2 == int(st2[1] + st2[7])
+    assert st2[0] == st[0] and st2[6] == st[6]          # closest-hit and shadow rays
+    assert abs(total2 - total) <= 0.05 * total
+    assert all(float(c.min()) >= 1.0 for c in costs2)
     with pytest.raises(api.N.QrtError):
         gs.cost_maps(views, alb, params, stats, tuning=dict(mode=1))
 
@@ -293,6 +304,49 @@ def test_adjoint_modes_agree(api, tiny):
     gs.check()
     # same terms, different atomic order
     torch.testing.assert_close(g1, g2, rtol=1e-5, atol=1e-7)
+
+
+def _open_box():
+    """Five inward faces of [-1,1]^3 (the top open), each an instance of one
+    4x4-quad plane: paths bounce for many depths before they escape."""
+    v, q = I.plane_mesh(4)
+    faces = [
+        (np.eye(3), (0.0, 0.0, -1.0)),                                   # floor
+        (np.array([[0, 0, 1], [1, 0, 0], [0, 1, 0]], float), (-1.0, 0.0, 0.0)),
+        (np.array([[0, 0, 1], [1, 0, 0], [0, 1, 0]], float), (1.0, 0.0, 0.0)),
+        (np.array([[1, 0, 0], [0, 0, -1], [0, 1, 0]], float), (0.0, -1.0, 0.0)),
+        (np.array([[1, 0, 0], [0, 0, -1], [0, 1, 0]], float), (0.0, 1.0, 0.0)),
+    ]
+    xf = np.array([np.concatenate([L, np.array(t)[:, None]], axis=1).ravel() for L, t in faces],
+                  dtype=np.float32)
+    return I.Scene([(v, q)], xf, np.zeros(len(faces), dtype=np.uint32))
+
+
+def test_adjoint_beyond_recorded_shadow_depths(api):
+    """The wavefront adjoint replays shadow-ray visibility from bits the
+    primal records for depths 1..32 and traces the shadow rays of deeper
+    vertices; the single-kernel adjoint traces every shadow ray again.  In an
+    open box that keeps paths bouncing past depth 32 the two gradients agree."""
+    sc = _open_box()
+    gs = api.Scene(sc)
+    view = I.View(eye=(0.1, 0.2, 0.6), look=(0.0, 0.0, -1.0), up=(0, 1, 0), vfov_deg=100.0,
+                  w=64, h=64, spp=16)
+    D = 40
+    params = I.Params(max_depth=D, env=(0.5, 0.5, 0.5), sun_dir=(0.2, 0.3, 1.0), sun_E=(3, 2, 1))
+    alb = torch.from_numpy(I.albedo(sc.n_quads, lo=0.85, hi=0.95)).cuda()
+    log = torch.zeros(api.path_log_words([view], D), dtype=torch.int32, device="cuda")
+    gs.render([view], alb, params, path_log=log)
+    gl = log.cpu().numpy().view(np.uint32).reshape(-1, 2 * D + 1)
+    assert (gl[:, 2 * 32] != NONE).sum() > 50          # hits at depth 33 exist
+    dimg = torch.from_numpy(np.random.default_rng(5).normal(size=(view.h, view.w, 3))
+                            .astype(np.float32)).cuda()
+    g1 = torch.zeros_like(alb)
+    g2 = torch.zeros_like(alb)
+    gs.adjoint([view], alb, [dimg], g1, params, tuning=dict(mode=1))
+    gs.adjoint([view], alb, [dimg], g2, params, tuning=dict(mode=2))
+    gs.check()
+    assert float(g1.abs().max()) > 0.0
+    torch.testing.assert_close(g1, g2, rtol=1e-5, atol=1e-6 * float(g1.abs().max()))
 
 
 def test_autotuner_choice_is_valid_and_changes_no_pixel(api, tiny, tmp_path):
