@@ -16,7 +16,6 @@ __global__ void __maxnreg__(occupancy_regs(OCC)) trace_kernel(const DevScene S, 
                                                        unsigned long long* stats, int stack_cap) {
     TraceStats st{0, 0, 0, 0, 0, 0};
     Traversal<ANY, kMaxStack, FETCH> T;
-    T.cap = stack_cap;
     uint64_t i = 0;
     uint32_t err = 0;
     uint64_t bad = ~0ull;
@@ -39,8 +38,8 @@ __global__ void __maxnreg__(occupancy_regs(OCC)) trace_kernel(const DevScene S, 
             hits[i] = make_uint4(__float_as_uint(T.h.t), T.h.inst, T.h.prim, uv);
         }
     };
-    persistent_trace<ANY, kMaxStack, FETCH>(S, T, st, cursor, (unsigned long long)n, batch, start_ray,
-                                            finish_ray);
+    persistent_trace<ANY, kMaxStack, FETCH>(S, T, st, cursor, (unsigned long long)n, batch, stack_cap,
+                                            start_ray, finish_ray);
     if (err) {
         atomicOr(S.err, err);
         atomicMin(S.err + 1, (uint32_t)min(bad, (uint64_t)0xFFFFFFFEu));

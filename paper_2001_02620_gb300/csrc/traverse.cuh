@@ -59,7 +59,6 @@ struct Hit {
 struct RaySetup {
     float ox, oy, oz;     // origin
     float ix, iy, iz;     // reciprocal direction, |d| clamped away from 0
-    uint32_t neg;         // bit a: direction negative along axis a
     float delta;
     float dx, dy, dz;  // direction in the current space (for the shear)
 };
@@ -87,7 +86,6 @@ __device__ __forceinline__ void setup_boxes(RaySetup& r, float ox, float oy, flo
     r.ix = __frcp_rn(clamp_dir(dx));
     r.iy = __frcp_rn(clamp_dir(dy));
     r.iz = __frcp_rn(clamp_dir(dz));
-    r.neg = (r.ix < 0.f ? 1u : 0u) | (r.iy < 0.f ? 2u : 0u) | (r.iz < 0.f ? 4u : 0u);
     r.delta = delta;
     r.dx = dx;
     r.dy = dy;
@@ -189,9 +187,12 @@ __device__ __forceinline__ int node_children(const QNode* node, const RaySetup& 
     const float bny = by - py, bfy = by + py;
     const float bnz = bz - pz, bfz = bz + pz;
     // words: lo x,y,z = B.x, B.y, B.z ; hi x,y,z = B.w, C.x, C.y
-    const uint32_t nwx = (r.neg & 1u) ? B.w : B.x, fwx = (r.neg & 1u) ? B.x : B.w;
-    const uint32_t nwy = (r.neg & 2u) ? C.x : B.y, fwy = (r.neg & 2u) ? B.y : C.x;
-    const uint32_t nwz = (r.neg & 4u) ? C.y : B.z, fwz = (r.neg & 4u) ? B.z : C.y;
+    // near/far planes by the sign of the direction (compared here rather than
+    // kept as bits: one register less per ray)
+    const bool sx = r.ix < 0.f, sy = r.iy < 0.f, sz = r.iz < 0.f;
+    const uint32_t nwx = sx ? B.w : B.x, fwx = sx ? B.x : B.w;
+    const uint32_t nwy = sy ? C.x : B.y, fwy = sy ? B.y : C.x;
+    const uint32_t nwz = sz ? C.y : B.z, fwz = sz ? B.z : C.y;
     const uint32_t meta = D.z;
     const uint32_t child[4] = {C.z, C.w, D.x, D.y};
 #pragma unroll
@@ -457,10 +458,10 @@ struct Traversal {
     // any-hit rays never cull by distance (tmax stays put until the ray
     // ends), so their entries hold the reference alone
     std::conditional_t<ANY, uint32_t, uint64_t> stack[STACK];
-    int cap;  // stack entries a ray may use (<= STACK); set once per kernel
     int sp, inst_sp;
     bool top, have;
-    uint32_t node_base, quad_base, cur_inst, cur, steps, max_steps, err;
+    uint32_t node_base, cur_inst, cur, err;
+    uint32_t budget;  // inner-node tests left before the step limit
     float cur_t;     // entry distance of the box of cur (from its parent's test)
     float h_eps;     // error bound of h.t (0 if exact)
     uint32_t pleaf;  // postponed BLAS leaf reference (0 = none)
@@ -487,15 +488,13 @@ struct Traversal {
         inst_sp = -1;
         top = true;
         node_base = S.tlas_base;
-        quad_base = 0;
         cur_inst = 0;
         te = 0.f;
         cur = 0;  // TLAS root, an inner reference
         cur_t = t0;
         h_eps = 0.f;
         have = S.n_inst > 0;
-        steps = 0;
-        max_steps = msteps;
+        budget = msteps;
         err = 0;
         pleaf = 0;
         setup_world(S);
@@ -521,10 +520,11 @@ struct Traversal {
     __device__ __forceinline__ bool step(const DevScene& S, TraceStats& st) {
         if (have) {
             if (!(cur & kRefLeaf)) {
-                if (++steps > max_steps) {
+                if (budget == 0) {
                     err |= kErrStepLimit;
                     return false;
                 }
+                --budget;
                 ++st.nodes;
                 float t[4];
                 uint32_t ref[4];
@@ -533,7 +533,7 @@ struct Traversal {
                 if (nh == 0) {
                     have = false;
                 } else {
-                    if (sp + nh - 1 > cap) {
+                    if (sp + nh - 1 > STACK) {
                         err |= kErrStackOverflow;
                         return false;
                     }
@@ -622,11 +622,12 @@ struct Traversal {
     }
 
     // Tests the inner node cur and moves on (precondition: wants_inner()).
-    __device__ __forceinline__ void inner_step(const DevScene& S, TraceStats& st) {
-        if (++steps > max_steps) {
+    __device__ __forceinline__ void inner_step(const DevScene& S, TraceStats& st, int cap) {
+        if (budget == 0) {
             stop(kErrStepLimit);
             return;
         }
+        --budget;
         ++st.nodes;
         float t[4];
         uint32_t ref[4];
@@ -711,7 +712,6 @@ struct Traversal {
         const float fdy = __fmaf_rn(m1.w, wdx, __fmaf_rn(m2.x, wdy, __fmul_rn(m2.y, wdz)));
         const float fdz = __fmaf_rn(m2.z, wdx, __fmaf_rn(m2.w, wdy, __fmul_rn(m3.x, wdz)));
         node_base = __float_as_uint(m3.y);
-        quad_base = __float_as_uint(m3.z);
         // 2^-22 (kappa + 2) (|o''| + R): rounding of W, of W (p - c), of W d and
         // of the slab and shear arithmetic, with a factor-two margin
         const float delta = __fmul_rn(2.384185791015625e-07f * (m3.w + 2.0f),
@@ -749,6 +749,9 @@ struct Traversal {
         const float smax = __fsub_rn(tmax, te);
         const InstDev* ip = S.inst + cur_inst;
         const InstDev64* ip64 = S.inst64 + cur_inst;
+        // read here (an L1 hit after the instance entry) rather than kept
+        // live for the whole BLAS traversal
+        const uint32_t quad_base = __ldg(&ip->quad_base);
         for (uint32_t k = 0; k < cnt; ++k) {
             const uint32_t slot = quad_base + first + k;
             float tt, uu, vv;
@@ -815,7 +818,9 @@ struct Traversal {
 
 // Persistent warp-synchronous traversal loop over work items [0, count)
 // claimed from *cursor.  Each lane holds one ray; start(k) sets item k up in
-// T (T.init), done() consumes the finished ray in T.  A lane claims `batch`
+// T (T.init), done() consumes the finished ray in T; a ray may use cap (<=
+// STACK) stack entries, a launch-wide value passed down rather than kept per
+// ray.  A lane claims `batch`
 // items at a time; the idle lanes of a warp claim theirs with one atomic
 // (warp-aggregated), so a launch costs about one atomic per warp and
 // refill round instead of one per thread.  Per outer iteration
@@ -827,7 +832,7 @@ struct Traversal {
 template <bool ANY, int STACK, int FETCH, class Idx, class Start, class Done>
 __device__ __forceinline__ void persistent_trace(const DevScene& S, Traversal<ANY, STACK, FETCH>& T,
                                                  TraceStats& st, Idx* cursor, Idx count,
-                                                 uint32_t batch, Start start, Done done) {
+                                                 uint32_t batch, int cap, Start start, Done done) {
     const unsigned FULL = 0xFFFFFFFFu;
     const unsigned lane = threadIdx.x & 31u;
     bool busy = false, exhausted = false;
@@ -873,7 +878,7 @@ __device__ __forceinline__ void persistent_trace(const DevScene& S, Traversal<AN
             // outer iteration makes progress.
             const unsigned bo = __ballot_sync(FULL, busy && !w);
             if (bo && 2 * __popc(bw) <= __popc(bo)) break;
-            if (w) T.inner_step(S, st);
+            if (w) T.inner_step(S, st, cap);
         }
         if (busy) {
             if (T.at_instance()) {
@@ -901,7 +906,6 @@ __device__ __forceinline__ uint32_t trace_ray(const DevScene& S, float wox, floa
                                               float tmax, uint32_t max_steps, Hit& h,
                                               TraceStats& st) {
     Traversal<ANY, STACK, FETCH> T;
-    T.cap = STACK;
     T.init(S, wox, woy, woz, wdx, wdy, wdz, tmin, tmax, max_steps, st);
     while (T.step(S, st)) {
     }

@@ -110,7 +110,6 @@ __global__ void __maxnreg__(occupancy_regs(OCC)) wave_trace(const __grid_constan
     const uint32_t batch = A.batch;
     TraceStats st{0, 0, 0, 0, 0, 0};
     Traversal<ANY, kMaxStack, FETCH> T;
-    T.cap = stack_cap;
     uint32_t j = 0;
     uint32_t err = 0;
     auto start_ray = [&](uint32_t k) {
@@ -127,7 +126,7 @@ __global__ void __maxnreg__(occupancy_regs(OCC)) wave_trace(const __grid_constan
     auto finish_ray = [&]() {
         err |= T.err;
         if constexpr (STATS) {
-            if (A.cost_on) atomicAdd(A.B.cost + j, T.steps);
+            if (A.cost_on) atomicAdd(A.B.cost + j, A.P.max_steps - T.budget);
         }
         if (ANY) {
             if (T.h.inst == 0xFFFFFFFFu) {
@@ -147,7 +146,8 @@ __global__ void __maxnreg__(occupancy_regs(OCC)) wave_trace(const __grid_constan
             A.B.hit[j] = make_uint4(__float_as_uint(T.h.t), T.h.inst, T.h.prim, T.h.slot);
         }
     };
-    persistent_trace<ANY, kMaxStack, FETCH>(A.S, T, st, fetch, count, batch, start_ray, finish_ray);
+    persistent_trace<ANY, kMaxStack, FETCH>(A.S, T, st, fetch, count, batch, stack_cap, start_ray,
+                                            finish_ray);
     if (err) atomicOr(A.S.err, err);
     if constexpr (STATS) add_stats(A.stats + (ANY ? 6 : 0), st);
 }
