@@ -22,6 +22,7 @@ __global__ void __maxnreg__(occupancy_regs(OCC)) trace_kernel(const DevScene S, 
     auto start_ray = [&](unsigned long long k) {
         i = k;
         const float4 a = __ldg(rays + 2 * i), b = __ldg(rays + 2 * i + 1);
+        T.err = 0;  // per ray: the first affected ray is reported
         T.init(S, a.x, a.y, a.z, b.x, b.y, b.z, a.w, b.w, max_steps, st);
     };
     auto finish_ray = [&]() {

@@ -460,7 +460,8 @@ struct Traversal {
     std::conditional_t<ANY, uint32_t, uint64_t> stack[STACK];
     int sp, inst_sp;
     bool top, have;
-    uint32_t node_base, cur_inst, cur, err;
+    uint32_t node_base, cur_inst, cur;
+    uint32_t err;     // device error bits; init leaves them, the kernel resets them
     uint32_t budget;  // inner-node tests left before the step limit
     float cur_t;     // entry distance of the box of cur (from its parent's test)
     float h_eps;     // error bound of h.t (0 if exact)
@@ -495,7 +496,6 @@ struct Traversal {
         h_eps = 0.f;
         have = S.n_inst > 0;
         budget = msteps;
-        err = 0;
         pleaf = 0;
         setup_world(S);
     }
@@ -738,6 +738,13 @@ struct Traversal {
         return hi;
     }
 
+    // The closest hit's original quad index, looked up from its slot once the
+    // ray has ended (ties during traversal read it on demand), so it is not
+    // live through the traversal.  Any-hit results carry no quad index.
+    __device__ __forceinline__ void resolve_prim(const DevScene& S) {
+        if constexpr (!ANY) h.prim = h.inst == 0xFFFFFFFFu ? 0xFFFFFFFFu : __ldg(S.prim + h.slot);
+    }
+
     // Tests the quads of the current BLAS leaf; returns true when an any-hit
     // query is answered.  Two candidates whose FP32 distances are within
     // their error bounds of each other are ordered by their FP64 distances.
@@ -766,7 +773,6 @@ struct Traversal {
             if (ANY) {
                 h.t = tt;
                 h.inst = cur_inst;
-                h.prim = __ldg(S.prim + slot);
                 h.slot = slot;
                 return true;
             }
@@ -778,13 +784,13 @@ struct Traversal {
                 const double tb = exact_t(S, h.inst, h.slot, wox, woy, woz, wdx, wdy, wdz, tmin);
                 const double tc = ex64 ? t64
                                        : exact_t(S, cur_inst, slot, wox, woy, woz, wdx, wdy, wdz, tmin);
-                const uint32_t pr = __ldg(S.prim + slot);
-                const bool better = tc < tb || (tc == tb && (cur_inst < h.inst ||
-                                                             (cur_inst == h.inst && pr < h.prim)));
+                const bool better =
+                    tc < tb || (tc == tb && (cur_inst < h.inst ||
+                                             (cur_inst == h.inst &&
+                                              __ldg(S.prim + slot) < __ldg(S.prim + h.slot))));
                 if (better && tc < (double)tmax) {
                     h.t = (float)tc;
                     h.inst = cur_inst;
-                    h.prim = pr;
                     h.u = uu;
                     h.v = vv;
                     h.slot = slot;
@@ -795,16 +801,14 @@ struct Traversal {
             if (tt < h.t) {
                 h.t = tt;
                 h.inst = cur_inst;
-                h.prim = __ldg(S.prim + slot);
                 h.u = uu;
                 h.v = vv;
                 h.slot = slot;
                 h_eps = ex64 ? 0.f : sh.eps_t;
             } else if (tt == h.t) {
-                const uint32_t pr = __ldg(S.prim + slot);
-                if (cur_inst < h.inst || (cur_inst == h.inst && pr < h.prim)) {
+                if (cur_inst < h.inst ||
+                    (cur_inst == h.inst && __ldg(S.prim + slot) < __ldg(S.prim + h.slot))) {
                     h.inst = cur_inst;
-                    h.prim = pr;
                     h.u = uu;
                     h.v = vv;
                     h.slot = slot;
@@ -835,10 +839,12 @@ __device__ __forceinline__ void persistent_trace(const DevScene& S, Traversal<AN
                                                  uint32_t batch, int cap, Start start, Done done) {
     const unsigned FULL = 0xFFFFFFFFu;
     const unsigned lane = threadIdx.x & 31u;
-    bool busy = false, exhausted = false;
+    // [next, end) = this lane's claimed items not yet started; a claim that
+    // lands at or past count leaves end == count, which ends the claiming
+    bool busy = false;
     Idx next = 0, end = 0;
     for (;;) {
-        const bool need = !busy && !exhausted && next >= end;
+        const bool need = !busy && next >= end && end < count;
         const unsigned want = __ballot_sync(FULL, need);
         if (want) {
             const int leader = __ffs(want) - 1;
@@ -848,10 +854,9 @@ __device__ __forceinline__ void persistent_trace(const DevScene& S, Traversal<AN
             if (need) {
                 next = base + (Idx)batch * (Idx)__popc(want & ((1u << lane) - 1u));
                 end = min(next + (Idx)batch, count);
-                exhausted = next >= count;
             }
         }
-        if (!busy && !exhausted) {
+        if (!busy && next < end) {
             start(next++);
             busy = true;
         }
@@ -890,6 +895,7 @@ __device__ __forceinline__ void persistent_trace(const DevScene& S, Traversal<AN
                 }
             }
             if (T.finished() || (ANY && T.h.inst != 0xFFFFFFFFu)) {
+                T.resolve_prim(S);
                 done();
                 busy = false;
             }
@@ -906,9 +912,11 @@ __device__ __forceinline__ uint32_t trace_ray(const DevScene& S, float wox, floa
                                               float tmax, uint32_t max_steps, Hit& h,
                                               TraceStats& st) {
     Traversal<ANY, STACK, FETCH> T;
+    T.err = 0;
     T.init(S, wox, woy, woz, wdx, wdy, wdz, tmin, tmax, max_steps, st);
     while (T.step(S, st)) {
     }
+    T.resolve_prim(S);
     h = T.h;
     return T.err;
 }

@@ -110,8 +110,8 @@ __global__ void __maxnreg__(occupancy_regs(OCC)) wave_trace(const __grid_constan
     const uint32_t batch = A.batch;
     TraceStats st{0, 0, 0, 0, 0, 0};
     Traversal<ANY, kMaxStack, FETCH> T;
+    T.err = 0;  // accumulated over this thread's rays
     uint32_t j = 0;
-    uint32_t err = 0;
     auto start_ray = [&](uint32_t k) {
         j = queue[k];
         if (ANY) {
@@ -119,12 +119,14 @@ __global__ void __maxnreg__(occupancy_regs(OCC)) wave_trace(const __grid_constan
             T.init(A.S, o.x, o.y, o.z, A.P.sun_l[0], A.P.sun_l[1], A.P.sun_l[2], 0.f, kInfF,
                    A.P.max_steps, st);
         } else {
+            // path rays span (0, inf) (the spawn point is offset off the
+            // surface): constant bounds fold into the traversal instead of
+            // occupying two registers per ray
             const float4 o = A.B.ray_o[j], d = A.B.ray_d[j];
-            T.init(A.S, o.x, o.y, o.z, d.x, d.y, d.z, o.w, d.w, A.P.max_steps, st);
+            T.init(A.S, o.x, o.y, o.z, d.x, d.y, d.z, 0.f, kInfF, A.P.max_steps, st);
         }
     };
     auto finish_ray = [&]() {
-        err |= T.err;
         if constexpr (STATS) {
             if (A.cost_on) atomicAdd(A.B.cost + j, A.P.max_steps - T.budget);
         }
@@ -148,7 +150,7 @@ __global__ void __maxnreg__(occupancy_regs(OCC)) wave_trace(const __grid_constan
     };
     persistent_trace<ANY, kMaxStack, FETCH>(A.S, T, st, fetch, count, batch, stack_cap, start_ray,
                                             finish_ray);
-    if (err) atomicOr(A.S.err, err);
+    if (T.err) atomicOr(A.S.err, T.err);
     if constexpr (STATS) add_stats(A.stats + (ANY ? 6 : 0), st);
 }
 

@@ -21,8 +21,8 @@ constexpr int kCtrFetchShadow = 3;
 constexpr int kVisDepths = 32;
 
 struct WaveBufs {
-    float4* ray_o;   // origin.xyz, tmin
-    float4* ray_d;   // direction.xyz, tmax
+    float4* ray_o;   // origin.xyz, tmin (0: path rays span (0, inf))
+    float4* ray_d;   // direction.xyz, tmax (inf)
     float4* beta;    // throughput
     float4* L;       // radiance (primal) / sun terms so far (replay); w: bits
                      // of the path's unoccluded shadow rays, depths 1..32
