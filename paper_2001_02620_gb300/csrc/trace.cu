@@ -19,9 +19,11 @@ __global__ void __maxnreg__(occupancy_regs(OCC)) trace_kernel(const DevScene S, 
     uint64_t i = 0;
     uint32_t err = 0;
     uint64_t bad = ~0ull;
+    WRay w{};  // kept per lane: reloading it from the ray array measured slower here
     auto start_ray = [&](unsigned long long k) {
         i = k;
         const float4 a = __ldg(rays + 2 * i), b = __ldg(rays + 2 * i + 1);
+        w = WRay{a.x, a.y, a.z, b.x, b.y, b.z};
         T.err = 0;  // per ray: the first affected ray is reported
         T.init(S, a.x, a.y, a.z, b.x, b.y, b.z, a.w, b.w, max_steps, st);
     };
@@ -39,8 +41,9 @@ __global__ void __maxnreg__(occupancy_regs(OCC)) trace_kernel(const DevScene S, 
             hits[i] = make_uint4(__float_as_uint(T.h.t), T.h.inst, T.h.prim, uv);
         }
     };
+    auto world_ray = [&]() { return w; };
     persistent_trace<ANY, kMaxStack, FETCH>(S, T, st, cursor, (unsigned long long)n, batch, stack_cap,
-                                            start_ray, finish_ray);
+                                            start_ray, finish_ray, world_ray);
     if (err) {
         atomicOr(S.err, err);
         atomicMin(S.err + 1, (uint32_t)min(bad, (uint64_t)0xFFFFFFFEu));

@@ -55,6 +55,14 @@ struct Hit {
     uint32_t slot;  // global quad slot of the hit (for shading)
 };
 
+// A world-space ray (origin, direction).  The traversal asks a caller-given
+// functor for it where it is needed (instance entry, return to the TLAS, FP64
+// re-tests) instead of keeping six floats live for the whole ray: kernels
+// whose rays sit in device memory reload them from there.
+struct WRay {
+    float ox, oy, oz, dx, dy, dz;
+};
+
 // Ray in the current space, with everything the node and quad tests reuse.
 struct RaySetup {
     float ox, oy, oz;     // origin
@@ -338,10 +346,10 @@ static __device__ __noinline__ int quad_test64(const InstDev* ip, const InstDev6
 // error band of zero, or the hit distance within eps_t of either end of the
 // interval -- is re-tested by quad_test64, which returns the world t
 // (*t64_out, *exact64 = 1).  Returns 1 on a hit.
+template <class World>
 __device__ __forceinline__ int quad_test(const RaySetup& r, const Shear& sh, const QuadDev* q,
-                                         const InstDev* ip,
-                                         const InstDev64* ip64, float wox, float woy, float woz,
-                                         float wdx, float wdy, float wdz, float smin, float smax,
+                                         const InstDev* ip, const InstDev64* ip64,
+                                         const World& world, float smin, float smax,
                                          float tmin, float* t_out, double* t64_out, float* u_out,
                                          float* v_out, int* exact64, uint32_t* n_fallback) {
     const float4* p = reinterpret_cast<const float4*>(q);
@@ -393,7 +401,8 @@ __device__ __forceinline__ int quad_test(const RaySetup& r, const Shear& sh, con
         ++*n_fallback;
         double t64;
         float vv[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
-        if (!quad_test64(ip, ip64, wox, woy, woz, wdx, wdy, wdz, vv, tmin, &t64, u_out, v_out))
+        const WRay w = world();
+        if (!quad_test64(ip, ip64, w.ox, w.oy, w.oz, w.dx, w.dy, w.dz, vv, tmin, &t64, u_out, v_out))
             return 0;
         *t_out = (float)t64;
         *t64_out = t64;
@@ -452,7 +461,7 @@ __device__ __forceinline__ void add_stats(unsigned long long* stats, const Trace
 // lanes, so no lane waits for the slowest ray of its warp.
 template <bool ANY, int STACK, int FETCH>
 struct Traversal {
-    float wox, woy, woz, wdx, wdy, wdz, tmin, tmax;
+    float tmin, tmax;
     float te;  // object-space parameter offset: t = s + te
     RaySetup r;
     // any-hit rays never cull by distance (tmax stays put until the ray
@@ -471,12 +480,6 @@ struct Traversal {
     __device__ __forceinline__ void init(const DevScene& S, float ox, float oy, float oz, float dx,
                                          float dy, float dz, float t0, float t1, uint32_t msteps,
                                          TraceStats& st) {
-        wox = ox;
-        woy = oy;
-        woz = oz;
-        wdx = dx;
-        wdy = dy;
-        wdz = dz;
         tmin = t0;
         tmax = t1;
         h.t = t1;
@@ -497,7 +500,7 @@ struct Traversal {
         have = S.n_inst > 0;
         budget = msteps;
         pleaf = 0;
-        setup_world(S);
+        setup_world(S, WRay{ox, oy, oz, dx, dy, dz});
     }
 
     // The world ray's box-test setup, widened by 2^-20 (|o| + R_top): the
@@ -505,9 +508,9 @@ struct Traversal {
     // arithmetic at the top level.  Recomputed on every return to the TLAS
     // rather than kept live: at 64 registers that shrinks the closest-hit
     // kernel's spill stores from 500 to 384 bytes per thread.
-    __device__ __forceinline__ void setup_world(const DevScene& S) {
-        setup_boxes(r, wox, woy, woz, wdx, wdy, wdz,
-                    9.5367431640625e-07f * (maxabs3(wox, woy, woz) + S.R_top));
+    __device__ __forceinline__ void setup_world(const DevScene& S, const WRay& w) {
+        setup_boxes(r, w.ox, w.oy, w.oz, w.dx, w.dy, w.dz,
+                    9.5367431640625e-07f * (maxabs3(w.ox, w.oy, w.oz) + S.R_top));
     }
 
     // far end of the interval in the current space (object space: s units,
@@ -517,7 +520,8 @@ struct Traversal {
                    : __fadd_rn(__fsub_rn(h.t, te), 1.9073486328125e-06f * (fabsf(h.t) + fabsf(te)));
     }
 
-    __device__ __forceinline__ bool step(const DevScene& S, TraceStats& st) {
+    template <class World>
+    __device__ __forceinline__ bool step(const DevScene& S, TraceStats& st, const World& world) {
         if (have) {
             if (!(cur & kRefLeaf)) {
                 if (budget == 0) {
@@ -545,10 +549,10 @@ struct Traversal {
                     return true;
                 }
             } else if (top) {
-                enter_instance(S, st);
+                enter_instance(S, st, world);
                 return true;
             } else {
-                if (leaf(S, st)) return false;  // any hit found
+                if (leaf(S, st, world)) return false;  // any hit found
                 have = false;
             }
         }
@@ -557,7 +561,7 @@ struct Traversal {
             top = true;
             node_base = S.tlas_base;
             te = 0.f;
-            setup_world(S);
+            setup_world(S, world());
         }
         if (sp == 0) return false;
         const uint64_t e = stack[--sp];
@@ -593,7 +597,8 @@ struct Traversal {
     // boundary is reached while a leaf of this instance is still postponed.
     // BLAS leaves met on the way are postponed (one at a time) so that the
     // lane keeps traversing inner nodes with the rest of its warp.
-    __device__ __forceinline__ void advance(const DevScene& S) {
+    template <class World>
+    __device__ __forceinline__ void advance(const DevScene& S, const World& world) {
         for (;;) {
             if (have) {
                 if (pleaf == 0 && !top && (cur & kRefLeaf)) {
@@ -608,7 +613,7 @@ struct Traversal {
                 top = true;
                 node_base = S.tlas_base;
                 te = 0.f;
-                setup_world(S);
+                setup_world(S, world());
             }
             if (sp == 0) return;
             const uint64_t e = stack[--sp];
@@ -622,7 +627,9 @@ struct Traversal {
     }
 
     // Tests the inner node cur and moves on (precondition: wants_inner()).
-    __device__ __forceinline__ void inner_step(const DevScene& S, TraceStats& st, int cap) {
+    template <class World>
+    __device__ __forceinline__ void inner_step(const DevScene& S, TraceStats& st, int cap,
+                                               const World& world) {
         if (budget == 0) {
             stop(kErrStepLimit);
             return;
@@ -646,30 +653,33 @@ struct Traversal {
             cur = ref[0];
             cur_t = t[0];
         }
-        advance(S);
+        advance(S, world);
     }
 
     // Tests one BLAS leaf (the postponed one first); returns true when an
     // any-hit query is answered (precondition: at_leaf()).
-    __device__ __forceinline__ bool leaf_step(const DevScene& S, TraceStats& st) {
+    template <class World>
+    __device__ __forceinline__ bool leaf_step(const DevScene& S, TraceStats& st, const World& world) {
         if (pleaf) {
             const uint32_t keep = cur;
             cur = pleaf;
             pleaf = 0;
-            const bool done = leaf(S, st);
+            const bool done = leaf(S, st, world);
             cur = keep;
             if (done) return true;
         } else {
-            if (leaf(S, st)) return true;
+            if (leaf(S, st, world)) return true;
             have = false;
         }
-        advance(S);
+        advance(S, world);
         return false;
     }
 
     // Enters the instance of the TLAS leaf cur (precondition: at_instance()).
-    __device__ __forceinline__ void instance_step(const DevScene& S, TraceStats& st) {
-        enter_instance(S, st);
+    template <class World>
+    __device__ __forceinline__ void instance_step(const DevScene& S, TraceStats& st,
+                                                  const World& world) {
+        enter_instance(S, st, world);
     }
 
     // Moves the ray into the instance's object space.  The world point
@@ -678,8 +688,12 @@ struct Traversal {
     // (two-product / two-sum), so the FP32 object-space origin W (p - c)
     // carries an error proportional to the object's size only; the BLAS then
     // works in s = t - te.
-    __device__ __forceinline__ void enter_instance(const DevScene& S, TraceStats& st) {
+    template <class World>
+    __device__ __forceinline__ void enter_instance(const DevScene& S, TraceStats& st,
+                                                   const World& world) {
         cur_inst = cur & kRefIndexMask;
+        const WRay w = world();
+        const float wox = w.ox, woy = w.oy, woz = w.oz, wdx = w.dx, wdy = w.dy, wdz = w.dz;
         const float4* ip = reinterpret_cast<const float4*>(S.inst + cur_inst);
         const float4 m0 = __ldg(ip), m1 = __ldg(ip + 1), m2 = __ldg(ip + 2), m3 = __ldg(ip + 3);
         // m0 = (c, R); m1 = (w0 w1 w2 w3); m2 = (w4 w5 w6 w7); m3 = (w8, node_base, quad_base, kappa)
@@ -748,7 +762,8 @@ struct Traversal {
     // Tests the quads of the current BLAS leaf; returns true when an any-hit
     // query is answered.  Two candidates whose FP32 distances are within
     // their error bounds of each other are ordered by their FP64 distances.
-    __device__ __forceinline__ bool leaf(const DevScene& S, TraceStats& st) {
+    template <class World>
+    __device__ __forceinline__ bool leaf(const DevScene& S, TraceStats& st, const World& world) {
         const Shear sh = make_shear(r);
         const uint32_t first = cur & kRefIndexMask;
         const uint32_t cnt = ((cur >> 27) & 0xFu) + 1u;
@@ -765,8 +780,8 @@ struct Traversal {
             double t64;
             int ex64;
             ++st.quads;
-            if (!quad_test(r, sh, S.quads + slot, ip, ip64, wox, woy, woz, wdx, wdy, wdz, smin, smax, tmin,
-                           &tt, &t64, &uu, &vv, &ex64, &st.fallbacks))
+            if (!quad_test(r, sh, S.quads + slot, ip, ip64, world, smin, smax, tmin, &tt, &t64, &uu,
+                           &vv, &ex64, &st.fallbacks))
                 continue;
             if (!ex64) tt = __fadd_rn(tt, te);
             if (!(tt > tmin && tt < tmax)) continue;
@@ -781,9 +796,10 @@ struct Traversal {
                 !(h.slot == slot && h.inst == cur_inst)) {
                 // near tie with the current best: decide on FP64 distances
                 ++st.fallbacks;
-                const double tb = exact_t(S, h.inst, h.slot, wox, woy, woz, wdx, wdy, wdz, tmin);
-                const double tc = ex64 ? t64
-                                       : exact_t(S, cur_inst, slot, wox, woy, woz, wdx, wdy, wdz, tmin);
+                const WRay w = world();
+                const double tb = exact_t(S, h.inst, h.slot, w.ox, w.oy, w.oz, w.dx, w.dy, w.dz, tmin);
+                const double tc =
+                    ex64 ? t64 : exact_t(S, cur_inst, slot, w.ox, w.oy, w.oz, w.dx, w.dy, w.dz, tmin);
                 const bool better =
                     tc < tb || (tc == tb && (cur_inst < h.inst ||
                                              (cur_inst == h.inst &&
@@ -822,7 +838,8 @@ struct Traversal {
 
 // Persistent warp-synchronous traversal loop over work items [0, count)
 // claimed from *cursor.  Each lane holds one ray; start(k) sets item k up in
-// T (T.init), done() consumes the finished ray in T; a ray may use cap (<=
+// T (T.init), done() consumes the finished ray in T, world() gives the world
+// ray of the lane's current item; a ray may use cap (<=
 // STACK) stack entries, a launch-wide value passed down rather than kept per
 // ray.  A lane claims `batch`
 // items at a time; the idle lanes of a warp claim theirs with one atomic
@@ -833,10 +850,11 @@ struct Traversal {
 // groups) until few lanes are left with an inner node, then lanes enter
 // instances or test one leaf each.  Finished lanes refill
 // immediately, so no lane waits for the slowest ray of its warp.
-template <bool ANY, int STACK, int FETCH, class Idx, class Start, class Done>
+template <bool ANY, int STACK, int FETCH, class Idx, class Start, class Done, class World>
 __device__ __forceinline__ void persistent_trace(const DevScene& S, Traversal<ANY, STACK, FETCH>& T,
                                                  TraceStats& st, Idx* cursor, Idx count,
-                                                 uint32_t batch, int cap, Start start, Done done) {
+                                                 uint32_t batch, int cap, Start start, Done done,
+                                                 World world) {
     const unsigned FULL = 0xFFFFFFFFu;
     const unsigned lane = threadIdx.x & 31u;
     // [next, end) = this lane's claimed items not yet started; a claim that
@@ -869,7 +887,7 @@ __device__ __forceinline__ void persistent_trace(const DevScene& S, Traversal<AN
             const bool wt = busy && T.at_instance();
             const unsigned bt = __ballot_sync(FULL, wt);
             if (__popc(bt) >= 8) {
-                if (wt) T.instance_step(S, st);
+                if (wt) T.instance_step(S, st, world);
                 continue;
             }
             const bool w = busy && T.wants_inner();
@@ -883,13 +901,13 @@ __device__ __forceinline__ void persistent_trace(const DevScene& S, Traversal<AN
             // outer iteration makes progress.
             const unsigned bo = __ballot_sync(FULL, busy && !w);
             if (bo && 2 * __popc(bw) <= __popc(bo)) break;
-            if (w) T.inner_step(S, st, cap);
+            if (w) T.inner_step(S, st, cap, world);
         }
         if (busy) {
             if (T.at_instance()) {
-                T.instance_step(S, st);
+                T.instance_step(S, st, world);
             } else if (T.at_leaf()) {
-                if (T.leaf_step(S, st)) {
+                if (T.leaf_step(S, st, world)) {
                     T.have = false;
                     T.pleaf = 0;
                 }
@@ -914,7 +932,8 @@ __device__ __forceinline__ uint32_t trace_ray(const DevScene& S, float wox, floa
     Traversal<ANY, STACK, FETCH> T;
     T.err = 0;
     T.init(S, wox, woy, woz, wdx, wdy, wdz, tmin, tmax, max_steps, st);
-    while (T.step(S, st)) {
+    const auto world = [=] { return WRay{wox, woy, woz, wdx, wdy, wdz}; };
+    while (T.step(S, st, world)) {
     }
     T.resolve_prim(S);
     h = T.h;

@@ -148,8 +148,18 @@ __global__ void __maxnreg__(occupancy_regs(OCC)) wave_trace(const __grid_constan
             A.B.hit[j] = make_uint4(__float_as_uint(T.h.t), T.h.inst, T.h.prim, T.h.slot);
         }
     };
+    // the world ray is read back from the queue buffers where the traversal
+    // needs it, not kept live per lane
+    auto world_ray = [&]() {
+        if (ANY) {
+            const float4 o = __ldg(A.B.sray_o + j);
+            return WRay{o.x, o.y, o.z, A.P.sun_l[0], A.P.sun_l[1], A.P.sun_l[2]};
+        }
+        const float4 o = __ldg(A.B.ray_o + j), d = __ldg(A.B.ray_d + j);
+        return WRay{o.x, o.y, o.z, d.x, d.y, d.z};
+    };
     persistent_trace<ANY, kMaxStack, FETCH>(A.S, T, st, fetch, count, batch, stack_cap, start_ray,
-                                            finish_ray);
+                                            finish_ray, world_ray);
     if (T.err) atomicOr(A.S.err, T.err);
     if constexpr (STATS) add_stats(A.stats + (ANY ? 6 : 0), st);
 }
