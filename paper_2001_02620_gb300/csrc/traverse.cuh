@@ -68,7 +68,6 @@ struct RaySetup {
     float ox, oy, oz;     // origin
     float ix, iy, iz;     // reciprocal direction, |d| clamped away from 0
     float delta;
-    float dx, dy, dz;  // direction in the current space (for the shear)
 };
 
 // Watertight shear of the current-space ray in affine form,
@@ -95,14 +94,12 @@ __device__ __forceinline__ void setup_boxes(RaySetup& r, float ox, float oy, flo
     r.iy = __frcp_rn(clamp_dir(dy));
     r.iz = __frcp_rn(clamp_dir(dz));
     r.delta = delta;
-    r.dx = dx;
-    r.dy = dy;
-    r.dz = dz;
 }
 
-__device__ __forceinline__ Shear make_shear(const RaySetup& r) {
+// (dx, dy, dz): the ray direction in the current space, the same value the
+// box set-up was made from
+__device__ __forceinline__ Shear make_shear(const RaySetup& r, float dx, float dy, float dz) {
     Shear sh;
-    const float dx = r.dx, dy = r.dy, dz = r.dz;
     const float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
     // kz = dominant axis, (kx, ky) the next two in cyclic order; selects
     // instead of indexed arrays keep everything in registers
@@ -722,9 +719,8 @@ struct Traversal {
                               __fmaf_rn(m1.w, exl, __fmaf_rn(m2.x, eyl, __fmul_rn(m2.y, ezl))))));
         const float roz = __fmaf_rn(m2.z, ex, __fmaf_rn(m2.w, ey, __fmaf_rn(m3.x, ez,
                               __fmaf_rn(m2.z, exl, __fmaf_rn(m2.w, eyl, __fmul_rn(m3.x, ezl))))));
-        const float fdx = __fmaf_rn(m1.x, wdx, __fmaf_rn(m1.y, wdy, __fmul_rn(m1.z, wdz)));
-        const float fdy = __fmaf_rn(m1.w, wdx, __fmaf_rn(m2.x, wdy, __fmul_rn(m2.y, wdz)));
-        const float fdz = __fmaf_rn(m2.z, wdx, __fmaf_rn(m2.w, wdy, __fmul_rn(m3.x, wdz)));
+        float fdx, fdy, fdz;
+        object_dir(m1, m2, m3, wdx, wdy, wdz, fdx, fdy, fdz);
         node_base = __float_as_uint(m3.y);
         // 2^-22 (kappa + 2) (|o''| + R): rounding of W, of W (p - c), of W d and
         // of the slab and shear arithmetic, with a factor-two margin
@@ -735,6 +731,16 @@ struct Traversal {
         top = false;
         ++st.insts;
         cur = 0;
+    }
+
+    // W d: the world direction in the instance's object space (m1..m3 hold
+    // W row by row).  Recomputed at each leaf rather than kept per ray.
+    static __device__ __forceinline__ void object_dir(const float4& m1, const float4& m2,
+                                                      const float4& m3, float wdx, float wdy,
+                                                      float wdz, float& fdx, float& fdy, float& fdz) {
+        fdx = __fmaf_rn(m1.x, wdx, __fmaf_rn(m1.y, wdy, __fmul_rn(m1.z, wdz)));
+        fdy = __fmaf_rn(m1.w, wdx, __fmaf_rn(m2.x, wdy, __fmul_rn(m2.y, wdz)));
+        fdz = __fmaf_rn(m2.z, wdx, __fmaf_rn(m2.w, wdy, __fmul_rn(m3.x, wdz)));
     }
 
     // (o + te d) - c per axis as a float pair hi + *lo, exact up to the
@@ -764,7 +770,15 @@ struct Traversal {
     // their error bounds of each other are ordered by their FP64 distances.
     template <class World>
     __device__ __forceinline__ bool leaf(const DevScene& S, TraceStats& st, const World& world) {
-        const Shear sh = make_shear(r);
+        Shear sh;
+        {
+            const float4* mp = reinterpret_cast<const float4*>(S.inst + cur_inst);
+            const float4 m1 = __ldg(mp + 1), m2 = __ldg(mp + 2), m3 = __ldg(mp + 3);
+            const WRay w = world();
+            float dx, dy, dz;
+            object_dir(m1, m2, m3, w.dx, w.dy, w.dz, dx, dy, dz);
+            sh = make_shear(r, dx, dy, dz);
+        }
         const uint32_t first = cur & kRefIndexMask;
         const uint32_t cnt = ((cur >> 27) & 0xFu) + 1u;
         const float smin = __fsub_rn(tmin, te);
