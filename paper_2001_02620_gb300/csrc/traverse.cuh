@@ -1,16 +1,15 @@
 // Device-side traversal of the two-level quad BVH (qrt_layout.h).
 //
 // Top level: four-wide TLAS over instance world boxes.  At a TLAS leaf the ray
-// is re-centred at a point t_e on it near the object, formed exactly with
-// error-free FP32 transformations, and moved into the instance's object space
-// (the direction is not renormalised, so t is shared by both levels); the
-// object's BLAS is traversed on the same stack with a parameter s = t - t_e.
-// Closest-hit rays take t_e where they enter the instance's box: their stack
-// entries keep each box's entry distance (64 bits: distance, reference), which
-// also culls entries beyond the best hit.  Any-hit rays never cull (tmax is
-// fixed until the ray ends), so their entries are the 32-bit reference alone
-// (half the local-memory traffic) and t_e is where the ray passes closest to
-// the object origin.
+// is re-centred at t_e, where it passes closest to the object origin (never
+// before tmin), formed exactly with error-free FP32 transformations, and moved
+// into the instance's object space (the direction is not renormalised, so t
+// is shared by both levels); the object's BLAS is traversed on the same stack
+// with a parameter s = t - t_e.  Closest-hit stack entries keep each box's
+// entry distance (64 bits: distance, reference) to cull entries beyond the
+// best hit; any-hit rays never cull (tmax is fixed until the ray ends), so
+// their entries are the 32-bit reference alone (half the local-memory
+// traffic).
 // When the stack drains back to the level where the instance was entered,
 // the world ray is restored.  Leaves of a BLAS hold up to 16 quads stored
 // contiguously.
@@ -465,11 +464,12 @@ struct Traversal {
     // ends), so their entries hold the reference alone
     std::conditional_t<ANY, uint32_t, uint64_t> stack[STACK];
     int sp, inst_sp;
-    bool top, have;
+    bool have;
+    // at the top level (no instance entered): inst_sp < 0
+    __device__ __forceinline__ bool top() const { return inst_sp < 0; }
     uint32_t node_base, cur_inst, cur;
     uint32_t err;     // device error bits; init leaves them, the kernel resets them
     uint32_t budget;  // inner-node tests left before the step limit
-    float cur_t;     // entry distance of the box of cur (from its parent's test)
     float h_eps;     // error bound of h.t (0 if exact)
     uint32_t pleaf;  // postponed BLAS leaf reference (0 = none)
     Hit h;
@@ -487,12 +487,10 @@ struct Traversal {
         ++st.rays;
         sp = 0;
         inst_sp = -1;
-        top = true;
         node_base = S.tlas_base;
         cur_inst = 0;
         te = 0.f;
         cur = 0;  // TLAS root, an inner reference
-        cur_t = t0;
         h_eps = 0.f;
         have = S.n_inst > 0;
         budget = msteps;
@@ -513,7 +511,7 @@ struct Traversal {
     // far end of the interval in the current space (object space: s units,
     // widened by the rounding of h.t - te)
     __device__ __forceinline__ float limit() const {
-        return top ? h.t
+        return top() ? h.t
                    : __fadd_rn(__fsub_rn(h.t, te), 1.9073486328125e-06f * (fabsf(h.t) + fabsf(te)));
     }
 
@@ -529,7 +527,7 @@ struct Traversal {
                 ++st.nodes;
                 float t[4];
                 uint32_t ref[4];
-                const float lo = top ? tmin : __fsub_rn(tmin, te);
+                const float lo = top() ? tmin : __fsub_rn(tmin, te);
                 const int nh = node_children<FETCH>(S.nodes + node_base + cur, r, lo, limit(), t, ref);
                 if (nh == 0) {
                     have = false;
@@ -542,10 +540,9 @@ struct Traversal {
                     for (int k = 3; k >= 1; --k)
                         if (k < nh) stack[sp++] = ANY ? ref[k] : (((uint64_t)__float_as_uint(t[k]) << 32) | ref[k]);
                     cur = ref[0];
-                    cur_t = t[0];
                     return true;
                 }
-            } else if (top) {
+            } else if (top()) {
                 enter_instance(S, st, world);
                 return true;
             } else {
@@ -554,8 +551,8 @@ struct Traversal {
             }
         }
         // pop
-        if (!top && sp == inst_sp) {
-            top = true;
+        if (!top() && sp == inst_sp) {
+            inst_sp = -1;
             node_base = S.tlas_base;
             te = 0.f;
             setup_world(S, world());
@@ -565,7 +562,6 @@ struct Traversal {
         const float tn = ANY ? tmin : __uint_as_float((uint32_t)(e >> 32));
         if (ANY || tn <= limit()) {
             cur = (uint32_t)e;
-            cur_t = tn;
             have = true;
         }
         return true;
@@ -577,9 +573,9 @@ struct Traversal {
     // current), or finished.
 
     __device__ __forceinline__ bool wants_inner() const { return have && !(cur & kRefLeaf); }
-    __device__ __forceinline__ bool at_instance() const { return have && (cur & kRefLeaf) && top; }
+    __device__ __forceinline__ bool at_instance() const { return have && (cur & kRefLeaf) && top(); }
     __device__ __forceinline__ bool at_leaf() const {
-        return pleaf != 0 || (have && (cur & kRefLeaf) && !top);
+        return pleaf != 0 || (have && (cur & kRefLeaf) && !top());
     }
     __device__ __forceinline__ bool finished() const { return !have && pleaf == 0; }
 
@@ -598,16 +594,16 @@ struct Traversal {
     __device__ __forceinline__ void advance(const DevScene& S, const World& world) {
         for (;;) {
             if (have) {
-                if (pleaf == 0 && !top && (cur & kRefLeaf)) {
+                if (pleaf == 0 && !top() && (cur & kRefLeaf)) {
                     pleaf = cur;
                     have = false;
                 } else {
                     return;
                 }
             }
-            if (!top && sp == inst_sp) {
+            if (!top() && sp == inst_sp) {
                 if (pleaf) return;
-                top = true;
+                inst_sp = -1;
                 node_base = S.tlas_base;
                 te = 0.f;
                 setup_world(S, world());
@@ -617,7 +613,6 @@ struct Traversal {
             const float tn = ANY ? tmin : __uint_as_float((uint32_t)(e >> 32));
             if (ANY || tn <= limit()) {
                 cur = (uint32_t)e;
-                cur_t = tn;
                 have = true;
             }
         }
@@ -635,7 +630,7 @@ struct Traversal {
         ++st.nodes;
         float t[4];
         uint32_t ref[4];
-        const float lo = top ? tmin : __fsub_rn(tmin, te);
+        const float lo = top() ? tmin : __fsub_rn(tmin, te);
         const int nh = node_children<FETCH>(S.nodes + node_base + cur, r, lo, limit(), t, ref);
         if (nh == 0) {
             have = false;
@@ -648,7 +643,6 @@ struct Traversal {
             for (int k = 3; k >= 1; --k)
                 if (k < nh) stack[sp++] = ANY ? ref[k] : (((uint64_t)__float_as_uint(t[k]) << 32) | ref[k]);
             cur = ref[0];
-            cur_t = t[0];
         }
         advance(S, world);
     }
@@ -694,20 +688,17 @@ struct Traversal {
         const float4* ip = reinterpret_cast<const float4*>(S.inst + cur_inst);
         const float4 m0 = __ldg(ip), m1 = __ldg(ip + 1), m2 = __ldg(ip + 2), m3 = __ldg(ip + 3);
         // m0 = (c, R); m1 = (w0 w1 w2 w3); m2 = (w4 w5 w6 w7); m3 = (w8, node_base, quad_base, kappa)
-        if constexpr (ANY) {
-            // no box entry distance on a reference-only stack: re-centre
-            // where the ray passes closest to the object origin (never
-            // before tmin); hits before that point have s < 0
+        // Re-centre where the ray passes closest to the object origin (never
+        // before tmin), so the re-centred origin lies within the object's
+        // reach; hits before that point have s < 0.  (Re-centring at the
+        // instance box's entry distance instead needs that distance kept per
+        // stack entry and per ray, and measured slower with more FP64
+        // re-tests.)
+        {
             const float cx = __fsub_rn(m0.x, wox), cy = __fsub_rn(m0.y, woy), cz = __fsub_rn(m0.z, woz);
             const float dd = __fmaf_rn(wdx, wdx, __fmaf_rn(wdy, wdy, __fmul_rn(wdz, wdz)));
             const float tc = __fdiv_rn(__fmaf_rn(cx, wdx, __fmaf_rn(cy, wdy, __fmul_rn(cz, wdz))), dd);
             te = (tc > tmin && tc < kInfF) ? tc : tmin;
-        } else {
-            // where the ray enters the instance's world box (never before
-            // tmin): every hit lies beyond it, so s = t - te starts at 0 and
-            // keeps full precision near the origin of rays that start on a
-            // surface
-            te = (cur_t < h.t) ? fmaxf(tmin, cur_t) : tmin;
         }
         float exl, eyl, ezl;
         const float ex = exact_offset(wox, wdx, te, m0.x, &exl);
@@ -728,7 +719,6 @@ struct Traversal {
                                       maxabs3(rox, roy, roz) + m0.w);
         setup_boxes(r, rox, roy, roz, fdx, fdy, fdz, delta);
         inst_sp = sp;
-        top = false;
         ++st.insts;
         cur = 0;
     }
