@@ -294,6 +294,31 @@ def bench_cost_map(api, scene, view, d_alb, params, dev, tuning=None):
             "max": float(c.max()), "pixels": int(c.numel())}
 
 
+def bench_device_tlas(api, scene, sc, view, d_alb, params, dev, tuning=None, rays=0):
+    """The same scene with its TLAS built on the device (linear BVH over the
+    instances' Morton order) instead of the host's binned SAH: TLAS build time,
+    render throughput, and how many pixels differ from the SAH scene's image."""
+    import torch
+    t0 = time.time()
+    s2 = api.Scene(sc, build_opts=dict(tlas_builder=1))
+    build_s = time.time() - t0
+    ref = torch.empty((view.h, view.w, 3), device=dev)
+    out = torch.empty_like(ref)
+    t_sah = _time(lambda: scene.render([view], d_alb, params, outs=[ref], tuning=tuning), 5)
+    t_dev = _time(lambda: s2.render([view], d_alb, params, outs=[out], tuning=tuning), 5)
+    s2.check()
+    differ = float((out != ref).any(dim=-1).float().mean().item())
+    res = {"tlas_build_s": s2.stats["phase_seconds"][3],
+           "sah_tlas_build_s": scene.stats["phase_seconds"][3],
+           "scene_build_s": build_s, "tlas_nodes": s2.stats["tlas_nodes"],
+           "tlas_depth": s2.stats["tlas_depth"], "sah_tlas_depth": scene.stats["tlas_depth"],
+           "mrays_s": rays / t_dev / 1e6, "sah_mrays_s": rays / t_sah / 1e6,
+           "pixels_differing": differ,
+           "note": "tlas_build_s covers the build and the host invariant check (phase 3)"}
+    s2.close()
+    return res
+
+
 def bench_adjoint(api, scene, sc, dev, tuning=None):
     """Adjoint workload (512x512, 8 spp, depth 4): replay adjoint vs primal."""
     import torch
@@ -346,13 +371,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--extras", default="trace,batched,adjoint,progressive,costmap",
+    ap.add_argument("--extras", default="trace,batched,adjoint,progressive,costmap,device_tlas",
                     help="comma list of sub-measurements to add (or 'none')")
     ap.add_argument("--res", type=int, default=0,
                     help="override the view side (small profiling captures only)")
     ap.add_argument("--spp", type=int, default=0, help="override spp (profiling only)")
     ap.add_argument("--no-tune", action="store_true", help="library default launch parameters")
     ap.add_argument("--workload", default="mid", choices=sorted(WORKLOADS))
+    ap.add_argument("--tlas-builder", type=int, default=0, choices=[0, 1],
+                    help="TLAS builder: 0 binned SAH on the host, 1 linear BVH on the device")
     ap.add_argument("--moana-scale", type=float, default=1.0,
                     help="moana workload: fraction of the full counts (1 = 261M quads)")
     args = ap.parse_args()
@@ -386,7 +413,7 @@ def main():
         view.spp = args.spp
     view.pixel_base = rank * view.w * view.h  # each rank renders its own frame
     t0 = time.time()
-    scene = api.Scene(sc)
+    scene = api.Scene(sc, build_opts=dict(tlas_builder=args.tlas_builder) if args.tlas_builder else None)
     build_s = time.time() - t0
     dev = torch.device("cuda", local)
     d_alb = torch.from_numpy(alb).to(dev)
@@ -516,6 +543,7 @@ def main():
         "config": {"workload": WORKLOADS[args.workload] if args.workload != "moana" or
                    args.moana_scale == 1.0 else WORKLOADS["moana"] + f" x {args.moana_scale}",
                    "parallelism": f"replicas{world}",
+                   "tlas_builder": "device linear BVH" if args.tlas_builder else "host binned SAH",
                    "l2": f"working set {scene.stats['device_bytes'] / 1e9:.2f} GB > L2 (no flush)"},
         "path_samples_per_s": world * paths / (ms * 1e-3),
         "rays_per_step": rays, "paths_per_step": paths,
@@ -560,7 +588,7 @@ def main():
     }
     extras = [] if args.extras == "none" else args.extras.split(",")
     if args.workload != "mid":
-        extras = [e for e in extras if e in ("trace", "progressive", "costmap")]
+        extras = [e for e in extras if e in ("trace", "progressive", "costmap", "device_tlas")]
     if "trace" in extras:
         line["trace"] = bench_trace(scene, sc, dev, tuning, eye=view.eye)
     if "batched" in extras:
@@ -576,6 +604,9 @@ def main():
         line["cost_map"] = bench_cost_map(api, scene, view, d_alb, params, dev, tuning)
     if "progressive" in extras:
         line["progressive"] = bench_progressive(api, scene, view, d_alb, params, dev, tuning)
+    if "device_tlas" in extras and not args.tlas_builder:
+        line["device_tlas"] = bench_device_tlas(api, scene, sc, view, d_alb, params, dev, tuning,
+                                                rays=rays)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = oracle_sample(sc, view, params, alb, budget_s=12.0,
                                              frame=f"{view.w}x{view.h} {args.workload}")

@@ -185,13 +185,19 @@ typedef struct {
  *              (smaller boxes of a rotated object overlap fewer rays; the
  *              result is intersected with the root-box bound); 0 = default
  *              (6: up to 1024 boxes per instance, fewer for small meshes,
- *              whose cut stops at their leaves) */
+ *              whose cut stops at their leaves)
+ *   tlas_builder 0 = binned SAH on the host threads (default); 1 = linear BVH
+ *              over the instances' Morton order built on the current device
+ *              (much faster to build, looser tree); 2 = the same linear BVH
+ *              steps run on the host (a test aid that needs no GPU).  Every
+ *              TLAS passes the same invariant check before upload. */
 typedef struct {
     uint32_t max_leaf;
     uint32_t sah_bins;
     uint32_t threads;
     uint32_t degenerate;
     uint32_t inst_boxes;
+    uint32_t tlas_builder;
 } qrt_build_opts;
 
 /* Scene statistics (host).  build_seconds covers the host build (phases
@@ -366,6 +372,14 @@ int qrt_check(qrt_scene scene, qrt_stream stream);
  * message naming the broken invariant. */
 int qrt_blas_build_check(const qrt_mesh* mesh, const qrt_build_opts* opts, uint64_t* n_nodes,
                          uint32_t* depth);
+
+/* Test aid: builds a TLAS over n host boxes (float [n*6]: lo xyz, hi xyz)
+ * with opts->tlas_builder (1 needs a CUDA device, 0 and 2 run on the host),
+ * runs the invariant check (every box referenced once, every quantised child
+ * box containing its subtree) and reports the node count and depth.  Errors:
+ * INVALID_ARG (bad boxes, failed check), CUDA. */
+int qrt_tlas_build_check(const float* boxes, uint64_t n, const qrt_build_opts* opts,
+                         uint64_t* n_nodes, uint32_t* depth);
 
 #ifdef __cplusplus
 }

@@ -58,7 +58,7 @@ class qrt_params(C.Structure):
 
 class qrt_build_opts(C.Structure):
     _fields_ = [("max_leaf", C.c_uint32), ("sah_bins", C.c_uint32), ("threads", C.c_uint32),
-                ("degenerate", C.c_uint32), ("inst_boxes", C.c_uint32)]
+                ("degenerate", C.c_uint32), ("inst_boxes", C.c_uint32), ("tlas_builder", C.c_uint32)]
 
 
 class qrt_scene_stats(C.Structure):
@@ -104,6 +104,8 @@ SIGNATURES = {
     "qrt_check": (_i, [_vp, _vp]),
     "qrt_blas_build_check": (_i, [C.POINTER(qrt_mesh), C.POINTER(qrt_build_opts),
                                   C.POINTER(C.c_uint64), C.POINTER(C.c_uint32)]),
+    "qrt_tlas_build_check": (_i, [_vp, _u64, C.POINTER(qrt_build_opts), C.POINTER(C.c_uint64),
+                                  C.POINTER(C.c_uint32)]),
 }
 
 _lock = threading.Lock()

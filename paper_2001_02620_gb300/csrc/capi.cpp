@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "bvh_build.h"
+#include "lbvh.h"
 #include "launch.h"
 #include "wavefront.h"
 
@@ -293,7 +294,14 @@ BuildOpts resolve_build(const qrt_build_opts* o) {
     b.threads = o->threads;
     b.degenerate = o->degenerate;
     if (o->inst_boxes) b.inst_box_level = o->inst_boxes - 1;
+    b.tlas_builder = o->tlas_builder;
     return b;
+}
+
+// The TLAS with the builder the options name (checked by the caller).
+bool make_tlas(const std::vector<FBox>& boxes, const BuildOpts& bo, TlasResult& out, std::string& err) {
+    if (bo.tlas_builder == 0) return build_tlas(boxes, bo, out, err);
+    return build_tlas_lbvh(boxes, bo.tlas_builder == 1, out, err);
 }
 
 template <class T>
@@ -331,6 +339,7 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
             return fail(QRT_ERR_INVALID_ARG, "instance " + std::to_string(i) + " names mesh " +
                                                  std::to_string(mesh_ids[i]) + " out of range");
     if (opts && opts->inst_boxes > 6) return fail(QRT_ERR_INVALID_ARG, "build_opts.inst_boxes must be 0..6");
+    if (opts && opts->tlas_builder > 2) return fail(QRT_ERR_INVALID_ARG, "build_opts.tlas_builder must be 0..2");
     const BuildOpts bo = resolve_build(opts);
     auto t0 = std::chrono::steady_clock::now();
     // wall time of each build phase (reported in qrt_scene_stats)
@@ -539,7 +548,7 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
     lap(2);
     TlasResult tlas;
     std::string terr;
-    if (!build_tlas(wbox, bo, tlas, terr)) return fail(QRT_ERR_INVALID_ARG, "TLAS: " + terr);
+    if (!make_tlas(wbox, bo, tlas, terr)) return fail(QRT_ERR_INVALID_ARG, "TLAS: " + terr);
     {
         uint32_t d = 0;
         if (!check_wide(tlas.nodes, wbox, terr, &d)) return fail(QRT_ERR_INVALID_ARG, "TLAS check: " + terr);
@@ -1186,6 +1195,29 @@ int qrt_check(qrt_scene scene, qrt_stream stream) {
                     "traversal stack overflow (first affected item " + std::to_string(w[1]) + ")");
     return fail(QRT_ERR_STEP_LIMIT,
                 "traversal step limit exceeded (first affected item " + std::to_string(w[1]) + ")");
+}
+
+int qrt_tlas_build_check(const float* boxes, uint64_t n, const qrt_build_opts* opts,
+                         uint64_t* n_nodes, uint32_t* depth) {
+    if (!boxes && n) return fail(QRT_ERR_INVALID_ARG, "boxes is NULL");
+    if (opts && opts->tlas_builder > 2) return fail(QRT_ERR_INVALID_ARG, "build_opts.tlas_builder must be 0..2");
+    std::vector<FBox> items(n);
+    for (uint64_t i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            items[i].lo[a] = boxes[6 * i + a];
+            items[i].hi[a] = boxes[6 * i + 3 + a];
+        }
+    TlasResult t;
+    std::string err;
+    if (!make_tlas(items, resolve_build(opts), t, err)) {
+        const bool cuda = err.compare(0, 5, "CUDA:") == 0;
+        return fail(cuda ? QRT_ERR_CUDA : QRT_ERR_INVALID_ARG, err);
+    }
+    uint32_t d = 0;
+    if (!t.nodes.empty() && !check_wide(t.nodes, items, err, &d)) return fail(QRT_ERR_INVALID_ARG, err);
+    if (n_nodes) *n_nodes = t.nodes.size();
+    if (depth) *depth = d;
+    return QRT_OK;
 }
 
 int qrt_blas_build_check(const qrt_mesh* mesh, const qrt_build_opts* opts, uint64_t* n_nodes,

@@ -89,6 +89,25 @@ def test_mid_trace_closest_and_any(api, mid):
     assert acc_all / total < 1e-5, f"{acc_all} near-tie mismatches in {total} rays"
 
 
+def test_mid_device_built_tlas(api, mid):
+    """The mid scene (100k instances) with its TLAS built on the device: every
+    ray set matches the oracle with no unexplained mismatch."""
+    sc, gs, osc = mid
+    g2 = api.Scene(sc, build_opts=dict(tlas_builder=1))
+    total = acc_all = 0
+    for name, rays in _mid_rays(sc).items():
+        d = torch.from_numpy(rays).cuda()
+        h = g2.trace_closest(d).cpu().numpy().view(np.uint32)
+        g2.check()
+        o_t, o_i, o_p, _, _ = osc.trace_closest(rays)
+        n, acc, bad = classify_closest(sc, rays, h[:, 1], h[:, 2], o_t, o_i, o_p)
+        assert not bad, (name, bad[:5])
+        total += len(rays)
+        acc_all += acc
+    assert acc_all / total < 1e-5
+    del g2
+
+
 def test_mid_frame_time_is_dominated_by_traversal(api, mid):
     """The paper's Table 1 finds 67-75 % of a frame in ray traversal and
     intersection with full shading; with its plain diffuse shading this

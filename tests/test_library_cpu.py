@@ -162,3 +162,69 @@ def test_blas_rejects_bad_meshes(native):
     vn[0, 0] = np.nan
     rc, *_, msg = _check_mesh(native, vn, q)
     assert rc == native.QRT_ERR_INVALID_ARG and "non-finite" in msg
+
+
+def _check_tlas(native, boxes, builder):
+    L = native.lib()
+    b = np.ascontiguousarray(boxes, dtype=np.float32)
+    o = native.qrt_build_opts()
+    o.tlas_builder = builder
+    n = C.c_uint64()
+    d = C.c_uint32()
+    rc = L.qrt_tlas_build_check(b.ctypes.data, b.shape[0], C.byref(o), C.byref(n), C.byref(d))
+    return rc, n.value, d.value, L.qrt_last_error().decode()
+
+
+def _random_boxes(rng, n, spread=100.0, size=5.0):
+    c = rng.uniform(-spread, spread, size=(n, 3))
+    e = rng.uniform(0.1, size, size=(n, 3))
+    return np.concatenate([c - e, c + e], axis=1)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 17, 1000, 100000])
+def test_linear_tlas_invariants_on_host(native, n):
+    """The linear-BVH TLAS steps (Morton order, radix-tree nodes, bottom-up
+    boxes, four-wide collapse, quantisation), run on the host: every instance
+    referenced once and every quantised child box containing its subtree."""
+    boxes = _random_boxes(np.random.default_rng(n), n)
+    rc, nodes, depth, msg = _check_tlas(native, boxes, 2)
+    assert rc == 0, msg
+    assert 1 <= nodes <= max(1, n - 1)
+    assert depth >= int(np.ceil(np.log(max(n, 2)) / np.log(4)))
+    assert depth <= 3 * int(np.ceil(np.log2(max(n, 2)))) + 2
+    rc0, nodes0, _, msg0 = _check_tlas(native, boxes, 0)   # the SAH builder on the same boxes
+    assert rc0 == 0, msg0
+
+
+def test_linear_tlas_degenerate_inputs_on_host(native):
+    rng = np.random.default_rng(7)
+    cases = {
+        # equal Morton keys everywhere: positions break the ties
+        "identical": np.tile(np.array([[0, 0, 0, 1, 1, 1]], np.float32), (1000, 1)),
+        # zero centre extent on two axes
+        "line": np.stack([np.arange(5000.0), np.zeros(5000), np.zeros(5000),
+                          np.arange(5000.0) + 0.5, np.zeros(5000), np.zeros(5000)], axis=1),
+        # far from the origin, tiny extents
+        "far": _random_boxes(rng, 1000) * 1e-6 + 3e4,
+        # huge spread, heavy overlap
+        "wide": _random_boxes(rng, 20000, spread=1e6, size=1e5),
+        # points (zero-volume boxes)
+        "points": np.repeat(rng.uniform(-10, 10, size=(3000, 3)), 2, axis=1).reshape(3000, 6)[:, [0, 2, 4, 1, 3, 5]],
+    }
+    for name, boxes in cases.items():
+        rc, nodes, depth, msg = _check_tlas(native, boxes, 2)
+        assert rc == 0, (name, msg)
+        assert nodes <= boxes.shape[0] - 1, name
+
+
+def test_linear_tlas_rejects_bad_input_on_host(native):
+    boxes = _random_boxes(np.random.default_rng(1), 10)
+    bad = boxes.copy()
+    bad[3, 2] = np.nan
+    assert _check_tlas(native, bad, 2)[0] == native.QRT_ERR_INVALID_ARG
+    inverted = boxes.copy()
+    inverted[4, 0], inverted[4, 3] = 5.0, -5.0
+    assert _check_tlas(native, inverted, 2)[0] == native.QRT_ERR_INVALID_ARG
+    assert _check_tlas(native, boxes, 3)[0] == native.QRT_ERR_INVALID_ARG
+    rc, nodes, depth, _ = _check_tlas(native, boxes[:0], 2)
+    assert rc == 0 and nodes == 0
