@@ -548,7 +548,8 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
     lap(2);
     TlasResult tlas;
     std::string terr;
-    if (!make_tlas(wbox, bo, tlas, terr)) return fail(QRT_ERR_INVALID_ARG, "TLAS: " + terr);
+    if (!make_tlas(wbox, bo, tlas, terr))
+        return fail(terr.compare(0, 5, "CUDA:") == 0 ? QRT_ERR_CUDA : QRT_ERR_INVALID_ARG, "TLAS: " + terr);
     {
         uint32_t d = 0;
         if (!check_wide(tlas.nodes, wbox, terr, &d)) return fail(QRT_ERR_INVALID_ARG, "TLAS check: " + terr);
