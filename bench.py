@@ -294,28 +294,35 @@ def bench_cost_map(api, scene, view, d_alb, params, dev, tuning=None):
             "max": float(c.max()), "pixels": int(c.numel())}
 
 
-def bench_device_tlas(api, scene, sc, view, d_alb, params, dev, tuning=None, rays=0):
-    """The same scene with its TLAS built on the device (linear BVH over the
-    instances' Morton order) instead of the host's binned SAH: TLAS build time,
-    render throughput, and how many pixels differ from the SAH scene's image."""
+def bench_device_build(api, scene, sc, view, d_alb, params, dev, tuning=None, rays=0):
+    """The same scene with its TLAS, then also its BLASes, built on the device
+    (linear BVHs over Morton order) instead of the host's binned SAH: build
+    times, render throughput, and how many pixels differ from the SAH scene's
+    image."""
     import torch
-    t0 = time.time()
-    s2 = api.Scene(sc, build_opts=dict(tlas_builder=1))
-    build_s = time.time() - t0
     ref = torch.empty((view.h, view.w, 3), device=dev)
     out = torch.empty_like(ref)
     t_sah = _time(lambda: scene.render([view], d_alb, params, outs=[ref], tuning=tuning), 5)
-    t_dev = _time(lambda: s2.render([view], d_alb, params, outs=[out], tuning=tuning), 5)
-    s2.check()
-    differ = float((out != ref).any(dim=-1).float().mean().item())
-    res = {"tlas_build_s": s2.stats["phase_seconds"][3],
-           "sah_tlas_build_s": scene.stats["phase_seconds"][3],
-           "scene_build_s": build_s, "tlas_nodes": s2.stats["tlas_nodes"],
-           "tlas_depth": s2.stats["tlas_depth"], "sah_tlas_depth": scene.stats["tlas_depth"],
-           "mrays_s": rays / t_dev / 1e6, "sah_mrays_s": rays / t_sah / 1e6,
-           "pixels_differing": differ,
-           "note": "tlas_build_s covers the build and the host invariant check (phase 3)"}
-    s2.close()
+    res = {"sah": {"blas_build_s": scene.stats["phase_seconds"][0],
+                   "tlas_build_s": scene.stats["phase_seconds"][3],
+                   "tlas_depth": scene.stats["tlas_depth"], "max_blas_depth": scene.stats["max_blas_depth"],
+                   "mrays_s": rays / t_sah / 1e6},
+           "note": "build seconds cover the build and the host invariant check of that level"}
+    for name, opts in (("device_tlas", dict(tlas_builder=1)),
+                       ("device_blas_and_tlas", dict(tlas_builder=1, blas_builder=1))):
+        t0 = time.time()
+        s2 = api.Scene(sc, build_opts=opts)
+        build_s = time.time() - t0
+        t_dev = _time(lambda: s2.render([view], d_alb, params, outs=[out], tuning=tuning), 5)
+        s2.check()
+        ph = s2.stats["phase_seconds"]
+        res[name] = {"blas_build_s": ph[0] + ph[1], "tlas_build_s": ph[3], "scene_build_s": build_s,
+                     "tlas_depth": s2.stats["tlas_depth"], "max_blas_depth": s2.stats["max_blas_depth"],
+                     "mrays_s": rays / t_dev / 1e6,
+                     "pixels_differing": float((out != ref).any(dim=-1).float().mean().item())}
+        s2.close()
+        del s2
+    res["sah"]["blas_build_s"] += scene.stats["phase_seconds"][1]
     return res
 
 
@@ -371,7 +378,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--extras", default="trace,batched,adjoint,progressive,costmap,device_tlas",
+    ap.add_argument("--extras", default="trace,batched,adjoint,progressive,costmap,device_build",
                     help="comma list of sub-measurements to add (or 'none')")
     ap.add_argument("--res", type=int, default=0,
                     help="override the view side (small profiling captures only)")
@@ -588,7 +595,7 @@ def main():
     }
     extras = [] if args.extras == "none" else args.extras.split(",")
     if args.workload != "mid":
-        extras = [e for e in extras if e in ("trace", "progressive", "costmap", "device_tlas")]
+        extras = [e for e in extras if e in ("trace", "progressive", "costmap", "device_build")]
     if "trace" in extras:
         line["trace"] = bench_trace(scene, sc, dev, tuning, eye=view.eye)
     if "batched" in extras:
@@ -604,9 +611,9 @@ def main():
         line["cost_map"] = bench_cost_map(api, scene, view, d_alb, params, dev, tuning)
     if "progressive" in extras:
         line["progressive"] = bench_progressive(api, scene, view, d_alb, params, dev, tuning)
-    if "device_tlas" in extras and not args.tlas_builder:
-        line["device_tlas"] = bench_device_tlas(api, scene, sc, view, d_alb, params, dev, tuning,
-                                                rays=rays)
+    if "device_build" in extras and not args.tlas_builder:
+        line["device_build"] = bench_device_build(api, scene, sc, view, d_alb, params, dev, tuning,
+                                                  rays=rays)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = oracle_sample(sc, view, params, alb, budget_s=12.0,
                                              frame=f"{view.w}x{view.h} {args.workload}")

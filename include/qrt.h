@@ -190,7 +190,12 @@ typedef struct {
  *              over the instances' Morton order built on the current device
  *              (much faster to build, looser tree); 2 = the same linear BVH
  *              steps run on the host (a test aid that needs no GPU).  Every
- *              TLAS passes the same invariant check before upload. */
+ *              TLAS passes the same invariant check before upload.
+ *   blas_builder the same choice for the per-mesh BLASes: 0 = binned SAH per
+ *              mesh on the host threads (default); 1 = all meshes' linear BVHs
+ *              in one pass on the current device (at most 8192 meshes; not
+ *              with degenerate); 2 = those steps on the host (test aid).
+ *              Every BLAS passes the invariant check before upload. */
 typedef struct {
     uint32_t max_leaf;
     uint32_t sah_bins;
@@ -198,6 +203,7 @@ typedef struct {
     uint32_t degenerate;
     uint32_t inst_boxes;
     uint32_t tlas_builder;
+    uint32_t blas_builder;
 } qrt_build_opts;
 
 /* Scene statistics (host).  build_seconds covers the host build (phases
@@ -372,6 +378,13 @@ int qrt_check(qrt_scene scene, qrt_stream stream);
  * message naming the broken invariant. */
 int qrt_blas_build_check(const qrt_mesh* mesh, const qrt_build_opts* opts, uint64_t* n_nodes,
                          uint32_t* depth);
+
+/* Test aid: builds the BLASes of n_mesh meshes as qrt_scene_create would
+ * (opts->blas_builder 1 needs a CUDA device; 0 and 2 run on the host),
+ * verifies every one as qrt_blas_build_check does and reports the total node
+ * count and the largest depth.  Errors: INVALID_ARG, CUDA. */
+int qrt_blases_build_check(const qrt_mesh* meshes, uint32_t n_mesh, const qrt_build_opts* opts,
+                           uint64_t* n_nodes, uint32_t* max_depth);
 
 /* Test aid: builds a TLAS over n host boxes (float [n*6]: lo xyz, hi xyz)
  * with opts->tlas_builder (1 needs a CUDA device, 0 and 2 run on the host),

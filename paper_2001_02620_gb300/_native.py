@@ -58,7 +58,8 @@ class qrt_params(C.Structure):
 
 class qrt_build_opts(C.Structure):
     _fields_ = [("max_leaf", C.c_uint32), ("sah_bins", C.c_uint32), ("threads", C.c_uint32),
-                ("degenerate", C.c_uint32), ("inst_boxes", C.c_uint32), ("tlas_builder", C.c_uint32)]
+                ("degenerate", C.c_uint32), ("inst_boxes", C.c_uint32), ("tlas_builder", C.c_uint32),
+                ("blas_builder", C.c_uint32)]
 
 
 class qrt_scene_stats(C.Structure):
@@ -106,6 +107,8 @@ SIGNATURES = {
                                   C.POINTER(C.c_uint64), C.POINTER(C.c_uint32)]),
     "qrt_tlas_build_check": (_i, [_vp, _u64, C.POINTER(qrt_build_opts), C.POINTER(C.c_uint64),
                                   C.POINTER(C.c_uint32)]),
+    "qrt_blases_build_check": (_i, [_vp, _u32, C.POINTER(qrt_build_opts), C.POINTER(C.c_uint64),
+                                    C.POINTER(C.c_uint32)]),
 }
 
 _lock = threading.Lock()

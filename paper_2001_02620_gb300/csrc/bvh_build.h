@@ -19,6 +19,7 @@ struct BuildOpts {
     uint32_t degenerate = 0;
     uint32_t inst_box_level = 5;  // BLAS level whose node boxes bound an instance (0 = root box)
     uint32_t tlas_builder = 0;    // 0 binned SAH (host), 1 linear BVH (device), 2 linear BVH (host)
+    uint32_t blas_builder = 0;    // the same choice for the BLASes
 };
 
 struct FBox {

@@ -295,6 +295,7 @@ BuildOpts resolve_build(const qrt_build_opts* o) {
     b.degenerate = o->degenerate;
     if (o->inst_boxes) b.inst_box_level = o->inst_boxes - 1;
     b.tlas_builder = o->tlas_builder;
+    b.blas_builder = o->blas_builder;
     return b;
 }
 
@@ -340,6 +341,9 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
                                                  std::to_string(mesh_ids[i]) + " out of range");
     if (opts && opts->inst_boxes > 6) return fail(QRT_ERR_INVALID_ARG, "build_opts.inst_boxes must be 0..6");
     if (opts && opts->tlas_builder > 2) return fail(QRT_ERR_INVALID_ARG, "build_opts.tlas_builder must be 0..2");
+    if (opts && opts->blas_builder > 2) return fail(QRT_ERR_INVALID_ARG, "build_opts.blas_builder must be 0..2");
+    if (opts && opts->blas_builder && opts->degenerate)
+        return fail(QRT_ERR_INVALID_ARG, "build_opts.degenerate needs the host BLAS builder");
     const BuildOpts bo = resolve_build(opts);
     auto t0 = std::chrono::steady_clock::now();
     // wall time of each build phase (reported in qrt_scene_stats)
@@ -358,7 +362,14 @@ int qrt_scene_create(const qrt_mesh* meshes, uint32_t n_mesh, const float* xform
     for (uint32_t m = 0; m < n_mesh; ++m) order[m] = m;
     std::sort(order.begin(), order.end(),
               [&](uint32_t a, uint32_t b) { return meshes[a].n_quads > meshes[b].n_quads; });
-    {
+    if (bo.blas_builder) {  // all meshes at once, linear BVHs
+        std::vector<MeshView> mv(n_mesh);
+        for (uint32_t m = 0; m < n_mesh; ++m)
+            mv[m] = MeshView{meshes[m].verts, meshes[m].n_verts, meshes[m].quads, meshes[m].n_quads};
+        std::string berr;
+        if (!build_blases_lbvh(mv, std::max(1u, std::min(bo.max_leaf, 8u)), bo.blas_builder == 1, blas, berr))
+            return fail(berr.compare(0, 5, "CUDA:") == 0 ? QRT_ERR_CUDA : QRT_ERR_INVALID_ARG, "BLAS: " + berr);
+    } else {
         unsigned nt = bo.threads ? bo.threads : std::max(1u, std::thread::hardware_concurrency());
         nt = std::min<unsigned>(nt, n_mesh);
         std::atomic<uint32_t> next{0};
@@ -1221,14 +1232,86 @@ int qrt_tlas_build_check(const float* boxes, uint64_t n, const qrt_build_opts* o
     return QRT_OK;
 }
 
+// Invariants of one built BLAS: every original quad in exactly one slot,
+// and the four-wide tree checked against the quads' exact boxes.
+static bool check_blas(const BlasResult& r, uint32_t n_quads, std::string& err, uint32_t* depth) {
+    std::vector<FBox> items(r.quads.size());
+    for (size_t s = 0; s < r.quads.size(); ++s) {
+        FBox b;
+        for (int a = 0; a < 3; ++a) {
+            b.lo[a] = std::min(std::min(r.quads[s].v[a], r.quads[s].v[3 + a]),
+                               std::min(r.quads[s].v[6 + a], r.quads[s].v[9 + a]));
+            b.hi[a] = std::max(std::max(r.quads[s].v[a], r.quads[s].v[3 + a]),
+                               std::max(r.quads[s].v[6 + a], r.quads[s].v[9 + a]));
+        }
+        items[s] = b;
+    }
+    std::vector<uint8_t> seen(n_quads, 0);
+    if (r.prim.size() != n_quads) {
+        err = "slot permutation broken";
+        return false;
+    }
+    for (uint32_t p : r.prim)
+        if (p >= n_quads || seen[p]++) {
+            err = "slot permutation broken";
+            return false;
+        }
+    return check_wide(r.nodes, items, err, depth);
+}
+
+int qrt_blases_build_check(const qrt_mesh* meshes, uint32_t n_mesh, const qrt_build_opts* opts,
+                           uint64_t* n_nodes, uint32_t* max_depth) {
+    if (!meshes || n_mesh == 0) return fail(QRT_ERR_INVALID_ARG, "meshes is NULL or empty");
+    const BuildOpts bo = resolve_build(opts);
+    if (bo.blas_builder > 2) return fail(QRT_ERR_INVALID_ARG, "build_opts.blas_builder must be 0..2");
+    std::vector<BlasResult> out(n_mesh);
+    std::string err;
+    if (bo.blas_builder) {
+        std::vector<MeshView> mv(n_mesh);
+        for (uint32_t m = 0; m < n_mesh; ++m) {
+            if (!meshes[m].verts || !meshes[m].quads) return fail(QRT_ERR_INVALID_ARG, "mesh arrays are NULL");
+            mv[m] = MeshView{meshes[m].verts, meshes[m].n_verts, meshes[m].quads, meshes[m].n_quads};
+        }
+        if (!build_blases_lbvh(mv, std::max(1u, std::min(bo.max_leaf, 8u)), bo.blas_builder == 1, out, err))
+            return fail(err.compare(0, 5, "CUDA:") == 0 ? QRT_ERR_CUDA : QRT_ERR_INVALID_ARG, err);
+    } else {
+        for (uint32_t m = 0; m < n_mesh; ++m)
+            if (!meshes[m].verts || !meshes[m].quads ||
+                !build_blas(meshes[m].verts, meshes[m].n_verts, meshes[m].quads, meshes[m].n_quads, bo,
+                            out[m], err))
+                return fail(QRT_ERR_INVALID_ARG, "mesh " + std::to_string(m) + ": " + err);
+    }
+    uint64_t total = 0;
+    uint32_t dmax = 0;
+    for (uint32_t m = 0; m < n_mesh; ++m) {
+        uint32_t d = 0;
+        if (!check_blas(out[m], meshes[m].n_quads, err, &d))
+            return fail(QRT_ERR_INVALID_ARG, "mesh " + std::to_string(m) + ": " + err);
+        total += out[m].nodes.size();
+        dmax = std::max(dmax, d);
+    }
+    if (n_nodes) *n_nodes = total;
+    if (max_depth) *max_depth = dmax;
+    return QRT_OK;
+}
+
 int qrt_blas_build_check(const qrt_mesh* mesh, const qrt_build_opts* opts, uint64_t* n_nodes,
                          uint32_t* depth) {
     if (!mesh || !mesh->verts || !mesh->quads)
         return fail(QRT_ERR_INVALID_ARG, "mesh or its arrays are NULL");
     BlasResult r;
     std::string err;
-    if (!build_blas(mesh->verts, mesh->n_verts, mesh->quads, mesh->n_quads, resolve_build(opts), r, err))
+    const BuildOpts bo = resolve_build(opts);
+    if (bo.blas_builder > 2) return fail(QRT_ERR_INVALID_ARG, "build_opts.blas_builder must be 0..2");
+    if (bo.blas_builder) {
+        std::vector<BlasResult> out;
+        const std::vector<MeshView> mv{MeshView{mesh->verts, mesh->n_verts, mesh->quads, mesh->n_quads}};
+        if (!build_blases_lbvh(mv, std::max(1u, std::min(bo.max_leaf, 8u)), bo.blas_builder == 1, out, err))
+            return fail(err.compare(0, 5, "CUDA:") == 0 ? QRT_ERR_CUDA : QRT_ERR_INVALID_ARG, err);
+        r = std::move(out[0]);
+    } else if (!build_blas(mesh->verts, mesh->n_verts, mesh->quads, mesh->n_quads, bo, r, err)) {
         return fail(QRT_ERR_INVALID_ARG, err);
+    }
     std::vector<FBox> items(r.quads.size());
     for (size_t s = 0; s < r.quads.size(); ++s) {
         FBox b;

@@ -23,4 +23,22 @@ namespace qrt {
 bool build_tlas_lbvh(const std::vector<FBox>& inst_boxes, bool on_device, TlasResult& out,
                      std::string& err);
 
+// One mesh's arrays as given to qrt_scene_create (host memory).
+struct MeshView {
+    const float* verts;
+    uint32_t n_verts;
+    const uint32_t* quads;
+    uint32_t n_quads;
+};
+
+// Builds every mesh's BLAS in one pass: all quads sorted by (mesh, Morton
+// code of the quad centre on the mesh's own grid of cubic cells), one radix
+// tree over them whose mesh-sized subtrees are the BLASes, subtrees of at
+// most max_leaf quads taken as leaves, collapsed to four-wide quantised
+// nodes with each mesh's nodes numbered from its own root.  The results have
+// the host builder's form (nodes, quads in slot order, original quad index
+// per slot, box, depth).  on_device as for the TLAS; at most 8192 meshes.
+bool build_blases_lbvh(const std::vector<MeshView>& meshes, uint32_t max_leaf, bool on_device,
+                       std::vector<BlasResult>& out, std::string& err);
+
 }  // namespace qrt

@@ -378,11 +378,43 @@ def test_linear_tlas_on_device(api, n):
     assert _tlas_check(api, same, 1)[0] == 0
 
 
+def test_linear_blas_on_device(api):
+    """Every mesh's linear BVH built on the device in one pass passes the
+    invariant check and has the shape of the same steps run on the host."""
+    import ctypes as C
+    N = api.N
+    rng = np.random.default_rng(3)
+    meshes = [I.tiny_mesh(), I.displaced_grid(rng, 5000), I.noisy_blob(rng, 3000),
+              I.sphere_mesh(10, 20), I.plane_mesh(1), I.plane_mesh(3), I.displaced_grid(rng, 65536)]
+    vv = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0]], dtype=np.float32)
+    meshes.append((vv, np.tile(np.array([[0, 1, 2, 3]], dtype=np.uint32), (50, 1))))
+    arr = (N.qrt_mesh * len(meshes))()
+    keep = []
+    for k, (v, q) in enumerate(meshes):
+        v = np.ascontiguousarray(v, dtype=np.float32)
+        q = np.ascontiguousarray(q, dtype=np.uint32)
+        keep += [v, q]
+        arr[k].verts = v.ctypes.data_as(C.POINTER(C.c_float))
+        arr[k].n_verts = v.shape[0]
+        arr[k].quads = q.ctypes.data_as(C.POINTER(C.c_uint32))
+        arr[k].n_quads = q.shape[0]
+    res = []
+    for builder in (1, 2):
+        o = N.qrt_build_opts()
+        o.blas_builder = builder
+        n, d = C.c_uint64(), C.c_uint32()
+        rc = N.lib().qrt_blases_build_check(arr, len(meshes), C.byref(o), C.byref(n), C.byref(d))
+        assert rc == 0, N.lib().qrt_last_error().decode()
+        res.append((n.value, d.value))
+    assert res[0] == res[1]
+
+
 def test_device_built_tlas_matches_oracle(api, tiny):
-    """A scene whose TLAS comes from the device's linear-BVH build: ray queries
-    match the oracle as the SAH-built scene's do, and renders agree with it."""
+    """A scene whose TLAS and BLAS come from the device's linear-BVH builds: ray
+    queries match the oracle as the SAH-built scene's do, and renders agree
+    with it."""
     sc, gs, osc = tiny
-    g2 = api.Scene(sc, build_opts=dict(tlas_builder=1))
+    g2 = api.Scene(sc, build_opts=dict(tlas_builder=1, blas_builder=1))
     rays = _rays(sc)
     d = torch.from_numpy(rays).cuda()
     h = g2.trace_closest(d).cpu().numpy().view(np.uint32)

@@ -228,3 +228,72 @@ def test_linear_tlas_rejects_bad_input_on_host(native):
     assert _check_tlas(native, boxes, 3)[0] == native.QRT_ERR_INVALID_ARG
     rc, nodes, depth, _ = _check_tlas(native, boxes[:0], 2)
     assert rc == 0 and nodes == 0
+
+
+def _varied_meshes():
+    rng = np.random.default_rng(3)
+    meshes = [I.tiny_mesh(), I.displaced_grid(rng, 5000), I.noisy_blob(rng, 3000),
+              I.sphere_mesh(10, 20), I.plane_mesh(1), I.plane_mesh(3)]
+    v, q = I.plane_mesh(16)
+    meshes.append((v * np.float32(1e-6) + np.float32(3e4), q))   # far away, tiny
+    meshes.append((v * np.float32(1e5), q))                       # huge
+    vv = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0]], dtype=np.float32)
+    meshes.append((vv, np.tile(np.array([[0, 1, 2, 3]], dtype=np.uint32), (50, 1))))  # coincident
+    return meshes
+
+
+def _check_meshes(native, meshes, **opts):
+    L = native.lib()
+    arr = (native.qrt_mesh * len(meshes))()
+    keep = []
+    for k, (v, q) in enumerate(meshes):
+        v = np.ascontiguousarray(v, dtype=np.float32)
+        q = np.ascontiguousarray(q, dtype=np.uint32)
+        keep += [v, q]
+        arr[k].verts = v.ctypes.data_as(C.POINTER(C.c_float))
+        arr[k].n_verts = v.shape[0]
+        arr[k].quads = q.ctypes.data_as(C.POINTER(C.c_uint32))
+        arr[k].n_quads = q.shape[0]
+    o = native.qrt_build_opts()
+    for k, val in opts.items():
+        setattr(o, k, val)
+    n = C.c_uint64()
+    d = C.c_uint32()
+    rc = L.qrt_blases_build_check(arr, len(meshes), C.byref(o), C.byref(n), C.byref(d))
+    return rc, n.value, d.value, L.qrt_last_error().decode()
+
+
+@pytest.mark.parametrize("leaf", [1, 4, 8])
+def test_linear_blas_invariants_on_host(native, leaf):
+    """The linear-BVH BLAS steps run on the host, one mesh at a time and all
+    meshes in one pass (mesh subtrees of one radix tree): every quad in one
+    slot, every quantised box containing its subtree, any leaf size."""
+    for v, q in _varied_meshes():
+        rc, n, d, msg = _check_mesh(native, v, q, max_leaf=leaf, blas_builder=2)
+        assert rc == 0, msg
+        assert n >= 1 and d >= 1
+    rc, n, d, msg = _check_meshes(native, _varied_meshes(), max_leaf=leaf, blas_builder=2)
+    assert rc == 0, msg
+
+
+def test_linear_blas_many_meshes_on_host(native):
+    """The mid scene's 128 prototype meshes in one pass: each mesh's subtree is
+    found and checked; node counts stay close to the SAH builder's."""
+    sc = I.mid_scene()
+    rc, n, d, msg = _check_meshes(native, sc.meshes, blas_builder=2)
+    assert rc == 0, msg
+    rc0, n0, d0, msg0 = _check_meshes(native, sc.meshes)
+    assert rc0 == 0, msg0
+    assert 0.7 * n0 <= n <= 1.3 * n0
+
+
+def test_linear_blas_rejects_bad_input_on_host(native):
+    v, q = I.plane_mesh(2)
+    bad = q.copy()
+    bad[1, 2] = v.shape[0]
+    assert _check_meshes(native, [(v, q), (v, bad)], blas_builder=2)[0] == native.QRT_ERR_INVALID_ARG
+    vn = v.copy()
+    vn[0, 1] = np.inf
+    assert _check_meshes(native, [(vn, q)], blas_builder=2)[0] == native.QRT_ERR_INVALID_ARG
+    assert _check_meshes(native, [(v, q)], blas_builder=3)[0] == native.QRT_ERR_INVALID_ARG
+    assert _check_mesh(native, v, q[:0], blas_builder=2)[0] == native.QRT_ERR_INVALID_ARG
