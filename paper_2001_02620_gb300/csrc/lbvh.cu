@@ -5,9 +5,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cub/device/device_radix_sort.cuh>
@@ -831,41 +833,67 @@ __global__ void k_collapse_blas(uint32_t n, const MeshDev* md, const uint32_t* c
 
 namespace {
 
+// fn(i) for i in [0, n) on all host cores (items claimed one at a time).
+template <class Fn>
+void parallel_for(size_t n, Fn fn) {
+    const unsigned nt = (unsigned)std::min<size_t>(n, std::max(1u, std::thread::hardware_concurrency()));
+    std::atomic<size_t> next{0};
+    auto work = [&]() {
+        for (size_t i; (i = next.fetch_add(1)) < n;) fn(i);
+    };
+    std::vector<std::thread> th;
+    for (unsigned k = 1; k < nt; ++k) th.emplace_back(work);
+    work();
+    for (auto& t : th) t.join();
+}
+
 // Mesh table: offsets, node regions and each mesh's Morton grid (the box of
 // its referenced vertices, one scale for all axes).  Also checks the input
-// as the host builder does.
+// as the host builder does; meshes are scanned in parallel.
 bool mesh_table(const std::vector<MeshView>& meshes, std::vector<MeshDev>& md, uint64_t& total_q,
                 uint64_t& total_v, std::string& err) {
     md.resize(meshes.size());
     total_q = total_v = 0;
     uint64_t nodes = 0;
-    for (size_t m = 0; m < meshes.size(); ++m) {
+    std::vector<std::string> errs(meshes.size());
+    std::vector<FBox> vbox(meshes.size());
+    parallel_for(meshes.size(), [&](size_t m) {
         const MeshView& mv = meshes[m];
         if (mv.n_quads == 0) {
-            err = "mesh " + std::to_string(m) + ": mesh has no quads";
-            return false;
+            errs[m] = "mesh has no quads";
+            return;
         }
         if (mv.n_quads > kMaxLocalIndex) {
-            err = "mesh " + std::to_string(m) + ": mesh has more than 2^27 quads";
-            return false;
+            errs[m] = "mesh has more than 2^27 quads";
+            return;
         }
-        float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        FBox b{{INFINITY, INFINITY, INFINITY}, {-INFINITY, -INFINITY, -INFINITY}};
         for (uint64_t k = 0; k < 4ull * mv.n_quads; ++k) {
             const uint32_t vi = mv.quads[k];
             if (vi >= mv.n_verts) {
-                err = "mesh " + std::to_string(m) + ": quad vertex index out of range";
-                return false;
+                errs[m] = "quad vertex index out of range";
+                return;
             }
             const float* v = mv.verts + 3 * (size_t)vi;
             for (int a = 0; a < 3; ++a) {
                 if (!std::isfinite(v[a])) {
-                    err = "mesh " + std::to_string(m) + ": non-finite vertex";
-                    return false;
+                    errs[m] = "non-finite vertex";
+                    return;
                 }
-                lo[a] = std::min(lo[a], v[a]);
-                hi[a] = std::max(hi[a], v[a]);
+                b.lo[a] = std::min(b.lo[a], v[a]);
+                b.hi[a] = std::max(b.hi[a], v[a]);
             }
         }
+        vbox[m] = b;
+    });
+    for (size_t m = 0; m < meshes.size(); ++m) {
+        if (!errs[m].empty()) {
+            err = "mesh " + std::to_string(m) + ": " + errs[m];
+            return false;
+        }
+        const MeshView& mv = meshes[m];
+        const float* lo = vbox[m].lo;
+        const float* hi = vbox[m].hi;
         MeshDev& d = md[m];
         d.quad_off = total_q;
         d.vert_off = total_v;
@@ -1182,8 +1210,8 @@ bool blases_on_device(const std::vector<MeshView>& meshes, const std::vector<Mes
         QRT_LBVH_TRY(cudaMemcpy(r.prim.data(), d_prim + d.quad_off, 4 * (size_t)d.n_quads,
                                 cudaMemcpyDeviceToHost));
         r.depth = mesh_depth[m];
-        r.box = quads_box(r.quads);
     }
+    parallel_for(n_mesh, [&](size_t m) { out[m].box = quads_box(out[m].quads); });
     return true;
 }
 
