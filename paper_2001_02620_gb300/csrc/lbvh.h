@@ -1,12 +1,13 @@
-// Linear BVH build of the TLAS (a builder the paper does not have: its BVHs
-// come from Embree on the CPU).  Instance boxes are ordered along a 63-bit
-// Morton curve of their centres, the binary hierarchy over that order is
-// formed node by node in parallel (Karras, "Maximizing Parallelism in the
-// Construction of BVHs, Octrees, and k-d Trees", HPG 2012), node boxes are
-// merged bottom-up, and the binary tree is collapsed top-down to four-wide
-// nodes with conservatively quantised child boxes (qrt_layout.h), the same
-// format the host's binned-SAH builder writes.  Off the hot path: it runs in
-// qrt_scene_create when the caller asks for it.
+// Linear BVH builds of the TLAS and of the BLASes (builders the paper does
+// not have: its BVHs come from Embree on the CPU).  Items (instance boxes, or
+// quads keyed by mesh) are ordered along a Morton curve of their centres, the
+// binary hierarchy over that order is formed node by node in parallel
+// (Karras, "Maximizing Parallelism in the Construction of BVHs, Octrees, and
+// k-d Trees", HPG 2012), node boxes are merged bottom-up, and the binary tree
+// is collapsed top-down to four-wide nodes with conservatively quantised
+// child boxes (qrt_layout.h), the same format the host's binned-SAH builder
+// writes.  Off the hot path: they run in qrt_scene_create when the caller
+// asks for them.
 #pragma once
 #include <string>
 #include <vector>
