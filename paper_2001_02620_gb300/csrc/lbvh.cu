@@ -1,8 +1,8 @@
 // Linear BVH builds of the TLAS and the BLASes on the GPU (declared in
-// lbvh.h).  Every step
-// is a function of one node or one item, written once for host and device:
-// the kernels call them per thread, and the host path runs the same functions
-// in loops, so the index arithmetic is exercised without a GPU.
+// lbvh.h).  Every step is a function of one node or one item, written once
+// for host and device: the kernels call them per thread, and the host path
+// runs the same functions in loops, so the index arithmetic is exercised
+// without a GPU.
 #include <cuda_runtime.h>
 
 #include <algorithm>
