@@ -352,15 +352,19 @@ def run_reference(args):
         return
     sc, view, params, alb = mid_workload()
     per = []
+    secs = []
     base = None
     for k in range(args.warmup + args.steps):
+        t0 = time.time()
         r = oracle_sample(sc, view, params, alb, budget_s=8.0 if k >= args.warmup else 2.0)
         if k >= args.warmup:
+            secs.append(time.time() - t0)
             per.append(r["value"])
             base = r
     v = float(np.median(per))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mrays/s", "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "ms_per_step": 1e3 * float(np.mean(secs)), "scaling": "weak",
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOADS["mid"],
                        "parallelism": f"{base['cores']} host threads (FP64 oracle)"},
@@ -387,6 +391,8 @@ def main():
     ap.add_argument("--workload", default="mid", choices=sorted(WORKLOADS))
     ap.add_argument("--tlas-builder", type=int, default=0, choices=[0, 1],
                     help="TLAS builder: 0 binned SAH on the host, 1 linear BVH on the device")
+    ap.add_argument("--blas-builder", type=int, default=0, choices=[0, 1],
+                    help="BLAS builder: 0 binned SAH on the host, 1 linear BVHs on the device")
     ap.add_argument("--moana-scale", type=float, default=1.0,
                     help="moana workload: fraction of the full counts (1 = 261M quads)")
     args = ap.parse_args()
@@ -420,7 +426,8 @@ def main():
         view.spp = args.spp
     view.pixel_base = rank * view.w * view.h  # each rank renders its own frame
     t0 = time.time()
-    scene = api.Scene(sc, build_opts=dict(tlas_builder=args.tlas_builder) if args.tlas_builder else None)
+    bopts = {k: v for k, v in (("tlas_builder", args.tlas_builder), ("blas_builder", args.blas_builder)) if v}
+    scene = api.Scene(sc, build_opts=bopts or None)
     build_s = time.time() - t0
     dev = torch.device("cuda", local)
     d_alb = torch.from_numpy(alb).to(dev)
@@ -551,6 +558,7 @@ def main():
                    args.moana_scale == 1.0 else WORKLOADS["moana"] + f" x {args.moana_scale}",
                    "parallelism": f"replicas{world}",
                    "tlas_builder": "device linear BVH" if args.tlas_builder else "host binned SAH",
+                   "blas_builder": "device linear BVHs" if args.blas_builder else "host binned SAH",
                    "l2": f"working set {scene.stats['device_bytes'] / 1e9:.2f} GB > L2 (no flush)"},
         "path_samples_per_s": world * paths / (ms * 1e-3),
         "rays_per_step": rays, "paths_per_step": paths,
@@ -611,7 +619,7 @@ def main():
         line["cost_map"] = bench_cost_map(api, scene, view, d_alb, params, dev, tuning)
     if "progressive" in extras:
         line["progressive"] = bench_progressive(api, scene, view, d_alb, params, dev, tuning)
-    if "device_build" in extras and not args.tlas_builder:
+    if "device_build" in extras and not (args.tlas_builder or args.blas_builder):
         line["device_build"] = bench_device_build(api, scene, sc, view, d_alb, params, dev, tuning,
                                                   rays=rays)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
