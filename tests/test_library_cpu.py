@@ -80,6 +80,17 @@ def test_host_side_argument_errors(native):
     rc = L.qrt_scene_create(m, 1, xf.ctypes.data_as(C.POINTER(C.c_float)),
                             ids.ctypes.data_as(C.POINTER(C.c_uint32)), 2, C.byref(o), C.byref(out))
     assert rc == native.QRT_ERR_INVALID_ARG and b"inst_boxes" in L.qrt_last_error()
+    for field, val, word in (("tlas_builder", 3, b"tlas_builder"), ("blas_builder", 3, b"blas_builder")):
+        o = native.qrt_build_opts()
+        setattr(o, field, val)
+        rc = L.qrt_scene_create(m, 1, xf.ctypes.data_as(C.POINTER(C.c_float)),
+                                ids.ctypes.data_as(C.POINTER(C.c_uint32)), 2, C.byref(o), C.byref(out))
+        assert rc == native.QRT_ERR_INVALID_ARG and word in L.qrt_last_error()
+    o = native.qrt_build_opts()
+    o.blas_builder, o.degenerate = 2, 1   # the chain-shaped test BLAS exists only on the host builder
+    rc = L.qrt_scene_create(m, 1, xf.ctypes.data_as(C.POINTER(C.c_float)),
+                            ids.ctypes.data_as(C.POINTER(C.c_uint32)), 2, C.byref(o), C.byref(out))
+    assert rc == native.QRT_ERR_INVALID_ARG and b"degenerate" in L.qrt_last_error()
     # a singular instance transform is found by the host build (no GPU needed)
     xs = xf.copy()
     xs[12:24] = [1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0]
