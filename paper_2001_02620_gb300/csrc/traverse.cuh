@@ -473,8 +473,10 @@ __device__ __forceinline__ void add_stats(unsigned long long* stats, const Trace
 // Resumable two-level traversal of one world ray.  init() sets the ray up;
 // each step() processes the current node, leaf or instance entry and pops the
 // next stack entry, returning false once the ray is finished (or stopped by
-// an error).  Persistent kernels interleave step() with refilling finished
-// lanes, so no lane waits for the slowest ray of its warp.
+// an error); trace_ray runs it to the end.  The persistent kernels instead
+// drive the warp-synchronous phase methods below from persistent_trace and
+// refill finished lanes, so no lane waits for the slowest ray of its warp.
+// The world ray itself is not kept: the callers' world() functors supply it.
 template <bool ANY, int STACK, int FETCH>
 struct Traversal {
     float tmin, tmax;
