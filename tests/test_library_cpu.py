@@ -308,3 +308,49 @@ def test_linear_blas_rejects_bad_input_on_host(native):
     assert _check_meshes(native, [(vn, q)], blas_builder=2)[0] == native.QRT_ERR_INVALID_ARG
     assert _check_meshes(native, [(v, q)], blas_builder=3)[0] == native.QRT_ERR_INVALID_ARG
     assert _check_mesh(native, v, q[:0], blas_builder=2)[0] == native.QRT_ERR_INVALID_ARG
+
+
+def test_linear_tlas_random_layouts_on_host(native):
+    """Random counts, spreads, sizes and clustering (many equal Morton codes):
+    the host-run linear TLAS always passes the invariant check."""
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=60, deadline=None)
+    @hyp.given(n=st.integers(1, 3000), spread=st.floats(1e-3, 1e6), size=st.floats(0.0, 10.0),
+               clusters=st.integers(1, 8), seed=st.integers(0, 2**31 - 1))
+    def run(n, spread, size, clusters, seed):
+        rng = np.random.default_rng(seed)
+        centres = rng.uniform(-spread, spread, size=(clusters, 3))
+        c = centres[rng.integers(0, clusters, size=n)] + rng.normal(0, spread * 1e-3, size=(n, 3))
+        e = rng.uniform(0, size * spread * 1e-3 + 1e-6, size=(n, 3))
+        boxes = np.concatenate([c - e, c + e], axis=1)
+        rc, nodes, depth, msg = _check_tlas(native, boxes, 2)
+        assert rc == 0, msg
+        assert nodes <= max(1, n - 1)
+
+    run()
+
+
+def test_linear_blas_random_meshes_on_host(native):
+    """Random mesh sets (counts, sizes, vertex sharing, coincident quads): the
+    host-run linear BLASes, all meshes in one pass, pass the invariant check."""
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=40, deadline=None)
+    @hyp.given(n_mesh=st.integers(1, 12), max_q=st.integers(1, 600), scale=st.floats(1e-3, 1e5),
+               leaf=st.integers(1, 8), seed=st.integers(0, 2**31 - 1))
+    def run(n_mesh, max_q, scale, leaf, seed):
+        rng = np.random.default_rng(seed)
+        meshes = []
+        for _ in range(n_mesh):
+            nq = int(rng.integers(1, max_q + 1))
+            nv = int(rng.integers(1, 4 * nq + 1))
+            v = (rng.normal(size=(nv, 3)) * scale).astype(np.float32)
+            q = rng.integers(0, nv, size=(nq, 4)).astype(np.uint32)
+            meshes.append((v, q))
+        rc, n, d, msg = _check_meshes(native, meshes, blas_builder=2, max_leaf=leaf)
+        assert rc == 0, msg
+
+    run()
