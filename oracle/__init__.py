@@ -78,7 +78,7 @@ def lib():
             L.ora_render.restype = C.c_int
             L.ora_render.argtypes = [C.c_void_p, C.POINTER(_View), f32p, C.POINTER(_Params),
                                      C.POINTER(C.c_int64), C.c_uint64, f64p, u32p, u32p, u32p,
-                                     u64p, u64p, C.c_int]
+                                     f64p, u64p, u64p, C.c_int]
             L.ora_render_grad.restype = C.c_int
             L.ora_render_grad.argtypes = [C.c_void_p, C.POINTER(_View), f32p, C.POINTER(_Params),
                                           C.POINTER(C.c_int64), C.c_uint64, f64p, f64p, C.c_int]
@@ -194,8 +194,13 @@ class OracleScene:
                             _p(occ, C.c_uint8), nthreads)
         return occ.astype(bool)
 
-    def render(self, view, albedo, params, pixels=None, log: bool = False, nthreads: int = 0):
-        """Returns dict(rgb=[n_pix,3] f64, escaped, truncated[, inst, prim, shadow])."""
+    def render(self, view, albedo, params, pixels=None, log: bool = False, nthreads: int = 0,
+               rays: bool = False):
+        """Returns dict(rgb=[n_pix,3] f64, escaped, truncated[, inst, prim, shadow][, rays]).
+        pixels: frame pixel indices y*w + x (None = the whole frame in order).
+        rays=True adds rays [n_paths, max_depth, 9]: per depth the origin and
+        direction of the closest-hit ray traced there and the origin of the
+        shadow ray traced from its hit (zeros where there was none)."""
         a = np.ascontiguousarray(albedo, dtype=np.float32).reshape(-1, 3)
         assert a.shape[0] == self.n_quads
         if pixels is None:
@@ -207,7 +212,9 @@ class OracleScene:
         rgb = np.zeros((n_pix, 3))
         D = int(params.max_depth)
         n_paths = n_pix * int(view.spp)
-        li = lp = ls = None
+        li = lp = ls = lr = None
+        if rays:
+            lr = np.zeros((n_paths, D, 9))
         if log:
             li = np.zeros((n_paths, D), dtype=np.uint32)
             lp = np.zeros((n_paths, D), dtype=np.uint32)
@@ -218,12 +225,14 @@ class OracleScene:
         rc = lib().ora_render(self._h, C.byref(cv), _p(a, C.c_float), C.byref(cp),
                               _p(px, C.c_int64), n_pix, _p(rgb, C.c_double),
                               _p(li, C.c_uint32), _p(lp, C.c_uint32), _p(ls, C.c_uint32),
-                              C.byref(esc), C.byref(tr), nthreads)
+                              _p(lr, C.c_double), C.byref(esc), C.byref(tr), nthreads)
         if rc != 0:
             raise ValueError(f"ora_render failed ({rc})")
         out = dict(rgb=rgb, escaped=esc.value, truncated=tr.value)
         if log:
             out.update(inst=li, prim=lp, shadow=ls)
+        if rays:
+            out["rays"] = lr
         return out
 
     def grad(self, view, albedo, params, dimage, pixels=None, nthreads: int = 0):

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <map>
 #include <thread>
 #include <vector>
 
@@ -175,44 +176,69 @@ struct Bvh {
     std::vector<uint32_t> items;  // item ids in leaf order
 };
 
-void build_rec(Bvh& bvh, const std::vector<Box>& boxes, std::vector<uint32_t>& ids, int lo, int hi,
-               int node) {
+// Nodes of the tree over m items: a node over m > 4 items splits them
+// m/2 : m - m/2, so the subtree sizes on one level take at most two values.
+uint64_t tree_nodes(uint64_t m) {
+    std::map<uint64_t, uint64_t> level{{m, 1}};
+    uint64_t nodes = 0;
+    while (!level.empty()) {
+        std::map<uint64_t, uint64_t> next;
+        for (const auto& sc : level) {
+            nodes += sc.second;
+            if (sc.first > 4) {
+                next[sc.first / 2] += sc.second;
+                next[sc.first - sc.first / 2] += sc.second;
+            }
+        }
+        level.swap(next);
+    }
+    return nodes;
+}
+
+// Builds the subtree over ids[lo, hi) into bvh.nodes[node ...] in preorder
+// (left subtree first): its size is known in advance, so the two halves of a
+// large node are built on two threads without changing the tree.
+void build_rec(Bvh& bvh, const std::vector<Box>& boxes, std::vector<uint32_t>& ids, int64_t lo,
+               int64_t hi, uint64_t node, int fork_levels) {
     Box b = empty_box(), cb = empty_box();
-    for (int i = lo; i < hi; ++i) {
+    for (int64_t i = lo; i < hi; ++i) {
         grow(b, boxes[ids[i]]);
         grow(cb, 0.5 * (boxes[ids[i]].lo + boxes[ids[i]].hi));
     }
     bvh.nodes[node].box = padded(b);
     if (hi - lo <= 4) {
-        bvh.nodes[node].first = lo;
-        bvh.nodes[node].count = hi - lo;
+        bvh.nodes[node].first = (int)lo;
+        bvh.nodes[node].count = (int)(hi - lo);
         return;
     }
     V3 ext = cb.hi - cb.lo;
     int axis = (ext.x >= ext.y && ext.x >= ext.z) ? 0 : (ext.y >= ext.z ? 1 : 2);
-    int mid = (lo + hi) / 2;
+    int64_t mid = (lo + hi) / 2;
     std::nth_element(ids.begin() + lo, ids.begin() + mid, ids.begin() + hi,
                      [&](uint32_t a, uint32_t c) {
                          double ca = comp(boxes[a].lo, axis) + comp(boxes[a].hi, axis);
                          double cc = comp(boxes[c].lo, axis) + comp(boxes[c].hi, axis);
                          return ca < cc || (ca == cc && a < c);
                      });
-    int l = (int)bvh.nodes.size();
-    bvh.nodes.emplace_back();
-    bvh.nodes.emplace_back();
-    bvh.nodes[node].left = l;
-    bvh.nodes[node].right = l + 1;
-    build_rec(bvh, boxes, ids, lo, mid, l);
-    build_rec(bvh, boxes, ids, mid, hi, l + 1);
+    const uint64_t l = node + 1, r = node + 1 + tree_nodes((uint64_t)(mid - lo));
+    bvh.nodes[node].left = (int)l;
+    bvh.nodes[node].right = (int)r;
+    if (fork_levels > 0 && hi - lo >= (1 << 16)) {
+        std::thread t([&] { build_rec(bvh, boxes, ids, lo, mid, l, fork_levels - 1); });
+        build_rec(bvh, boxes, ids, mid, hi, r, fork_levels - 1);
+        t.join();
+    } else {
+        build_rec(bvh, boxes, ids, lo, mid, l, 0);
+        build_rec(bvh, boxes, ids, mid, hi, r, 0);
+    }
 }
 
 Bvh build_bvh(const std::vector<Box>& boxes) {
     Bvh bvh;
     std::vector<uint32_t> ids(boxes.size());
     for (size_t i = 0; i < ids.size(); ++i) ids[i] = (uint32_t)i;
-    bvh.nodes.reserve(2 * boxes.size() + 1);
-    bvh.nodes.emplace_back();
-    if (!boxes.empty()) build_rec(bvh, boxes, ids, 0, (int)boxes.size(), 0);
+    bvh.nodes.resize(boxes.empty() ? 1 : tree_nodes(boxes.size()));
+    if (!boxes.empty()) build_rec(bvh, boxes, ids, 0, (int64_t)boxes.size(), 0, 4);
     bvh.items = ids;
     return bvh;
 }
@@ -524,7 +550,8 @@ struct PathRecord {
 // (with the given albedo) and its record.
 void trace_path(const ora_scene& s, const ora_view& view, const float* albedo,
                 const ora_params& p, uint32_t x, uint32_t y, uint32_t k, double L[3],
-                PathRecord* rec, uint32_t* log_inst, uint32_t* log_prim, uint32_t* log_shadow) {
+                PathRecord* rec, uint32_t* log_inst, uint32_t* log_prim, uint32_t* log_shadow,
+                double* log_rays) {
     const uint64_t pix = view.pixel_base + (uint64_t)y * view.w + x;
     const uint32_t smp = view.sample_base + k;  // Philox counter: (pixel, sample, bounce)
     double xi[4];
@@ -541,6 +568,11 @@ void trace_path(const ora_scene& s, const ora_view& view, const float* albedo,
         rec->escaped = false;
     }
     for (uint32_t i = 1; i <= p.max_depth; ++i) {
+        if (log_rays) {
+            // the ray traced at depth i: origin, direction (shadow origin below)
+            double* r = log_rays + 9 * (i - 1);
+            r[0] = o.x, r[1] = o.y, r[2] = o.z, r[3] = d.x, r[4] = d.y, r[5] = d.z;
+        }
         HitRec h = closest(s, o, d, 0.0, kInf, 0);
         if (log_inst) {
             log_inst[i - 1] = h.inst;
@@ -563,6 +595,10 @@ void trace_path(const ora_scene& s, const ora_view& view, const float* albedo,
             double cl = dot(n, l);
             if (cl > 0.0) {
                 if (i <= 16) shadow_bits |= 1u << (2 * (i - 1));
+                if (log_rays) {
+                    double* r = log_rays + 9 * (i - 1) + 6;
+                    r[0] = sp.x, r[1] = sp.y, r[2] = sp.z;
+                }
                 bool occ = any_hit(s, sp, l, 0.0, kInf, 0);
                 if (occ) {
                     if (i <= 16) shadow_bits |= 2u << (2 * (i - 1));
@@ -629,7 +665,7 @@ ora_scene* ora_scene_new(uint32_t n_mesh, const float* const* verts, const uint3
     });
     s->inst.resize(n_inst);
     std::vector<Box> wboxes(n_inst);
-    for (uint64_t i = 0; i < n_inst; ++i) {
+    parallel_for(n_inst, 0, [&](uint64_t i) {
         Instance& I = s->inst[i];
         const float* x = xforms + 12 * i;
         for (int r = 0; r < 3; ++r) {
@@ -647,7 +683,7 @@ ora_scene* ora_scene_new(uint32_t n_mesh, const float* const* verts, const uint3
         }
         I.world_box = padded(wb);
         wboxes[i] = I.world_box;
-    }
+    });
     s->tlas = build_bvh(wboxes);
     return s;
 }
@@ -706,7 +742,7 @@ void ora_sample_cosine(const double n[3], double xi1, double xi2, double out[3])
 
 int ora_render(const ora_scene* s, const ora_view* view, const float* albedo,
                const ora_params* p, const int64_t* pixels, uint64_t n_pix, double* rgb,
-               uint32_t* log_inst, uint32_t* log_prim, uint32_t* log_shadow,
+               uint32_t* log_inst, uint32_t* log_prim, uint32_t* log_shadow, double* log_rays,
                uint64_t* n_escaped, uint64_t* n_truncated, int nthreads) {
     if (p->max_depth == 0 || p->max_depth > 256) return -1;
     std::atomic<uint64_t> esc{0}, trunc{0};
@@ -722,7 +758,8 @@ int ora_render(const ora_scene* s, const ora_view* view, const float* albedo,
             trace_path(*s, *view, albedo, *p, x, y, smp, L, &rec,
                        log_inst ? log_inst + path * D : nullptr,
                        log_prim ? log_prim + path * D : nullptr,
-                       log_shadow ? log_shadow + path : nullptr);
+                       log_shadow ? log_shadow + path : nullptr,
+                       log_rays ? log_rays + path * D * 9 : nullptr);
             if (log_inst) {
                 for (uint32_t i = (uint32_t)rec.verts.size() + (rec.escaped ? 1 : 0); i < D; ++i) {
                     log_inst[path * D + i] = kNone;
@@ -762,7 +799,7 @@ int ora_render_grad(const ora_scene* s, const ora_view* view, const float* albed
         std::vector<Entry>& out = parts[k];
         for (uint32_t smp = 0; smp < spp; ++smp) {
             double L[3];
-            trace_path(*s, *view, albedo, *p, x, y, smp, L, &rec, nullptr, nullptr, nullptr);
+            trace_path(*s, *view, albedo, *p, x, y, smp, L, &rec, nullptr, nullptr, nullptr, nullptr);
             const size_t m = rec.verts.size();
             for (int c = 0; c < 3; ++c) {
                 double w = dimage[3 * k + c] / (double)spp;

@@ -96,12 +96,17 @@ void ora_sample_cosine(const double n[3], double xi1, double xi2, double out[3])
  * non-NULL they receive, per path (pixel-major, then sample), max_depth
  * entries of the hit instance / quad (0xFFFFFFFF = no hit); log_shadow gets
  * per path 2 bits per vertex for the first 16 vertices: bit 2i = shadow ray
- * traced at vertex i, bit 2i+1 = it was occluded.  max_depth is 1..256.  n_escaped/n_truncated (nullable) count paths
- * that left the scene / ran out of depth on a surface. */
+ * traced at vertex i, bit 2i+1 = it was occluded.  max_depth is 1..256.
+ * log_rays (nullable, zeroed by the caller) receives per path max_depth
+ * records of 9 doubles: origin and direction of the closest-hit ray traced
+ * at that depth, then the origin of the shadow ray traced from its hit
+ * (records of rays not traced stay as given).  n_escaped/n_truncated
+ * (nullable) count paths that left the scene / ran out of depth on a
+ * surface. */
 int ora_render(const ora_scene* s, const ora_view* view, const float* albedo,
                const ora_params* p, const int64_t* pixels, uint64_t n_pix,
                double* rgb, uint32_t* log_inst, uint32_t* log_prim, uint32_t* log_shadow,
-               uint64_t* n_escaped, uint64_t* n_truncated, int nthreads);
+               double* log_rays, uint64_t* n_escaped, uint64_t* n_truncated, int nthreads);
 
 /* Gradient of sum_p sum_c dimage[p,c] * I[p,c] with respect to the per-quad
  * albedo (n_quads x 3), accumulated into grad (doubles, zeroed by caller),

@@ -424,6 +424,57 @@ def test_render_pixel_subset_matches_full_image():
     np.testing.assert_array_equal(sub, full[px])
 
 
+def test_ray_log_follows_the_paths():
+    """The oracle's ray log (used to explain divergent GPU paths) records the
+    rays its paths trace: depth 1 is the camera ray from the eye; each
+    logged hit lies on its logged ray (the quad's FP64 intersection); the
+    next ray starts at the spawn point of that hit, p + (1e-4 + 1e-5 max|p|) n
+    with n the quad's world normal faced against the ray, which is also the
+    origin of the hit's shadow ray; rays not traced are left zero."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from parity import NONE, world_normal, world_quad
+    sc = I.tiny_scene()
+    osc = O.OracleScene(sc)
+    view = I.tiny_view()
+    view.w, view.h, view.spp = 40, 30, 2
+    p = I.Params(max_depth=4, sun_dir=I.MID_SUN_DIR, sun_E=(3.0, 3.0, 3.0))
+    r = osc.render(view, I.albedo(sc.n_quads), p, log=True, rays=True)
+    R = r["rays"]
+    assert R.shape == (40 * 30 * 2, 4, 9)
+    np.testing.assert_array_equal(R[:, 0, 0:3], np.broadcast_to(np.array(view.eye, float), (2400, 3)))
+    np.testing.assert_allclose(np.linalg.norm(R[:, 0, 3:6], axis=1), 1.0, rtol=1e-14)
+    l = np.array(I.MID_SUN_DIR, float) / np.linalg.norm(I.MID_SUN_DIR)
+    checked = shadows = 0
+    for k in range(2400):
+        for i in range(4):
+            inst, prim = r["inst"][k, i], r["prim"][k, i]
+            if inst == NONE:
+                assert (R[k, i + 1:] == 0).all()
+                break
+            o, d = R[k, i, 0:3], R[k, i, 3:6]
+            hit, t, _, _ = O.intersect_quad(o, d, world_quad(sc, inst, prim))
+            assert hit and t > 0
+            n = world_normal(sc, inst, prim)
+            if n @ d > 0:
+                n = -n
+            hp = o + t * d
+            sp = hp + (1e-4 + 1e-5 * np.abs(hp).max()) * n
+            traced = (r["shadow"][k] >> (2 * i)) & 1
+            if traced:
+                np.testing.assert_allclose(R[k, i, 6:9], sp, rtol=1e-12, atol=1e-12)
+                assert n @ l > 0
+                shadows += 1
+            else:
+                assert (R[k, i, 6:9] == 0).all()
+            if i + 1 < 4:
+                np.testing.assert_allclose(R[k, i + 1, 0:3], sp, rtol=1e-12, atol=1e-12)
+                np.testing.assert_allclose(np.linalg.norm(R[k, i + 1, 3:6]), 1.0, rtol=1e-12)
+                assert R[k, i + 1, 3:6] @ n > 0  # leaves on the faced side
+            checked += 1
+    assert checked > 200 and shadows > 20
+
+
 def test_progressive_samples_compose_to_one_render():
     """Section 5.4 renders one sample per pixel per frame.  A view's samples
     are drawn at sample_base + k: the mean of frames with spp = 1 and
