@@ -95,9 +95,17 @@ typedef struct {
  * distinct views should use disjoint ranges.  The call draws samples
  * sample_base .. sample_base + spp - 1 of every pixel: progressive rendering
  * (Section 5.4, one sample per pixel per frame) passes the frame number with
- * spp = 1 and sums the frames with qrt_accumulate.  out_rgb: DEVICE float
- * [h*w*3], row-major, receives the mean radiance over the call's spp samples
- * (overwritten). */
+ * spp = 1 and sums the frames with qrt_accumulate.
+ * Crop: crop_w = crop_h = 0 renders the whole w x h frame; otherwise only
+ * the rectangle [crop_x, crop_x + crop_w) x [crop_y, crop_y + crop_h) of the
+ * frame (it must lie inside it), with the camera and the random streams of
+ * the whole frame, so a crop's pixels are bit-identical to the same pixels
+ * of a whole-frame render.  This is how an image-parallel renderer hands a
+ * rank its tiles (Section 5.5, "The Distributed FrameBuffer": image tiles
+ * assigned to nodes that each hold the whole scene).
+ * out_rgb: DEVICE float [rh*rw*3], row-major over the rendered region (rw x
+ * rh = crop_w x crop_h, or w x h), receives the mean radiance over the
+ * call's spp samples (overwritten). */
 typedef struct {
     float eye[3];
     float look[3];
@@ -107,6 +115,7 @@ typedef struct {
     uint32_t sample_base;
     uint64_t pixel_base;
     float* out_rgb;
+    uint32_t crop_x, crop_y, crop_w, crop_h;
 } qrt_view;
 
 /* Launch tuning; 0 in any field selects the library default.
@@ -156,11 +165,22 @@ typedef struct {
  *               path had no such ray, then one word of shadow bits (bit 2i: a
  *               shadow ray was traced at vertex i, bit 2i+1: it was occluded;
  *               first 16 vertices).  Path p of view v sits at
- *               sum_{u<v}(w*h*spp)_u + (y*w + x)*spp + sample, each path taking
+ *               sum_{u<v}(rw*rh*spp)_u + (y'*rw + x')*spp + sample, (x', y')
+ *               the pixel within the view's rendered region, each path taking
  *               2*max_depth + 1 words.
  *   max_steps   traversal step limit per ray (0 = 2^20); exceeding it stops
  *               that ray and raises QRT_ERR_STEP_LIMIT.
- *   tuning      launch tuning (zeros = defaults). */
+ *   tuning      launch tuning (zeros = defaults).
+ *   d_ray_log   optional DEVICE float buffer for diagnostics (NULL = off),
+ *               16-byte aligned, indexed by path like d_path_log: per path
+ *               max_depth records of 12 floats, one per depth i = 1..max_depth:
+ *               the closest-hit ray traced at depth i as a qrt_ray (o, tmin,
+ *               d, tmax; the camera ray at depth 1, then each bounce ray as
+ *               spawned), then the origin of the shadow ray traced from the hit
+ *               of depth i (3 floats; its direction is the sun's) and one
+ *               unused float.  Records of rays a path did not trace are zero.
+ *               The exact FP32 rays let a test re-trace, in FP64, the ray on
+ *               which a path first left the oracle's path. */
 typedef struct {
     uint32_t max_depth;
     uint32_t flags;
@@ -171,6 +191,7 @@ typedef struct {
     uint32_t max_steps;
     uint32_t* d_path_log;
     qrt_tuning tuning;
+    float* d_ray_log;
 } qrt_params;
 
 /* BVH build options (NULL = defaults).
@@ -258,20 +279,24 @@ int qrt_render_spp(qrt_scene scene, const qrt_view* views, uint32_t n_views,
                    const float* d_albedo, const qrt_params* params, qrt_stream stream);
 
 /* qrt_render_spp for callers that cannot allocate device memory -- for
- * example code that runs while a stream is being captured into a CUDA graph,
- * an interactive frame loop that must not stall on cudaMalloc, or a process
- * whose device memory is owned by another allocator.  No paper counterpart:
- * it is an interface variant of this library, with the same results as
- * qrt_render_spp.
+ * example an interactive frame loop that must not stall on cudaMalloc, or a
+ * process whose device memory is owned by another allocator (a framework's
+ * caching pool, a host application that budgets every byte).  No paper
+ * counterpart: it is an interface variant of this library, with the same
+ * results as qrt_render_spp.
  *
  * It renders with the wavefront renderer, using as scratch a fixed array of
  * about 17 MB compiled into the library (device global memory held on every
  * GPU that loads the library, until the process exits), enough for chunks of
- * 2^17 paths; any number of views and paths is processed chunk by chunk.
- * The call allocates nothing and calls no cudaMalloc or cudaFree.  The first
- * call on a device looks up the array's device address (once per device;
- * make that first call before any stream capture).  tuning.chunk_log2 may be
- * 0 (= 17) or at most 17, and tuning.mode 0 or 2; anything else is rejected
+ * 2^17 paths; any number of views and paths is processed chunk by chunk, so
+ * a view's spp may be at most 2^17 (larger is rejected with
+ * QRT_ERR_INVALID_ARG).  The call allocates nothing and calls no cudaMalloc
+ * or cudaFree.  The first call on a device -- and the first after that
+ * device's context is made anew, e.g. after cudaDeviceReset -- looks up the
+ * array's device address; make that first call before any stream capture.
+ * Tuning is read as for qrt_render_spp (zeros = library defaults), except
+ * that the renderer is always the wavefront one: tuning.mode may be 0 or 2,
+ * and tuning.chunk_log2 0 (= 17) or at most 17; anything else is rejected
  * with QRT_ERR_INVALID_ARG.  Every call shares the one array and clears what
  * must start at zero itself, so calls that overlap on the GPU (different
  * streams, or different host threads) race with each other: order them on

@@ -41,7 +41,8 @@ class qrt_view(C.Structure):
     _fields_ = [("eye", C.c_float * 3), ("look", C.c_float * 3), ("up", C.c_float * 3),
                 ("vfov_deg", C.c_float), ("w", C.c_uint32), ("h", C.c_uint32),
                 ("spp", C.c_uint32), ("sample_base", C.c_uint32), ("pixel_base", C.c_uint64),
-                ("out_rgb", C.c_void_p)]
+                ("out_rgb", C.c_void_p), ("crop_x", C.c_uint32), ("crop_y", C.c_uint32),
+                ("crop_w", C.c_uint32), ("crop_h", C.c_uint32)]
 
 
 class qrt_tuning(C.Structure):
@@ -53,7 +54,8 @@ class qrt_tuning(C.Structure):
 class qrt_params(C.Structure):
     _fields_ = [("max_depth", C.c_uint32), ("flags", C.c_uint32), ("seed", C.c_uint64),
                 ("env", C.c_float * 3), ("sun_dir", C.c_float * 3), ("sun_E", C.c_float * 3),
-                ("max_steps", C.c_uint32), ("d_path_log", C.c_void_p), ("tuning", qrt_tuning)]
+                ("max_steps", C.c_uint32), ("d_path_log", C.c_void_p), ("tuning", qrt_tuning),
+                ("d_ray_log", C.c_void_p)]
 
 
 class qrt_build_opts(C.Structure):

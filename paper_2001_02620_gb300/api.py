@@ -29,7 +29,8 @@ def make_tuning(tuning: dict | None) -> N.qrt_tuning:
 
 
 def make_params(p: Params, tuning: dict | None = None, path_log: torch.Tensor | None = None,
-                max_steps: int = 0, stage_times: bool = False) -> N.qrt_params:
+                max_steps: int = 0, stage_times: bool = False,
+                ray_log: torch.Tensor | None = None) -> N.qrt_params:
     cp = N.qrt_params()
     cp.max_depth = int(p.max_depth)
     cp.flags = N.QRT_FLAG_STAGE_TIMES if stage_times else 0
@@ -39,6 +40,7 @@ def make_params(p: Params, tuning: dict | None = None, path_log: torch.Tensor | 
     cp.sun_E[:] = [float(x) for x in p.sun_E]
     cp.max_steps = int(max_steps)
     cp.d_path_log = _ptr(path_log)
+    cp.d_ray_log = _ptr(ray_log)
     cp.tuning = make_tuning(tuning)
     return cp
 
@@ -55,11 +57,30 @@ def make_views(views, outs) -> C.Array:
         cv.pixel_base = int(v.pixel_base)
         cv.sample_base = int(getattr(v, "sample_base", 0))
         cv.out_rgb = _ptr(o)
+        cv.crop_x, cv.crop_y = int(getattr(v, "crop_x", 0)), int(getattr(v, "crop_y", 0))
+        cv.crop_w, cv.crop_h = int(getattr(v, "crop_w", 0)), int(getattr(v, "crop_h", 0))
     return arr
 
 
+def region(v) -> tuple:
+    """(width, height) of the pixels a view renders: its crop, or the frame."""
+    cw, ch = int(getattr(v, "crop_w", 0)), int(getattr(v, "crop_h", 0))
+    return (int(v.w), int(v.h)) if cw == 0 and ch == 0 else (cw, ch)
+
+
+def n_paths(views) -> int:
+    return sum(region(v)[0] * region(v)[1] * int(v.spp) for v in views)
+
+
 def path_log_words(views, max_depth: int) -> int:
-    return sum(int(v.w) * int(v.h) * int(v.spp) for v in views) * (2 * int(max_depth) + 1)
+    return n_paths(views) * (2 * int(max_depth) + 1)
+
+
+RAY_LOG_FLOATS = 12  # per path and depth: closest-hit ray (8), shadow-ray origin (3), unused (1)
+
+
+def ray_log_floats(views, max_depth: int) -> int:
+    return n_paths(views) * int(max_depth) * RAY_LOG_FLOATS
 
 
 class Scene:
@@ -142,15 +163,16 @@ class Scene:
     def render(self, views, albedo: torch.Tensor, params: Params, outs=None,
                tuning: dict | None = None, path_log: torch.Tensor | None = None,
                max_steps: int = 0, stats: torch.Tensor | None = None, stream=None,
-               stage_times: bool = False):
-        """Renders views (list of inputs.View) into float32 [h, w, 3] tensors."""
+               stage_times: bool = False, ray_log: torch.Tensor | None = None):
+        """Renders views (list of inputs.View) into float32 [rh, rw, 3] tensors
+        (rw x rh: the view's crop, or its whole frame)."""
         if isinstance(views, View):
             views = [views]
         if outs is None:
-            outs = [torch.empty((v.h, v.w, 3), dtype=torch.float32, device=albedo.device)
-                    for v in views]
+            outs = [torch.empty((region(v)[1], region(v)[0], 3), dtype=torch.float32,
+                                device=albedo.device) for v in views]
         cv = make_views(views, outs)
-        cp = make_params(params, tuning, path_log, max_steps, stage_times)
+        cp = make_params(params, tuning, path_log, max_steps, stage_times, ray_log)
         L = N.lib()
         if stats is None:
             N.check(L.qrt_render_spp(self.handle, cv, len(views), _ptr(albedo), C.byref(cp),
@@ -168,9 +190,10 @@ class Scene:
         if isinstance(views, View):
             views = [views]
         if outs is None:
-            outs = [torch.empty((v.h, v.w, 3), dtype=torch.float32, device=albedo.device)
-                    for v in views]
-        costs = [torch.empty((v.h, v.w), dtype=torch.float32, device=albedo.device) for v in views]
+            outs = [torch.empty((region(v)[1], region(v)[0], 3), dtype=torch.float32,
+                                device=albedo.device) for v in views]
+        costs = [torch.empty((region(v)[1], region(v)[0]), dtype=torch.float32, device=albedo.device)
+                 for v in views]
         cv = make_views(views, outs)
         cp = make_params(params, tuning)
         cptr = (C.c_void_p * len(views))(*[_ptr(c) for c in costs])
@@ -210,8 +233,8 @@ class RenderGraph:
         if isinstance(views, View):
             views = [views]
         if outs is None:
-            outs = [torch.empty((v.h, v.w, 3), dtype=torch.float32, device=albedo.device)
-                    for v in views]
+            outs = [torch.empty((region(v)[1], region(v)[0], 3), dtype=torch.float32,
+                                device=albedo.device) for v in views]
         self.outs = outs
         self._keep = (scene, albedo)
         cv = make_views(views, outs)

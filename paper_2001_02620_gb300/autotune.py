@@ -1,18 +1,27 @@
 """Autotuner for the launch parameters of the renderer.
 
-Searches node-fetch width, block size and the trace kernels' register
-budget (resident warps per SM) by timing renders of a proxy view (the
-target view at reduced resolution, same spp and depth) and keeps the
-fastest configuration that raised no device error.  The stack's depth is
-not searched: a depth that suffices on the proxy can overflow on another
-view.  Its place is not searched either: the per-thread stack in local
-memory (cached in L1) beat a stack whose bottom 4-16 entries sit in shared
-memory in every measured configuration, and the shared-memory branch cost
-9 % even when switched off.  Rays claimed per fetch (`batch`) is left at 1:
-a batch of 2 measured 17 % slower on the mid render.  Results are cached as
-JSON keyed by (GPU name, SM count, scene class), so later runs skip the
-search.  None of the parameters changes a rendered value: images are
-bit-identical under every candidate.
+Searches node-fetch width, block size, the trace kernels' register budget
+(resident warps per SM), the rays a lane claims per fetch (`batch`) and the
+traversal stack depth, by timing renders of a proxy view (the target view at
+reduced resolution, same spp and depth), and keeps the fastest
+configuration that raised no device error.
+
+The stack depth is searched only among depths that provably suffice for the
+scene: a four-wide node pushes at most three entries before the traversal
+descends, and a ray's stack holds the pending entries of the nodes on one
+root-to-leaf path through the TLAS and one BLAS, so 3 * (TLAS depth + deepest
+BLAS depth) entries always suffice (depths in wide-node levels, from
+qrt_scene_stats).  A depth that merely sufficed on the proxy view could
+overflow on another view, and an overflow changes results.  Where no
+candidate below the library's 64 entries is proven, 64 is kept (overflows
+there are still detected and reported by qrt_check).  The stack's place is
+not searched: the per-thread stack in local memory (cached in L1) beat a
+stack whose bottom 4-16 entries sit in shared memory in every measured
+configuration, and the shared-memory branch cost 9 % even when switched off.
+
+Results are cached as JSON keyed by (GPU name, SM count, scene class), so
+later runs skip the search.  None of the parameters changes a rendered
+value: images are bit-identical under every candidate.
 """
 from __future__ import annotations
 
@@ -25,13 +34,22 @@ import time
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                              "autotune_cache", "qrt_tuning.json")
 
-# The stack depth is not searched: a shallower stack that suffices on the
-# proxy view can overflow on another view, and an overflow changes results.
 SPACE = {
     "block": [64, 128, 256],
     "fetch": [16, 32],
     "occupancy": [16, 24, 32],
+    "batch": [1, 2, 4, 8],
 }
+STACK_DEPTHS = (32, 64)   # the library's choices; 64 is its maximum
+
+
+def proven_stack_depths(tlas_depth: int, max_blas_depth: int) -> list[int]:
+    """Stack depths that cannot overflow on a scene with these BVH depths
+    (at most three pending entries per wide-node level of one TLAS path and
+    one BLAS path); the library maximum when none is proven."""
+    need = 3 * (int(tlas_depth) + int(max_blas_depth))
+    ok = [d for d in STACK_DEPTHS if d >= need]
+    return ok or [max(STACK_DEPTHS)]
 
 
 def candidates(space: dict | None = None) -> list[dict]:
@@ -107,6 +125,9 @@ def tune(scene, view, albedo, params, space: dict | None = None, reps: int = 3,
     pv = proxy_view(view)
     out = torch.empty((pv.h, pv.w, 3), device=albedo.device)
     timings = {}
+    space = dict(space or SPACE)
+    if "stack" not in space:
+        space["stack"] = proven_stack_depths(scene.stats["tlas_depth"], scene.stats["max_blas_depth"])
     for cand in candidates(space):
         ck = json.dumps(cand, sort_keys=True)
         try:

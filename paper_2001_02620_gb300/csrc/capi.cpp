@@ -232,10 +232,16 @@ Tune resolve_tuning(const qrt_tuning* t) {
 // (adjoint included) per stream, 2 % of GB300's memory.
 constexpr int kFitChunkMax = 25;
 
+// Pixels a view renders: its crop rectangle, or the whole frame.
+uint64_t region_pixels(const qrt_view& v) {
+    if (v.crop_w == 0 && v.crop_h == 0) return (uint64_t)v.w * v.h;
+    return (uint64_t)v.crop_w * v.crop_h;
+}
+
 void fit_chunk(Tune& t, const qrt_view* views, uint32_t n_views) {
     if (t.chunk_log2 != 0) return;
     uint64_t paths = 0;
-    for (uint32_t v = 0; v < n_views; ++v) paths += (uint64_t)views[v].w * views[v].h * views[v].spp;
+    for (uint32_t v = 0; v < n_views; ++v) paths += region_pixels(views[v]) * views[v].spp;
     int k = 10;
     while (k < kFitChunkMax && (1ull << k) < paths) ++k;
     t.chunk_log2 = k;
@@ -702,6 +708,14 @@ int make_views(const qrt_view* views, uint32_t first, uint32_t count, const floa
             return QRT_ERR_INVALID_ARG;
         }
         if (v.out_rgb && !aligned(v.out_rgb, 4)) return fail(QRT_ERR_ALIGN, "out_rgb must be 4-byte aligned");
+        const bool crop = v.crop_w != 0 || v.crop_h != 0;
+        if (crop && (v.crop_w == 0 || v.crop_h == 0 || (uint64_t)v.crop_x + v.crop_w > v.w ||
+                     (uint64_t)v.crop_y + v.crop_h > v.h)) {
+            std::snprintf(g_err, sizeof(g_err),
+                          "view %u: crop %ux%u at (%u, %u) is empty or leaves the %ux%u frame",
+                          first + k, v.crop_w, v.crop_h, v.crop_x, v.crop_y, v.w, v.h);
+            return QRT_ERR_INVALID_ARG;
+        }
         double eye[3] = {v.eye[0], v.eye[1], v.eye[2]};
         double f[3] = {v.look[0] - eye[0], v.look[1] - eye[1], v.look[2] - eye[2]};
         double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
@@ -728,8 +742,11 @@ int make_views(const qrt_view* views, uint32_t first, uint32_t count, const floa
         d.sxs = (float)(2.0 * th * aspect / v.w);
         d.sy0 = (float)th;
         d.sys = (float)(-2.0 * th / v.h);
-        d.w = v.w;
-        d.h = v.h;
+        d.w = crop ? v.crop_w : v.w;
+        d.h = crop ? v.crop_h : v.h;
+        d.x0 = crop ? v.crop_x : 0;
+        d.y0 = crop ? v.crop_y : 0;
+        d.fw = v.w;
         d.spp = v.spp;
         d.sample_base = v.sample_base;
         d.pixel_base = v.pixel_base;
@@ -742,8 +759,8 @@ int make_views(const qrt_view* views, uint32_t first, uint32_t count, const floa
             std::snprintf(g_err, sizeof(g_err), "d_dimage[%u] is NULL", first + k);
             return QRT_ERR_INVALID_ARG;
         }
-        items += (uint64_t)v.w * v.h;
-        paths += (uint64_t)v.w * v.h * v.spp;
+        items += (uint64_t)d.w * d.h;
+        paths += (uint64_t)d.w * d.h * v.spp;
     }
     A.n_items = items;
     A.n_views = count;
@@ -768,6 +785,8 @@ int make_params(const qrt_params* p, ParamsDev& P) {
     for (int c = 0; c < 3; ++c) P.sun_l[c] = sl > 0.0 ? (float)(p->sun_dir[c] / sl) : 0.f;
     P.path_log = p->d_path_log;
     if (P.path_log && !aligned(P.path_log, 4)) return fail(QRT_ERR_ALIGN, "d_path_log must be 4-byte aligned");
+    P.ray_log = p->d_ray_log;
+    if (P.ray_log && !aligned(P.ray_log, 16)) return fail(QRT_ERR_ALIGN, "d_ray_log must be 16-byte aligned");
     return QRT_OK;
 }
 
@@ -807,6 +826,15 @@ int wave_enqueue(qrt_scene scene, const qrt_view* views, uint32_t n_views, const
     const uint64_t cap = 1ull << t.chunk_log2;
     if (wave_workspace_bytes(cap, adjoint) > ws_bytes)
         return fail(QRT_ERR_INVALID_ARG, "wavefront workspace too small for chunk_log2");
+    // a chunk is cut at pixel boundaries, so it must hold all of a pixel's samples
+    for (uint32_t v = 0; v < n_views; ++v)
+        if ((uint64_t)views[v].spp > cap) {
+            std::snprintf(g_err, sizeof(g_err),
+                          "view %u: spp %u exceeds the %llu paths of a wavefront chunk "
+                          "(tuning.chunk_log2 %d; qrt_render_spp_static allows at most 2^%d)",
+                          v, views[v].spp, (unsigned long long)cap, t.chunk_log2, kStaticChunkLog2);
+            return QRT_ERR_INVALID_ARG;
+        }
     std::memset(&W, 0, sizeof(WaveArgs));
     std::memset(&R, 0, sizeof(RenderArgs));
     W.S = scene->S;
@@ -818,7 +846,10 @@ int wave_enqueue(qrt_scene scene, const qrt_view* views, uint32_t n_views, const
     W.cost_on = d_cost != nullptr;
     wave_carve(workspace, cap, adjoint, W.B);
     int rc = make_params(params, W.P);
-    if (adjoint) W.P.path_log = nullptr;
+    if (adjoint) {
+        W.P.path_log = nullptr;
+        W.P.ray_log = nullptr;
+    }
     // the view table is shared with the single-kernel renderer's layout
     uint64_t paths = 0;
     for (uint32_t first = 0; rc == QRT_OK && first < n_views; first += kMaxViewsPerLaunch) {
@@ -828,7 +859,7 @@ int wave_enqueue(qrt_scene scene, const qrt_view* views, uint32_t n_views, const
         for (uint32_t k = 0; k < cnt; ++k) {
             W.views[k] = R.views[k];
             if (d_cost) W.views[k].cost_out = d_cost[first + k];
-            paths += (uint64_t)views[first + k].w * views[first + k].h * views[first + k].spp;
+            paths += region_pixels(views[first + k]) * views[first + k].spp;
         }
         W.n_views = cnt;
         StageHook* hook = (params && (params->flags & QRT_FLAG_STAGE_TIMES)) ? &scene->timer : nullptr;
@@ -862,14 +893,17 @@ int render_enqueue(qrt_scene scene, const qrt_view* views, uint32_t n_views, con
         A->stats = stats;
         A->batch = (uint32_t)t.batch;
         rc = make_params(params, A->P);
-        if (adjoint) A->P.path_log = nullptr;
+        if (adjoint) {
+            A->P.path_log = nullptr;
+            A->P.ray_log = nullptr;
+        }
         uint64_t paths = 0;
         for (uint32_t first = 0; rc == QRT_OK && first < n_views; first += kMaxViewsPerLaunch) {
             const uint32_t cnt = std::min<uint32_t>(kMaxViewsPerLaunch, n_views - first);
             rc = make_views(views, first, cnt, d_dimage, *A, paths);
             if (rc) break;
             for (uint32_t k = 0; k < cnt; ++k)
-                paths += (uint64_t)views[first + k].w * views[first + k].h * views[first + k].spp;
+                paths += region_pixels(views[first + k]) * views[first + k].spp;
             cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
             if (e == cudaSuccess) e = launch_render(*A, t, scene->sm_count, s);
             if (e != cudaSuccess) rc = cuda_fail(e, "render launch");

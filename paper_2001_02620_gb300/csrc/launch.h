@@ -58,11 +58,16 @@ struct Tune {
 };
 
 // A view with its camera basis precomputed on the host (FP64 -> FP32).
+// w x h is the rendered region (the whole frame, or a crop of it at (x0, y0));
+// the camera and the random streams are those of the whole frame, whose
+// width is fw: region pixel k is frame pixel (x0 + k % w, y0 + k / w) with
+// global index pixel_base + y * fw + x.
 struct ViewDev {
     float eye[3];
     float f[3], r[3], u[3];
     float sx0, sxs, sy0, sys;  // sx = sx0 + px*sxs, sy = sy0 + py*sys
     uint32_t w, h, spp, sample_base;
+    uint32_t x0, y0, fw;
     uint64_t pixel_base;
     uint64_t item_begin;  // first work item (pixel) of this view in the launch
     uint64_t path_begin;  // first path index of this view (for the path log)
@@ -82,7 +87,12 @@ struct ParamsDev {
     float sun_E[3];
     uint32_t sun_on;
     uint32_t* path_log;
+    float* ray_log;  // diagnostics: 12 floats per path and depth (see qrt_params)
 };
+
+// Floats per path and depth in the ray log: closest-hit ray (8), shadow-ray
+// origin (3), unused (1).
+constexpr int kRayLogFloats = 12;
 
 struct RenderArgs {
     DevScene S;

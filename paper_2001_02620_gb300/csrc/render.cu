@@ -34,7 +34,7 @@ template <int STACK, int FETCH>
 __device__ __forceinline__ uint32_t path_sample(const RenderArgs& A, const ViewDev& V, uint32_t x,
                                              uint32_t y, uint64_t gpix, uint32_t smp, int mode,
                                              float* L, const float* Ltot, const float* w,
-                                             uint32_t* log, TraceStats* st) {
+                                             uint32_t* log, float* rlog, TraceStats* st) {
     const ParamsDev& P = A.P;
     const DevScene& S = A.S;
     uint32_t err = 0;
@@ -48,8 +48,12 @@ __device__ __forceinline__ uint32_t path_sample(const RenderArgs& A, const ViewD
     uint32_t shadow_bits = 0;
     const uint32_t D = P.max_depth;
     uint32_t i = 1;
+    if (rlog)
+        for (uint32_t k = 0; k < 3 * D; ++k)
+            reinterpret_cast<float4*>(rlog)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (; i <= D; ++i) {
         Hit h;
+        if (rlog) log_ray(rlog + (i - 1) * kRayLogFloats, o, d);
         err |= trace_ray<false, STACK, FETCH>(S, o.x, o.y, o.z, d.x, d.y, d.z, 0.0f, kInfF,
                                                P.max_steps, h, ls);
         if (log) {
@@ -76,6 +80,7 @@ __device__ __forceinline__ uint32_t path_sample(const RenderArgs& A, const ViewD
             const float cl = dot3(n, f3(P.sun_l[0], P.sun_l[1], P.sun_l[2]));
             if (cl > 0.f) {
                 if (i <= 16) shadow_bits |= 1u << (2 * (i - 1));
+                if (rlog) log_shadow_origin(rlog + (i - 1) * kRayLogFloats, sp);
                 Hit hs;
                 err |= trace_ray<true, STACK, FETCH>(S, sp.x, sp.y, sp.z, P.sun_l[0], P.sun_l[1],
                                                       P.sun_l[2], 0.0f, kInfF, P.max_steps, hs, ls);
@@ -161,18 +166,18 @@ __global__ void __launch_bounds__(256) render_kernel(const __grid_constant__ Ren
             if (item >= A.n_items) break;
             const ViewDev& V = A.views[find_view(A, item)];
             const uint64_t pix = item - V.item_begin;
-            const uint32_t x = (uint32_t)(pix % V.w), y = (uint32_t)(pix / V.w);
-            const uint64_t gpix = V.pixel_base + pix;
+            uint32_t x, y;
+            const uint64_t gpix = view_pixel(V, pix, &x, &y);
             const float inv_spp = __frcp_rn((float)V.spp);
             if (!ADJ) {
                 float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
                 for (uint32_t s = 0; s < V.spp; ++s) {
                     float L[3];
-                    uint32_t* log = A.P.path_log
-                                        ? A.P.path_log + (V.path_begin + pix * V.spp + s) * (2ull * D + 1)
-                                        : nullptr;
+                    const uint64_t g = V.path_begin + pix * V.spp + s;
+                    uint32_t* log = A.P.path_log ? A.P.path_log + g * (2ull * D + 1) : nullptr;
+                    float* rlog = A.P.ray_log ? ray_log_rec(A.P, g, 1) : nullptr;
                     const uint32_t e = path_sample<STACK, FETCH>(A, V, x, y, gpix, V.sample_base + s, 0, L, nullptr,
-                                                                 nullptr, log, &st);
+                                                                 nullptr, log, rlog, &st);
                     if (e) {
                         err |= e;
                         bad = min(bad, item);
@@ -193,8 +198,9 @@ __global__ void __launch_bounds__(256) render_kernel(const __grid_constant__ Ren
                 for (uint32_t s = 0; s < V.spp; ++s) {
                     float L[3], L2[3];
                     uint32_t e = path_sample<STACK, FETCH>(A, V, x, y, gpix, V.sample_base + s, 0, L, nullptr,
-                                                           nullptr, nullptr, &st);
-                    e |= path_sample<STACK, FETCH>(A, V, x, y, gpix, V.sample_base + s, 1, L2, L, w, nullptr, &st);
+                                                           nullptr, nullptr, nullptr, &st);
+                    e |= path_sample<STACK, FETCH>(A, V, x, y, gpix, V.sample_base + s, 1, L2, L, w, nullptr,
+                                                   nullptr, &st);
                     if (e) {
                         err |= e;
                         bad = min(bad, item);

@@ -47,6 +47,29 @@ __device__ __forceinline__ F3 normalize3(F3 a) {
     return f3(__fmul_rn(a.x, inv), __fmul_rn(a.y, inv), __fmul_rn(a.z, inv));
 }
 
+// Frame coordinates (x, y) of pixel k of a view's rendered region, and the
+// pixel's global index, which keys its random streams.
+__device__ __forceinline__ uint64_t view_pixel(const ViewDev& V, uint64_t k, uint32_t* x, uint32_t* y) {
+    const uint32_t ly = (uint32_t)(k / V.w);
+    *x = V.x0 + (uint32_t)(k - (uint64_t)ly * V.w);
+    *y = V.y0 + ly;
+    return V.pixel_base + (uint64_t)*y * V.fw + *x;
+}
+
+// Ray-log record of depth i (1-based) of path g: the closest-hit ray as
+// (o, 0, d, inf), then the shadow-ray origin (diagnostics only).
+__device__ __forceinline__ float* ray_log_rec(const ParamsDev& P, uint64_t g, uint32_t i) {
+    return P.ray_log + (g * P.max_depth + (i - 1)) * (uint64_t)kRayLogFloats;
+}
+__device__ __forceinline__ void log_ray(float* rec, F3 o, F3 d) {
+    float4* r = reinterpret_cast<float4*>(rec);
+    r[0] = make_float4(o.x, o.y, o.z, 0.f);
+    r[1] = make_float4(d.x, d.y, d.z, __int_as_float(0x7f800000));
+}
+__device__ __forceinline__ void log_shadow_origin(float* rec, F3 o) {
+    reinterpret_cast<float4*>(rec)[2] = make_float4(o.x, o.y, o.z, 0.f);
+}
+
 // Pinhole ray through (x + xi1, y + xi2) of view V (unit direction).
 __device__ __forceinline__ F3 camera_dir(const ViewDev& V, uint32_t x, uint32_t y, float xi1, float xi2) {
     const float px = __fadd_rn((float)x, xi1);

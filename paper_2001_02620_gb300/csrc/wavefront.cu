@@ -79,8 +79,9 @@ __global__ void __launch_bounds__(256) wave_gen(const __grid_constant__ WaveArgs
     const uint64_t local = g - V.path_begin;
     const uint64_t pix = local / V.spp;
     const uint32_t smp = V.sample_base + (uint32_t)(local - pix * V.spp);  // global sample index
-    const uint32_t x = (uint32_t)(pix % V.w), y = (uint32_t)(pix / V.w);
-    const uint4 xi = draw(A.P.seed, V.pixel_base + pix, smp, 0);
+    uint32_t x, y;
+    const uint64_t gpix = view_pixel(V, pix, &x, &y);
+    const uint4 xi = draw(A.P.seed, gpix, smp, 0);
     const F3 d = camera_dir(V, x, y, u01(xi.x), u01(xi.y));
     A.B.ray_o[j] = make_float4(V.eye[0], V.eye[1], V.eye[2], 0.f);
     A.B.ray_d[j] = make_float4(d.x, d.y, d.z, kInfF);
@@ -92,6 +93,11 @@ __global__ void __launch_bounds__(256) wave_gen(const __grid_constant__ WaveArgs
     if (A.P.path_log) {
         uint32_t* log = A.P.path_log + g * (2ull * A.P.max_depth + 1);
         for (uint32_t k = 0; k < 2 * A.P.max_depth + 1; ++k) log[k] = k == 2 * A.P.max_depth ? 0u : 0xFFFFFFFFu;
+    }
+    if (A.P.ray_log) {
+        float4* rl = reinterpret_cast<float4*>(ray_log_rec(A.P, g, 1));
+        for (uint32_t k = 0; k < 3 * A.P.max_depth; ++k) rl[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        log_ray(reinterpret_cast<float*>(rl), f3(V.eye[0], V.eye[1], V.eye[2]), d);
     }
 }
 
@@ -222,6 +228,7 @@ __global__ void __launch_bounds__(256) wave_shade(const __grid_constant__ WaveAr
         const float cl = dot3(nrm, f3(A.P.sun_l[0], A.P.sun_l[1], A.P.sun_l[2]));
         if (cl > 0.f) {
             if (log && depth <= 16) log[2 * D] |= 1u << (2 * (depth - 1));
+            if (A.P.ray_log) log_shadow_origin(ray_log_rec(A.P, g, depth), sp);
             const float kk = __fmul_rn(cl, 0.318309886183790671538f);  // cos / pi
             const float4 p = make_float4(__fmul_rn(__fmul_rn(b.x, a0), __fmul_rn(A.P.sun_E[0], kk)),
                                          __fmul_rn(__fmul_rn(b.y, a1), __fmul_rn(A.P.sun_E[1], kk)),
@@ -251,8 +258,11 @@ __global__ void __launch_bounds__(256) wave_shade(const __grid_constant__ WaveAr
     if ((uint32_t)depth < D) {
         const uint2 mt = A.B.meta[j];
         const ViewDev& V = A.views[find_view_by_item(A, mt.x)];
-        const uint4 xi = draw(A.P.seed, V.pixel_base + (mt.x - V.item_begin), mt.y, (uint32_t)depth);
+        uint32_t px, py;
+        const uint64_t gpix = view_pixel(V, mt.x - V.item_begin, &px, &py);
+        const uint4 xi = draw(A.P.seed, gpix, mt.y, (uint32_t)depth);
         const F3 nd = sample_cosine(nrm, u01(xi.x), u01(xi.y));
+        if (A.P.ray_log) log_ray(ray_log_rec(A.P, g, depth + 1), sp, nd);
         A.B.ray_o[j] = make_float4(sp.x, sp.y, sp.z, 0.f);
         A.B.ray_d[j] = make_float4(nd.x, nd.y, nd.z, kInfF);
         push(A.B.q[(depth + 1) & 1], A.B.ctr + kCtrStride * (depth + 1) + kCtrClosest, j);
@@ -344,22 +354,62 @@ void wave_carve(void* base, uint64_t C, bool adjoint, WaveBufs& B) {
 // loaded on every device that runs it; concurrent calls share it.
 static __device__ __align__(256) unsigned char g_static_workspace[kStaticWorkspaceBytes];
 
+// The array's address is looked up once per device and context: a context
+// made anew (after cudaDeviceReset, say) holds a new copy of the array at
+// another address, so the cache is keyed by the context's unique id
+// (cuCtxGetId, reached through the runtime's driver entry points; nothing is
+// linked against the driver library).
+namespace {
+using CtxGetCurrent = int (*)(void**);
+using CtxGetId = int (*)(void*, unsigned long long*);
+
+cudaError_t current_context_id(unsigned long long* id) {
+    static CtxGetCurrent get_current = nullptr;
+    static CtxGetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrent>(f);
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetId>(f);
+    });
+    if (!get_current || !get_id) return cudaErrorNotSupported;
+    void* ctx = nullptr;
+    if (get_current(&ctx) != 0 || !ctx) return cudaErrorDeviceUninitialized;
+    return get_id(ctx, id) == 0 ? cudaSuccess : cudaErrorDeviceUninitialized;
+}
+}  // namespace
+
 cudaError_t static_workspace(void** ptr) {
     constexpr int kMaxDevices = 64;
+    struct Entry {
+        unsigned long long ctx = 0;
+        void* addr = nullptr;
+    };
     static std::mutex mu;
-    static void* addr[kMaxDevices] = {};
+    static Entry cache[kMaxDevices];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    // makes the device's primary context current (initialising it if needed)
+    if ((e = cudaSetDevice(dev)) != cudaSuccess) return e;
+    unsigned long long ctx = 0;
+    if ((e = current_context_id(&ctx)) != cudaSuccess) return e;
     std::lock_guard<std::mutex> g(mu);
-    if (!addr[dev]) {
+    Entry& c = cache[dev];
+    if (!c.addr || c.ctx != ctx) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_static_workspace);
         if (e != cudaSuccess) return e;
-        addr[dev] = p;
+        c.addr = p;
+        c.ctx = ctx;
     }
-    *ptr = addr[dev];
+    *ptr = c.addr;
     return cudaSuccess;
 }
 

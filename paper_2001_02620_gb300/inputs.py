@@ -75,6 +75,19 @@ class View:
     spp: int
     pixel_base: int = 0
     sample_base: int = 0  # first sample index drawn (progressive frames)
+    # rendered region: the whole w x h frame when crop_w = crop_h = 0, else
+    # the crop_w x crop_h rectangle at (crop_x, crop_y) of that frame
+    crop_x: int = 0
+    crop_y: int = 0
+    crop_w: int = 0
+    crop_h: int = 0
+
+    @property
+    def region(self) -> tuple:
+        """(width, height) of the rendered region."""
+        if self.crop_w == 0 and self.crop_h == 0:
+            return int(self.w), int(self.h)
+        return int(self.crop_w), int(self.crop_h)
 
 
 @dataclass

@@ -82,3 +82,257 @@ def split_log(glog, D):
 def path_agreement(glog, ref, D):
     gi, gp, gs = split_log(glog, D)
     return (gi == ref["inst"]).all(1) & (gp == ref["prim"]).all(1) & (gs == ref["shadow"])
+
+
+# --------------------------------------------------------------------------
+# Divergent render paths.  Past the camera ray the two sides trace different
+# rays: the GPU spawns each bounce from an FP32 hit point and samples its
+# direction in FP32, the oracle does both in FP64.  Where such a small
+# difference moves a ray across a quad edge or past a near-equal hit, the
+# paths part.  explain_divergences() takes every path whose hit IDs or
+# shadow bits differ, finds the first depth where they do, and requires that
+#   (a) the ray the GPU traced there is the oracle's ray up to FP32 rounding:
+#       direction within DIR_TOL, origin within ORIGIN_TOL * (1 + |p|) / c,
+#       where c = |cos| of the angle at the hit the origin was spawned from
+#       (a grazing hit turns a rounding-size error in the ray into a larger
+#       error in the hit distance, hence in the spawn point), and
+#   (b) on that very FP32 ray the oracle gives the GPU's answer, or the
+#       GPU's answer is an FP64 near-tie (classify_closest / the any-hit
+#       analogue).
+# Paths failing (a) or (b) are unexplained.
+# --------------------------------------------------------------------------
+ORIGIN_TOL = 1e-4
+DIR_TOL = 1e-4
+
+
+def _unit(v):
+    return v / np.linalg.norm(v, axis=-1, keepdims=True)
+
+
+def world_normal(scene, inst, prim):
+    """FP64 unit geometric normal of a quad in world space (cross of the
+    diagonals moved by the inverse transpose), unfaced."""
+    v, q = scene.meshes[int(scene.mesh_ids[inst])]
+    P = v[q[prim]].astype(np.float64)
+    n = np.cross(P[2] - P[0], P[3] - P[1])
+    M = scene.xforms[inst].reshape(3, 4).astype(np.float64)[:, :3]
+    return _unit(np.linalg.inv(M).T @ n)
+
+
+def first_divergence(gi, gp, gs, oi, op, osh):
+    """Per path: (depth k >= 1 of the first difference or 0, kind) where kind
+    is 'hit' (instance or quad of the depth-k hit) or 'shadow' (the shadow
+    bits of vertex k, hits equal through depth k)."""
+    P, D = gi.shape
+    hit_bad = (gi != oi) | (gp != op)
+    kh = np.where(hit_bad.any(1), hit_bad.argmax(1) + 1, D + 1)
+    nv = min(D, 16)
+    sh = np.stack([((gs >> (2 * i)) & 3) != ((osh >> (2 * i)) & 3) for i in range(nv)], 1)
+    ks = np.where(sh.any(1), sh.argmax(1) + 1, D + 1)
+    k = np.minimum(kh, ks)
+    kind = np.where(k == kh, "hit", "shadow")
+    k = np.where(k > D, 0, k)
+    return k, kind
+
+
+def explain_divergences(scene, osc, glog, grays, ref, D, sun_dir, gpu_closest=None):
+    """glog: GPU path log [P, 2D+1] (uint32); grays: GPU ray log [P, D, 12]
+    (float32); ref: oracle render dict with log=True, rays=True for the same
+    paths.  gpu_closest(rays float32 [n, 8]) -> (inst, prim) traces rays on
+    the GPU (used to name the occluder of a shadow ray only the GPU found
+    blocked).  Returns a dict of counts, the largest ray deviations seen and
+    the list of unexplained path indices."""
+    gi, gp, gs = split_log(glog, D)
+    oi, op, osh = ref["inst"], ref["prim"], ref["shadow"]
+    orays = ref["rays"]
+    k, kind = first_divergence(gi, gp, gs, oi, op, osh)
+    div = np.nonzero(k)[0]
+    sun = np.asarray(sun_dir, dtype=np.float64)
+    l64 = sun / np.linalg.norm(sun)
+    l32 = l64.astype(np.float32)
+    out = dict(paths=len(gi), divergent=len(div), by_ray=0, near_tie=0, grazing_sun=0,
+               unexplained=[], max_origin_dev=0.0, max_dir_dev=0.0, depths={})
+    hit_paths = [p for p in div if kind[p] == "hit"]
+    sh_paths = [p for p in div if kind[p] == "shadow"]
+    # (a) the GPU ray at the divergence is the oracle's ray up to rounding
+    ok_ray = {}
+    for p in div:
+        j = k[p] - 1
+        if kind[p] == "hit":
+            og, dg = grays[p, j, 0:3].astype(np.float64), grays[p, j, 4:7].astype(np.float64)
+            oo, do = orays[p, j, 0:3], orays[p, j, 3:6]
+            dev_d = float(np.abs(_unit(dg) - _unit(do)).max())
+            src = j - 1          # the hit this origin was spawned from (none for the camera ray)
+        else:
+            og, oo = grays[p, j, 8:11].astype(np.float64), orays[p, j, 6:9]
+            dev_d = 0.0
+            src = j
+        cosv = 1.0
+        if src >= 0:
+            nrm = world_normal(scene, oi[p, src], op[p, src])
+            cosv = max(abs(float(nrm @ _unit(orays[p, src, 3:6]))), 1e-3)
+        dev_o = float(np.abs(og - oo).max() / (1.0 + np.abs(oo).max())) * cosv
+        out["max_origin_dev"] = max(out["max_origin_dev"], dev_o)
+        out["max_dir_dev"] = max(out["max_dir_dev"], dev_d)
+        ok_ray[p] = dev_o <= ORIGIN_TOL and dev_d <= DIR_TOL
+        out["depths"][int(k[p])] = out["depths"].get(int(k[p]), 0) + 1
+    # (b) closest-hit divergences: the oracle on the GPU's own FP32 ray
+    if hit_paths:
+        rays = np.stack([grays[p, k[p] - 1, 0:8] for p in hit_paths]).astype(np.float32)
+        g_i = np.array([gi[p, k[p] - 1] for p in hit_paths], dtype=np.uint32)
+        g_p = np.array([gp[p, k[p] - 1] for p in hit_paths], dtype=np.uint32)
+        o_t, o_i, o_p, _, _ = osc.trace_closest(rays)
+        same = (o_i == g_i) & (o_p == g_p)
+        _, _, bad = classify_closest(scene, rays, g_i, g_p, o_t, o_i, o_p)
+        bad = set(bad)
+        for n, p in enumerate(hit_paths):
+            if not ok_ray[p]:
+                out["unexplained"].append(int(p))
+            elif same[n]:
+                out["by_ray"] += 1
+            elif n not in bad:
+                out["near_tie"] += 1
+            else:
+                out["unexplained"].append(int(p))
+    # shadow divergences at vertex k (hits equal through depth k)
+    if sh_paths:
+        rays = np.zeros((len(sh_paths), 8), dtype=np.float32)
+        for n, p in enumerate(sh_paths):
+            rays[n, 0:3] = grays[p, k[p] - 1, 8:11]
+            rays[n, 4:7] = l32
+            rays[n, 7] = np.inf
+        occ_o = osc.trace_any(rays)
+        need_gpu = []
+        for n, p in enumerate(sh_paths):
+            j = k[p] - 1
+            g_bits, o_bits = (gs[p] >> (2 * j)) & 3, (osh[p] >> (2 * j)) & 3
+            if (g_bits & 1) != (o_bits & 1):
+                # one side traced a shadow ray, the other did not: n.l is
+                # within rounding of zero at this vertex
+                nrm = world_normal(scene, gi[p, j], gp[p, j])
+                if abs(float(nrm @ l64)) <= 1e-5:
+                    out["grazing_sun"] += 1
+                else:
+                    out["unexplained"].append(int(p))
+                continue
+            if not ok_ray[p]:
+                out["unexplained"].append(int(p))
+                continue
+            g_occ = bool(g_bits & 2)
+            if occ_o[n] == g_occ:
+                out["by_ray"] += 1
+            elif not g_occ:
+                # the oracle finds an occluder the GPU missed: it must be grazed
+                t, i_, q_, _, _ = osc.trace_closest(rays[n:n + 1])
+                _, _, m = quad_eval(rays[n, 0:3].astype(np.float64), l64,
+                                    world_quad(scene, i_[0], q_[0]))
+                if abs(m) <= EDGE:
+                    out["near_tie"] += 1
+                else:
+                    out["unexplained"].append(int(p))
+            else:
+                need_gpu.append((n, p))
+        if need_gpu:
+            sel = np.stack([rays[n] for n, _ in need_gpu])
+            if gpu_closest is None:
+                out["unexplained"] += [int(p) for _, p in need_gpu]
+            else:
+                ci, cq = gpu_closest(sel)
+                for m_, (n, p) in enumerate(need_gpu):
+                    if ci[m_] == NONE:
+                        out["unexplained"].append(int(p))
+                        continue
+                    _, _, m = quad_eval(sel[m_, 0:3].astype(np.float64), l64,
+                                        world_quad(scene, ci[m_], cq[m_]))
+                    if abs(m) <= EDGE:
+                        out["near_tie"] += 1
+                    else:
+                        out["unexplained"].append(int(p))
+    return out
+
+
+def count_rays(glog, D):
+    """Closest-hit and shadow rays of logged paths (for the near-tie rate)."""
+    gi, _, gs = split_log(glog, D)
+    hits = (gi != NONE).sum()
+    escapes = ((gi == NONE).any(1)).sum()  # the ray after a path's last hit left the scene
+    shadow = sum(int(((gs >> (2 * i)) & 1).sum()) for i in range(min(D, 16)))
+    return int(hits + escapes + shadow)
+
+
+def render_parity(api, gs, osc, scene, view, alb, params, pixels=None, tuning=None):
+    """Renders `view` (whole frame, the given launch tuning) on the GPU with
+    path and ray logs, renders the sampled pixels (None = all) with the
+    oracle, and compares: returns (pix_ok [n] bool, per-pixel radiance error
+    where every sample's path agrees, oracle rgb there, divergence report
+    from explain_divergences with 'rays' = rays of the compared paths)."""
+    import torch
+    D = params.max_depth
+    spp = int(view.spp)
+    alb_d = torch.from_numpy(alb).cuda()
+    log = torch.zeros(api.path_log_words([view], D), dtype=torch.int32, device="cuda")
+    rlog = torch.zeros(api.ray_log_floats([view], D), dtype=torch.float32, device="cuda")
+    (img,) = gs.render([view], alb_d, params, path_log=log, ray_log=rlog, tuning=tuning)
+    gs.check()
+    npix = int(view.w) * int(view.h)
+    if pixels is None:
+        pixels = np.arange(npix, dtype=np.int64)
+    px = torch.from_numpy(np.asarray(pixels, dtype=np.int64)).cuda()
+    paths = (px[:, None] * spp + torch.arange(spp, device="cuda")[None, :]).reshape(-1)
+    glog = log.view(-1, 2 * D + 1)[paths].cpu().numpy().view(np.uint32)
+    grays = rlog.view(-1, D, 12)[paths].cpu().numpy()
+    g = img.reshape(-1, 3)[px].double().cpu().numpy()
+    ref = osc.render(view, alb, params, pixels=pixels, log=True, rays=True)
+    agree = path_agreement(glog, ref, D)
+    pix_ok = agree.reshape(-1, spp).all(1)
+    r = ref["rgb"]
+    err = np.abs(g[pix_ok] - r[pix_ok])
+
+    def gpu_closest(rays):
+        h = gs.trace_closest(torch.from_numpy(np.ascontiguousarray(rays)).cuda())
+        h = h.cpu().numpy().view(np.uint32)
+        return h[:, 1], h[:, 2]
+
+    rep = explain_divergences(scene, osc, glog, grays, ref, D, params.sun_dir, gpu_closest)
+    rep["rays"] = count_rays(glog, D)
+    rep["divergent_path_frac"] = rep["divergent"] / max(1, rep["paths"])
+    rep["near_tie_ray_frac"] = rep["near_tie"] / max(1, rep["rays"])
+    return pix_ok, err, r[pix_ok], rep
+
+
+def report_line(name, rep) -> str:
+    return (f"{name}: {rep['divergent']}/{rep['paths']} paths diverge "
+            f"({rep['divergent_path_frac']:.2e}): {rep['by_ray']} by the FP32 ray, "
+            f"{rep['near_tie']} FP64 near-ties ({rep['near_tie_ray_frac']:.1e} of {rep['rays']} rays), "
+            f"{rep['grazing_sun']} grazing sun, {len(rep['unexplained'])} unexplained; "
+            f"first depths {dict(sorted(rep['depths'].items()))}; max ray deviation "
+            f"origin {rep['max_origin_dev']:.1e} (x cos at its hit) direction {rep['max_dir_dev']:.1e}")
+
+
+def rays_from_render(api, gs, view, alb_d, params, depth_sets=(1, 2)):
+    """Ray sets dumped from a render through the ray log: {'depth1': camera
+    rays, 'depth2': the first diffuse bounce rays, 'shadow': the shadow rays
+    toward the sun} as float32 [n, 8] qrt_ray arrays (rays a path did not
+    trace are left out)."""
+    import torch
+    D = params.max_depth
+    rlog = torch.zeros(api.ray_log_floats([view], D), dtype=torch.float32, device="cuda")
+    gs.render([view], alb_d, params, ray_log=rlog)
+    gs.check()
+    r = rlog.view(-1, D, 12)
+    out = {}
+    for k in depth_sets:
+        rk = r[:, k - 1, 0:8]
+        keep = rk[:, 7] != 0  # tmax = inf on a traced ray, 0 on an empty record
+        out[f"depth{k}"] = rk[keep].cpu().numpy()
+    so = r[:, :, 8:11].reshape(-1, 3)
+    keep = (so != 0).any(1)
+    so = so[keep].cpu().numpy()
+    sun = np.asarray(params.sun_dir, dtype=np.float64)
+    l = (sun / np.linalg.norm(sun)).astype(np.float32)
+    sh = np.zeros((so.shape[0], 8), dtype=np.float32)
+    sh[:, 0:3] = so
+    sh[:, 4:7] = l
+    sh[:, 7] = np.inf
+    out["shadow"] = sh
+    return out

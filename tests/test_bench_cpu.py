@@ -9,8 +9,11 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_reference_arm_prints_one_json_line():
+    # the mid workload keeps the CPU suite short; the default (Moana-scale)
+    # workload runs the same code on a 261 M-quad scene
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
-                        "--warmup", "3"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+                        "--warmup", "3", "--workload", "mid"], cwd=ROOT, capture_output=True,
+                       text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1, r.stdout[-2000:]
@@ -26,3 +29,8 @@ def test_reference_arm_prints_one_json_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "Mrays/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+    # the GPU arm prints the same config dict for the same workload
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["config"] == bench.workload_config("mid", 1.0)
+    assert set(bench.workload_config("moana", 1.0)) == {"workload", "l2"}

@@ -12,7 +12,7 @@ import oracle as O
 from paper_2001_02620_gb300 import inputs as I
 
 from golden_data import table1
-from parity import NONE, classify_closest, path_agreement, split_log
+from parity import NONE, classify_closest, path_agreement, render_parity, report_line, split_log
 
 pytestmark = pytest.mark.gpu
 
@@ -34,29 +34,26 @@ def mid(api):
 
 
 def test_mid_render_sampled_pixels(api, mid):
+    """The benchmark's frame (1024x1024, 4 spp, depth 5, library default
+    launch) on 16384 sampled pixels: every path that leaves the oracle's is
+    explained at the depth where it does, and agreeing paths match the
+    oracle's radiance within 1e-4."""
     sc, gs, osc = mid
     view, params = I.mid_view(), I.mid_params()
     alb = I.albedo(sc.n_quads)
-    D = params.max_depth
-    log = torch.zeros(api.path_log_words([view], D), dtype=torch.int32, device="cuda")
-    (img,) = gs.render([view], torch.from_numpy(alb).cuda(), params, path_log=log)
-    gs.check()
     rng = np.random.default_rng(17)
-    px = np.sort(rng.choice(view.w * view.h, size=1024, replace=False))
-    ref = osc.render(view, alb, params, pixels=px, log=True)
-    glog = log.view(-1, 2 * D + 1).reshape(view.w * view.h, view.spp, 2 * D + 1)
-    glog = glog[torch.from_numpy(px).cuda()].reshape(-1, 2 * D + 1).cpu().numpy().view(np.uint32)
-    agree = path_agreement(glog, ref, D)
-    pix_ok = agree.reshape(-1, view.spp).all(1)
-    g = img.reshape(-1, 3)[torch.from_numpy(px).cuda()].double().cpu().numpy()
-    r = ref["rgb"]
-    err = np.abs(g[pix_ok] - r[pix_ok])
-    assert pix_ok.mean() > 0.97, f"divergent pixels {1 - pix_ok.mean():.3f}"
-    assert (err <= 1e-4 * np.abs(r[pix_ok]) + 1e-6).all(), err.max()
-    # the sampled paths exercise every branch: escapes, surfaces, sun, shadow
-    gi, gp, gs_bits = split_log(glog, D)
-    assert (gi[:, 0] != NONE).mean() > 0.5
-    assert ((gs_bits & 1) != 0).any() and ((gs_bits & 2) != 0).any()
+    px = np.sort(rng.choice(view.w * view.h, size=16384, replace=False))
+    pix_ok, err, r, rep = render_parity(api, gs, osc, sc, view, alb, params, pixels=px)
+    print(report_line("mid 1024^2 4 spp depth 5", rep))
+    assert not rep["unexplained"], rep["unexplained"][:8]
+    assert rep["near_tie"] <= max(1, 1e-5 * rep["rays"]), report_line("mid", rep)
+    # measured 5.2e-4 (34 of 65536 paths); the bound allows 3x that
+    assert rep["divergent_path_frac"] < 1.5e-3, report_line("mid", rep)
+    assert (err <= 1e-4 * np.abs(r) + 1e-6).all(), err.max()
+    # the sampled paths exercise every branch: surfaces, sun, shadow, and
+    # divergences first seen past the camera ray
+    assert rep["rays"] > 150000
+    assert len(rep["depths"]) >= 2
 
 
 def _mid_rays(sc):

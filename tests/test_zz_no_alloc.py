@@ -1,10 +1,12 @@
 """qrt_render_spp_static: the render entry point for callers that cannot
-allocate device memory (code running under stream capture, frame loops that
-must not stall on cudaMalloc, processes whose memory belongs to another
-allocator).  It renders with scratch held in a fixed array inside the
-library, so this test calls it through the C ABI and checks that it gives the
-same images as qrt_render_spp, twice in a row (the array keeps the previous
-call's contents, which must not leak into the next result)."""
+allocate device memory (frame loops that must not stall on cudaMalloc,
+processes whose device memory belongs to another allocator).  It renders
+with scratch held in a fixed array inside the library, so this test calls it
+through the C ABI and checks that it gives exactly the images of
+qrt_render_spp (the wavefront renderer is bit-reproducible across chunk
+sizes), twice in a row (the array keeps the previous call's contents, which
+must not leak into the next result), and that a call leaves the device's
+free memory unchanged."""
 import ctypes as C
 
 import numpy as np
@@ -28,8 +30,9 @@ def lib_api():
     return N, api
 
 
-def _call_static(N, api, scene, views, alb, params, tuning=None):
-    outs = [torch.full((v.h, v.w, 3), float("nan"), device="cuda") for v in views]
+def _call_static(N, api, scene, views, alb, params, tuning=None, outs=None):
+    if outs is None:
+        outs = [torch.full((v.h, v.w, 3), float("nan"), device="cuda") for v in views]
     cv = api.make_views(views, outs)
     cp = api.make_params(params, tuning)
     rc = N.lib().qrt_render_spp_static(scene.handle, cv, len(views), alb.data_ptr(), C.byref(cp),
@@ -50,14 +53,18 @@ def test_static_render_matches_render_spp(lib_api):
     alb = torch.from_numpy(I.albedo(sc.n_quads)).cuda()
     ref = scene.render(views, alb, params)
     torch.cuda.synchronize()
-    for _ in range(2):
-        rc, outs = _call_static(N, api, scene, views, alb, params)
+    for k in range(2):
+        outs = [torch.full((v.h, v.w, 3), float("nan"), device="cuda") for v in views]
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        rc, outs = _call_static(N, api, scene, views, alb, params, outs=outs)
         N.check(rc)
         scene.check()
         torch.cuda.synchronize()
+        if k == 1:  # the first call may still load kernel code; the second allocates nothing
+            assert torch.cuda.mem_get_info()[0] == free0
         for o, r in zip(outs, ref):
-            assert torch.isfinite(o).all()
-            torch.testing.assert_close(o, r, rtol=1e-4, atol=1e-6)
+            assert torch.equal(o, r)
     scene.close()
 
 
@@ -73,4 +80,10 @@ def test_static_render_rejects_oversized_chunk(lib_api):
     assert b"static workspace" in N.lib().qrt_last_error()
     rc, _ = _call_static(N, api, scene, [view], alb, I.tiny_params(), tuning=dict(mode=1))
     assert rc == N.QRT_ERR_INVALID_ARG
+    # a pixel's samples must fit one chunk of the static workspace
+    one = I.tiny_view()
+    one.w, one.h, one.spp = 1, 1, (1 << 17) + 1
+    rc, _ = _call_static(N, api, scene, [one], alb, I.tiny_params())
+    assert rc == N.QRT_ERR_INVALID_ARG
+    assert b"spp 131073" in N.lib().qrt_last_error()
     scene.close()
