@@ -1,11 +1,17 @@
 """Benchmark of the instanced-quad path tracer on one GB300 (or N replicas).
 
-A step is one qrt_render_spp of the mid workload: 64 prototypes + terrain
-(5.73 M unique quads), 100k instances, 1024x1024, 4 spp, path depth 5,
+A step is one qrt_render_spp of the Moana-scale workload: 5000 prototypes
+(261.1 M unique quads) instanced 39.3 M times (82.4 G instanced quads, the
+Moana Island statistics of Section 1), 1920x1080, 16 spp, path depth 8,
 environment + sun with shadow rays.  value = all rays traced per second
-(closest-hit + shadow), the accounting of the paper's Mray/s (Section 6, "Results").
+(closest-hit + shadow), the accounting of the paper's Mray/s (Section 6,
+"Results").  The mid workload (5.73 M unique quads, 100 k instances,
+1024x1024, 4 spp, depth 5) is measured in the same run as a sub-measurement
+(key "mid"), with the batched-views and adjoint workloads that are defined
+on it.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+       [--workload moana|mid] [--moana-scale S]
 Under torchrun each rank renders its own frame (weak scaling, no collective
 on the data path); rank 0 prints one JSON line.
 """
@@ -49,17 +55,19 @@ def kernel_source_hash() -> str:
 
 
 def recorded_traffic(workload: str):
-    """DRAM bytes per launch of the closest-hit trace kernel from the committed
-    ncu summary, if it was taken on the current kernel sources."""
+    """DRAM bytes per launch of the closest-hit trace kernel as recorded from
+    a committed ncu capture (not measured in this run), if that capture was
+    taken on the current kernel sources: (bytes, kernel, source note)."""
     p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     try:
         d = json.load(open(p))
     except (OSError, ValueError):
-        return None, None
+        return None, None, None
     e = d.get(workload)
     if not e or e.get("kernel_source_hash") != kernel_source_hash():
-        return None, None
-    return float(e["dram_bytes_per_launch"]), e.get("kernel")
+        return None, None, None
+    return (float(e["dram_bytes_per_launch"]), e.get("kernel"),
+            "recorded, not measured in this run: " + e.get("source", "profiles/roofline_traffic.json"))
 
 
 def peaks():
@@ -136,36 +144,53 @@ WORKLOADS = {
              "2048^2 terrain = 261.1M unique quads, 39.3M clustered instances (82.4G instanced "
              "quads), 1920x1080, 16 spp, depth 8, env + sun shadow rays",
 }
+# what stands between timed steps and the L2 (the same words on both arms)
+L2_NOTE = {
+    "mid": "no flush: scene (0.36 GB) and per-path state (0.7 GB) exceed the 129 MB L2",
+    "moana": "no flush: scene (23 GB) and per-path state (5.5 GB) exceed the 129 MB L2",
+}
 
 
-def oracle_sample(sc, view, params, alb, budget_s: float, frame: str = "1024x1024 mid"):
-    """Times the FP64 oracle on a bounded pixel sample of the same workload."""
-    import oracle as O
-    t0 = time.time()
-    osc = O.OracleScene(sc)
-    build_s = time.time() - t0
-    rng = np.random.default_rng(99)
+def workload_config(workload: str, scale: float) -> dict:
+    """The config dict both arms print (identical for the same workload)."""
+    w = WORKLOADS[workload]
+    if workload == "moana" and scale != 1.0:
+        w += f" x {scale}"
+    return {"workload": w, "l2": L2_NOTE[workload]}
+
+
+def load_workload(workload: str, scale: float):
+    return moana_workload(scale) if workload == "moana" else mid_workload()
+
+
+def oracle_sample(osc, view, params, alb, budget_s: float, frame: str, seed: int = 99,
+                  build_s: float | None = None):
+    """Times the FP64 oracle (all host cores) on a bounded random pixel sample
+    of the workload's frame: batches of 256, 512, ... pixels (all spp) until
+    budget_s seconds of oracle time are spent."""
+    rng = np.random.default_rng(seed)
     npix = view.w * view.h
     n = 256
     rays = 0
     elapsed = 0.0
     done = 0
     while elapsed < budget_s and done < npix:
-        px = rng.choice(npix, size=n, replace=False)
+        px = np.sort(rng.choice(npix, size=min(n, npix), replace=False))
         t = time.time()
         r = osc.render(view, alb, params, pixels=px, log=True)
         dt = time.time() - t
         hits = int((r["inst"] != 0xFFFFFFFF).sum())
         sh = r["shadow"]
-        shadow = sum(int(((sh >> (2 * i)) & 1).sum()) for i in range(params.max_depth))
+        shadow = sum(int(((sh >> (2 * i)) & 1).sum()) for i in range(min(16, params.max_depth)))
         rays += hits + int(r["escaped"]) + shadow
         elapsed += dt
-        done += n
+        done += len(px)
         n *= 2
     cores = os.cpu_count() or 1
+    extra = f", oracle BVH build {build_s:.1f} s excluded" if build_s is not None else ""
     return {"value": rays / elapsed / 1e6, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
             "sample": f"{done} random pixels x {view.spp} spp of the {frame} frame "
-                      f"({rays} rays, {elapsed:.1f} s FP64, oracle BVH build {build_s:.1f} s excluded)",
+                      f"({rays} rays, {elapsed:.1f} s FP64{extra})",
             "paths_per_s": done * view.spp / elapsed}
 
 
@@ -187,36 +212,58 @@ def _time(fn, reps: int, warm: int = 2) -> float:
     return float(np.median(ts))
 
 
-def bench_trace(scene, sc, dev, tuning=None, eye=(2048.0, -300.0, 450.0)):
-    """trace_closest / trace_any throughput on 4M-ray sets over the scene:
-    a coherent bundle from the camera, incoherent rays from random origins,
-    and parallel rays toward the sun."""
+def dumped_rays(api, scene, view, d_alb, params, n: int, tuning=None):
+    """Ray sets dumped from a render of the workload's camera through the ray
+    log (enough samples per pixel for n camera rays): 'primary' = the camera
+    rays, 'diffuse' = the rays leaving the first hit (depth 2), 'shadow' =
+    the shadow rays toward the sun; each float32 [<= n, 8] on the device, in
+    the order the renderer traces them."""
+    import dataclasses
     import torch
-    from paper_2001_02620_gb300 import inputs as I
-    ext = float(sc.meta.get("extent", 4096.0))
-    lo = np.array([0.0, 0.0, -150.0])
-    hi = np.array([ext, ext, 250.0])
-    n = 1 << 22
-    sets = {
-        "primary": I.rays_focused(n, eye, lo, hi, seed=51),
-        "incoherent": I.rays_random(n, lo, hi, seed=52),
-        "shadow": I.rays_parallel(n, lo, hi, I.MID_SUN_DIR, seed=53),
-    }
+    spp = max(1, -(-n // (view.w * view.h)))
+    v = dataclasses.replace(view, spp=spp)
+    D = params.max_depth
+    rlog = torch.zeros(api.ray_log_floats([v], D), dtype=torch.float32, device=d_alb.device)
+    scene.render([v], d_alb, params, ray_log=rlog, tuning=tuning)
+    scene.check()
+    r = rlog.view(-1, D, 12)
     out = {}
-    hits = torch.empty((n, 4), dtype=torch.int32, device=dev)
-    bits = torch.empty(((n + 31) // 32,), dtype=torch.int32, device=dev)
-    for name, rays in sets.items():
-        d = torch.from_numpy(rays).to(dev)
+    for name, k in (("primary", 0), ("diffuse", 1)):
+        rk = r[:, k, 0:8]
+        out[name] = rk[rk[:, 7] != 0][:n].contiguous()
+    so = r[:, :, 8:11].reshape(-1, 3)
+    so = so[(so != 0).any(1)][:n]
+    sun = torch.tensor(params.sun_dir, dtype=torch.float64)
+    sh = torch.zeros((so.shape[0], 8), dtype=torch.float32, device=so.device)
+    sh[:, 0:3] = so
+    sh[:, 4:7] = (sun / sun.norm()).float().to(so.device)
+    sh[:, 7] = float("inf")
+    out["shadow"] = sh
+    del rlog, r
+    return out
+
+
+def bench_trace(api, scene, view, d_alb, params, dev, tuning=None, n=1 << 22):
+    """trace_closest / trace_any throughput on ray sets dumped from a render
+    of the workload's view: camera rays, first diffuse bounces, shadow rays."""
+    import torch
+    out = {}
+    for name, d in dumped_rays(api, scene, view, d_alb, params, n, tuning).items():
+        m = d.shape[0]
+        hits = torch.empty((m, 4), dtype=torch.int32, device=dev)
+        bits = torch.empty(((m + 31) // 32,), dtype=torch.int32, device=dev)
         tc = _time(lambda: scene.trace_closest(d, hits, tuning=tuning), 5)
         ta = _time(lambda: scene.trace_any(d, bits, tuning=tuning), 5)
         st = torch.zeros(6, dtype=torch.int64, device=dev)
         scene.trace_stats(d, False, hits, st)
         s = st.cpu().numpy()
-        out[name] = {"closest_mrays_s": n / tc / 1e6, "any_mrays_s": n / ta / 1e6,
+        out[name] = {"rays": m, "closest_mrays_s": m / tc / 1e6, "any_mrays_s": m / ta / 1e6,
                      "hit_rate": float((hits[:, 1] != -1).float().mean().item()),
-                     "nodes_per_ray": float(s[1]) / n, "quads_per_ray": float(s[2]) / n,
-                     "instances_per_ray": float(s[3]) / n}
+                     "nodes_per_ray": float(s[1]) / m, "quads_per_ray": float(s[2]) / m,
+                     "instances_per_ray": float(s[3]) / m}
     scene.check()
+    out["source"] = ("rays dumped from a render of the workload's view (qrt_params.d_ray_log), "
+                     "in the order the renderer traces them")
     return out
 
 
@@ -353,16 +400,24 @@ def bench_adjoint(api, scene, sc, dev, tuning=None):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle (the plain CPU implementation the
+    GPU path is checked against) timed on the host cores, each step a
+    bounded random pixel sample of the same workload's frame."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    sc, view, params, alb = mid_workload()
-    per = []
-    secs = []
+    import oracle as O
+    sc, view, params, alb = load_workload(args.workload, args.moana_scale)
+    t0 = time.time()
+    osc = O.OracleScene(sc)
+    build_s = time.time() - t0
+    per, secs = [], []
     base = None
+    frame = f"{view.w}x{view.h} {args.workload}"
     for k in range(args.warmup + args.steps):
         t0 = time.time()
-        r = oracle_sample(sc, view, params, alb, budget_s=8.0 if k >= args.warmup else 2.0)
+        r = oracle_sample(osc, view, params, alb, budget_s=5.0 if k >= args.warmup else 1.0,
+                          frame=frame, seed=1000 + k, build_s=build_s)
         if k >= args.warmup:
             secs.append(time.time() - t0)
             per.append(r["value"])
@@ -372,13 +427,210 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "ms_per_step": 1e3 * float(np.mean(secs)), "scaling": "weak",
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS["mid"],
-                       "parallelism": f"{base['cores']} host threads (FP64 oracle)"},
+            "config": workload_config(args.workload, args.moana_scale),
+            "setup": {"parallelism": f"{base['cores']} host threads (FP64 oracle)",
+                      "oracle_build_s": build_s},
             "cpu_baseline": {"value": v, "unit": "Mrays/s", "cores": base["cores"], "kind": "oracle",
-                             "sample": base["sample"]},
+                             "sample": f"per step: {base['sample']}"},
             "e2e": {"value": v, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "vs_baseline": None}
     print(json.dumps(line), flush=True)
+
+
+def measure(scene, view, d_alb, params, tuning, steps, warmup, world, dev, clocks=None):
+    """One workload's headline numbers: traversal counters of one render,
+    then `warmup` untimed steps and `steps` timed steps (barrier and device
+    synchronisation on both sides, CUDA events on the launch stream, max over
+    ranks), then the same steps again with a CUDA event pair around every
+    stage launch (stages in order) for the per-kernel times."""
+    import torch
+    import torch.distributed as dist
+    stream = torch.cuda.current_stream()
+    img = torch.empty((view.h, view.w, 3), device=dev)
+
+    def step(stage_times=False):
+        scene.render([view], d_alb, params, outs=[img], tuning=tuning, stage_times=stage_times)
+
+    stats = torch.zeros(STAT_WORDS, dtype=torch.int64, device=dev)
+    scene.render([view], d_alb, params, outs=[img], stats=stats, tuning=tuning)
+    scene.check()
+    st = [int(x) for x in stats.cpu().numpy()]
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    scene.stage_times(reset=True)
+    if world > 1:
+        dist.barrier()
+    if clocks:
+        clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1) / steps
+    clk = clocks.stop() if clocks else None
+    scene.check()
+    scene.stage_times(reset=True)
+    for _ in range(steps):
+        step(stage_times=True)
+    torch.cuda.synchronize()
+    stages = scene.stage_times(reset=True)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    c_rays, c_nodes, c_quads, c_insts, c_fb, verts = st[0:6]
+    s_rays, s_nodes, s_quads, s_insts, s_fb, _ = st[6:12]
+    # algorithmic bytes: 64 B per node, 48 B per quad tested, 64 B per
+    # instance entry; per closest-hit ray 32 B ray + 4 B queue slot read and a
+    # 16 B hit written; per shadow ray 16 B origin + 4 B slot + 16 B pending
+    # term read and 16 B radiance updated
+    closest_bytes = 64 * c_nodes + 48 * c_quads + 64 * c_insts + (32 + 4 + 16) * c_rays
+    shadow_bytes = 64 * s_nodes + 48 * s_quads + 64 * s_insts + (16 + 4 + 16 + 16) * s_rays
+    frame_bytes = closest_bytes + shadow_bytes + (12 + 48 + 64) * verts + 12 * view.w * view.h
+    rays = c_rays + s_rays
+    staged_ms = sum(v[0] for v in stages.values()) / steps
+    tr_ms, tr_n = stages["trace_closest"]
+    return {"ms": ms, "rays": rays, "paths": view.w * view.h * view.spp, "img": img, "clocks": clk,
+            "stages": stages, "staged_ms": staged_ms,
+            "closest_ms_step": tr_ms / steps, "closest_launches_step": tr_n / steps,
+            "closest_bytes": closest_bytes, "frame_bytes": frame_bytes,
+            "launches_step": sum(v[1] for v in stages.values()) / steps,
+            "counters": {"closest": {"rays": c_rays, "nodes": c_nodes, "quads": c_quads,
+                                     "instance_entries": c_insts, "fp64_retests": c_fb},
+                         "shadow": {"rays": s_rays, "nodes": s_nodes, "quads": s_quads,
+                                    "instance_entries": s_insts, "fp64_retests": s_fb},
+                         "vertices": verts}}
+
+
+def roofline(m, workload, world, hbm, peak_kind, l2_gbs):
+    """Roofline of the dominant kernel (closest-hit trace): its algorithmic
+    bytes per launch over its CUDA-event launch time, against the HBM copy
+    peak (a scene far larger than L2) or the measured L2 read bandwidth (a
+    scene whose hot set stays in L2)."""
+    ms_launch = m["closest_ms_step"] / max(1.0, m["closest_launches_step"])
+    bytes_launch = m["closest_bytes"] / max(1.0, m["closest_launches_step"])
+    achieved = bytes_launch / (ms_launch * 1e-3) / 1e9 if ms_launch > 0 else None
+    traffic, traffic_kernel, traffic_src = recorded_traffic(workload)
+    bound, peak, unit_kind = ("hbm", hbm, f"{peak_kind} hbm_gbs") if workload == "moana" else \
+        ("l2", l2_gbs, "measured here: qrt_read_bandwidth over a 64 MB buffer, 40 sweeps")
+    value = world * m["rays"] / (m["ms"] * 1e-3) / 1e6
+    return {"bound": bound,
+            "kernel": "wave_trace<closest> (closest-hit trace, "
+                      f"{m['closest_launches_step']:.0f} launches per step, "
+                      f"{100 * m['closest_ms_step'] / m['staged_ms']:.1f}% of a step whose stages run in order)",
+            "kernel_timing": "CUDA events around each launch on its stream in a second pass of the same "
+                             "steps with the stages in order (the headline pass overlaps shadow and "
+                             "closest-hit launches on two streams)",
+            "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if achieved else None,
+            "peak_kind": unit_kind + (" (of measured)" if peak_kind == "measured" or bound == "l2"
+                                      else " (of fallback)"),
+            "traffic": traffic, "traffic_kernel": traffic_kernel,
+            "traffic_source": traffic_src or "no ncu capture of the current kernel sources",
+            "algorithmic_bytes_per_launch": bytes_launch,
+            "hbm_gbs": hbm, "hbm_frac": achieved / hbm if achieved else None,
+            "l2_read_gbs": l2_gbs, "l2_frac": achieved / l2_gbs if achieved else None,
+            # loose upper bound: 48 compulsory bytes per ray (32 B ray in,
+            # 16 B hit out) against the HBM copy bandwidth
+            "compulsory_bound_grays_s": hbm / 48.0,
+            "compulsory_frac": (value / 1e3) / (hbm / 48.0),
+            "frame_algorithmic_gbs": m["frame_bytes"] / (m["ms"] * 1e-3) / 1e9}
+
+
+def e2e(scene, view, alb, d_alb, params, tuning, steps, dev):
+    """The metric end to end through the public API with host buffers: every
+    step uploads its albedo from pinned host memory and reads its image
+    back; the upload of step k + 1 runs on a copy stream into a second
+    device buffer while step k renders (double buffering, as a caller
+    feeding a new albedo every frame would)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    h_alb = torch.from_numpy(alb).pin_memory()
+    d_albs = [d_alb, torch.empty_like(d_alb)]
+    imgs = [torch.empty((view.h, view.w, 3), device=dev) for _ in range(2)]
+    h_imgs = [torch.empty((view.h, view.w, 3)).pin_memory() for _ in range(2)]
+    copy_stream = torch.cuda.Stream()
+    uploaded = [torch.cuda.Event() for _ in range(2)]
+    rendered = [torch.cuda.Event() for _ in range(2)]
+
+    def upload(k):
+        b = k % 2
+        copy_stream.wait_event(rendered[b])        # the render that last read buffer b
+        with torch.cuda.stream(copy_stream):
+            d_albs[b].copy_(h_alb, non_blocking=True)
+        uploaded[b].record(copy_stream)
+
+    def steps_(n):
+        upload(0)
+        for k in range(n):
+            if k + 1 < n:
+                upload(k + 1)
+            b = k % 2
+            stream.wait_event(uploaded[b])
+            scene.render([view], d_albs[b], params, outs=[imgs[b]], tuning=tuning)
+            rendered[b].record(stream)
+            h_imgs[b].copy_(imgs[b], non_blocking=True)
+
+    steps_(2)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    steps_(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    del d_albs[1]
+    return ms, int(alb.nbytes), int(view.w * view.h * 3 * 4)
+
+
+def sub_measurement(api, I, args, dev, world, hbm, peak_kind, l2_gbs, extras):
+    """The mid workload measured beside the headline, with the batched-views
+    and adjoint workloads that are defined on the mid scene."""
+    sc, view, params, alb = mid_workload()
+    t0 = time.time()
+    scene = api.Scene(sc)
+    build_s = time.time() - t0
+    d_alb = torch_from(alb, dev)
+    tuning = None
+    if not args.no_tune:
+        from paper_2001_02620_gb300 import autotune
+        tuning = autotune.tune(scene, view, d_alb, params, scene_name="mid")
+    m = measure(scene, view, d_alb, params, tuning, max(5, args.steps // 2), 3, world, dev)
+    out = {"workload": WORKLOADS["mid"], "value": world * m["rays"] / (m["ms"] * 1e-3) / 1e6,
+           "unit": "Mrays/s", "ms_per_step": m["ms"],
+           "path_samples_per_s": world * m["paths"] / (m["ms"] * 1e-3),
+           "rays_per_step": m["rays"], "counters": m["counters"],
+           "roofline": roofline(m, "mid", world, hbm, peak_kind, l2_gbs),
+           "stages_ms_per_step": {k: v[0] / max(5, args.steps // 2) for k, v in m["stages"].items()},
+           "scene_build_s": build_s, "tuning": tuning}
+    if "trace" in extras:
+        out["trace"] = bench_trace(api, scene, view, d_alb, params, dev, tuning)
+    if "batched" in extras:
+        out["batched_vs_plain"] = bench_batched(api, scene, d_alb, dev, tuning)
+        # many small views (32-128 px, 1-4 spp): where one launch per view
+        # leaves the GPU idle between launches and in each launch's tail
+        out["batched_small_vs_plain"] = bench_batched(
+            api, scene, d_alb, dev, tuning,
+            views=I.batched_views(n_views=64, min_log2=5.0, max_log2=7.0, max_spp=4))
+    if "adjoint" in extras:
+        out["adjoint_vs_primal"] = bench_adjoint(api, scene, sc, dev, tuning)
+    if "progressive" in extras:
+        out["progressive"] = bench_progressive(api, scene, view, d_alb, params, dev, tuning)
+    scene.close()
+    return out
+
+
+def torch_from(a, dev):
+    import torch
+    return torch.from_numpy(a).to(dev)
 
 
 def main():
@@ -388,13 +640,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--extras", default="trace,batched,adjoint,progressive,costmap,device_build",
+    ap.add_argument("--extras", default="trace,batched,adjoint,progressive,costmap,device_build,mid",
                     help="comma list of sub-measurements to add (or 'none')")
     ap.add_argument("--res", type=int, default=0,
                     help="override the view side (small profiling captures only)")
     ap.add_argument("--spp", type=int, default=0, help="override spp (profiling only)")
     ap.add_argument("--no-tune", action="store_true", help="library default launch parameters")
-    ap.add_argument("--workload", default="mid", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="moana", choices=sorted(WORKLOADS))
     ap.add_argument("--tlas-builder", type=int, default=0, choices=[0, 1],
                     help="TLAS builder: 0 binned SAH on the host, 1 linear BVH on the device")
     ap.add_argument("--blas-builder", type=int, default=0, choices=[0, 1],
@@ -420,11 +672,9 @@ def main():
     from paper_2001_02620_gb300 import api, inputs as I
     from paper_2001_02620_gb300 import build as B
     B.build()
+    extras = [] if args.extras == "none" else args.extras.split(",")
     t_gen = time.time()
-    if args.workload == "moana":
-        sc, view, params, alb = moana_workload(args.moana_scale)
-    else:
-        sc, view, params, alb = mid_workload()
+    sc, view, params, alb = load_workload(args.workload, args.moana_scale)
     gen_s = time.time() - t_gen
     if args.res:
         view.w = view.h = args.res
@@ -436,170 +686,46 @@ def main():
     scene = api.Scene(sc, build_opts=bopts or None)
     build_s = time.time() - t0
     dev = torch.device("cuda", local)
-    d_alb = torch.from_numpy(alb).to(dev)
-    img = torch.empty((view.h, view.w, 3), device=dev)
-    stream = torch.cuda.current_stream()
+    d_alb = torch_from(alb, dev)
 
     tuning = None
     tune_s = 0.0
     if not args.no_tune:
         from paper_2001_02620_gb300 import autotune
         t0 = time.time()
-        tuning = autotune.tune(scene, view, d_alb, params, scene_name="mid")
+        tuning = autotune.tune(scene, view, d_alb, params, scene_name=args.workload)
         tune_s = time.time() - t0
-
-    def step(stage_times=False):
-        scene.render([view], d_alb, params, outs=[img], tuning=tuning, stage_times=stage_times)
-
-    # counters of one render (same launch configuration, counters added)
-    stats = torch.zeros(STAT_WORDS, dtype=torch.int64, device=dev)
-    scene.render([view], d_alb, params, outs=[img], stats=stats, tuning=tuning)
-    scene.check()
-    st = [int(x) for x in stats.cpu().numpy()]
-    c_rays, c_nodes, c_quads, c_insts, c_fb, verts = st[0:6]
-    s_rays, s_nodes, s_quads, s_insts, s_fb, _ = st[6:12]
-    rays, nodes, quads, insts, fallbacks = (c_rays + s_rays, c_nodes + s_nodes, c_quads + s_quads,
-                                            c_insts + s_insts, c_fb + s_fb)
-    paths = view.w * view.h * view.spp
     # L2 read bandwidth of this GPU (a 64 MB L2-resident buffer swept 40
-    # times with L2-only loads): the second roofline denominator
+    # times with L2-only loads): the roofline denominator of an L2-resident scene
     l2_gbs = api.read_bandwidth_gbs(64 << 20, 40)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    scene.stage_times(reset=True)
-    if world > 1:
-        dist.barrier()
-    clocks = Clocks(local)
-    clocks.start()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    clk = clocks.stop()
-    scene.check()
-    # per-kernel times: the same K steps again with a CUDA event pair around
-    # every stage launch.  A timed render runs its stages in order (the
-    # headline pass above overlaps each depth's shadow rays with the next
-    # depth's closest-hit rays on a second stream), so these are the
-    # kernels' own durations.
-    scene.stage_times(reset=True)
-    for _ in range(args.steps):
-        step(stage_times=True)
-    torch.cuda.synchronize()
-    stages = scene.stage_times(reset=True)
-    staged_ms = sum(v[0] for v in stages.values()) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-
-    # end to end through the public API with host buffers: every step
-    # uploads its albedo from pinned host memory and reads its image back.
-    # The upload of step k + 1 runs on a copy stream into a second device
-    # buffer while step k renders (double buffering, as a caller feeding a
-    # new albedo every frame would do).
-    h_alb = torch.from_numpy(alb).pin_memory()
-    d_albs = [d_alb, torch.empty_like(d_alb)]
-    imgs = [img, torch.empty_like(img)]
-    h_imgs = [torch.empty((view.h, view.w, 3)).pin_memory() for _ in range(2)]
-    copy_stream = torch.cuda.Stream()
-    uploaded = [torch.cuda.Event() for _ in range(2)]
-    rendered = [torch.cuda.Event() for _ in range(2)]
-
-    def upload(k):
-        b = k % 2
-        copy_stream.wait_event(rendered[b])        # the render that last read buffer b
-        with torch.cuda.stream(copy_stream):
-            d_albs[b].copy_(h_alb, non_blocking=True)
-        uploaded[b].record(copy_stream)
-
-    def e2e_steps(n):
-        upload(0)
-        for k in range(n):
-            if k + 1 < n:
-                upload(k + 1)
-            b = k % 2
-            stream.wait_event(uploaded[b])
-            scene.render([view], d_albs[b], params, outs=[imgs[b]], tuning=tuning)
-            rendered[b].record(stream)
-            h_imgs[b].copy_(imgs[b], non_blocking=True)
-
-    e2e_steps(2)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    e2e_steps(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
-
     hbm, peak_kind = peaks()
-    # algorithmic bytes: 64 B per node, 48 B per quad tested, 64 B per instance
-    # entry; per ray of the closest-hit kernel also 32 B ray + 4 B queue slot
-    # read and a 16 B hit written
-    closest_bytes = 64 * c_nodes + 48 * c_quads + 64 * c_insts + (32 + 4 + 16) * c_rays
-    shadow_bytes = 64 * s_nodes + 48 * s_quads + 64 * s_insts + (16 + 4 + 16 + 16) * s_rays
-    frame_bytes = closest_bytes + shadow_bytes + (12 + 48 + 64) * verts + 12 * view.w * view.h
-    tr_ms, tr_n = stages["trace_closest"]
-    tr_ms_step = tr_ms / args.steps
-    launches_step = tr_n / args.steps
-    achieved = closest_bytes / (tr_ms_step * 1e-3) / 1e9 if tr_ms_step > 0 else None
-    traffic, traffic_kernel = recorded_traffic(args.workload)
-    value = world * rays / (ms * 1e-3) / 1e6
+
+    m = measure(scene, view, d_alb, params, tuning, args.steps, args.warmup, world, dev,
+                clocks=Clocks(local))
+    e2e_ms, h2d, d2h = e2e(scene, view, alb, d_alb, params, tuning, args.steps, dev)
+    value = world * m["rays"] / (m["ms"] * 1e-3) / 1e6
     line = {
         "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": m["ms"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload] if args.workload != "moana" or
-                   args.moana_scale == 1.0 else WORKLOADS["moana"] + f" x {args.moana_scale}",
-                   "parallelism": f"replicas{world}",
-                   "tlas_builder": "device linear BVH" if args.tlas_builder else "host binned SAH",
-                   "blas_builder": "device linear BVHs" if args.blas_builder else "host binned SAH",
-                   "l2": f"working set {scene.stats['device_bytes'] / 1e9:.2f} GB > L2 (no flush)"},
-        "path_samples_per_s": world * paths / (ms * 1e-3),
-        "rays_per_step": rays, "paths_per_step": paths,
-        "counters": {"closest": {"rays": c_rays, "nodes": c_nodes, "quads": c_quads,
-                                 "instance_entries": c_insts, "fp64_retests": c_fb},
-                     "shadow": {"rays": s_rays, "nodes": s_nodes, "quads": s_quads,
-                                "instance_entries": s_insts, "fp64_retests": s_fb},
-                     "vertices": verts},
-        "roofline": {"bound": "hbm", "kernel": "wave_trace<closest> (closest-hit trace, "
-                     f"{launches_step:.0f} launches per step, {100 * tr_ms_step / staged_ms:.1f}% of a "
-                     "step whose stages run in order)",
-                     "kernel_timing": "CUDA events around each launch in a second pass of the same "
-                                      "steps with the stages in order (the headline pass overlaps "
-                                      "shadow and closest-hit launches on two streams)",
-                     "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm if achieved else None,
-                     "traffic": traffic, "traffic_kernel": traffic_kernel,
-                     "algorithmic_bytes_per_launch": closest_bytes / max(1.0, launches_step),
-                     "peak_kind": f"{peak_kind} hbm_gbs ({'of measured' if peak_kind == 'measured' else 'of fallback'})",
-                     "l2_read_gbs": l2_gbs, "l2_frac": achieved / l2_gbs if achieved else None,
-                     # loose upper bound: 48 compulsory bytes per ray (32 B ray in,
-                     # 16 B hit out) against the HBM copy bandwidth
-                     "compulsory_bound_grays_s": hbm / 48.0,
-                     "compulsory_frac": (value / 1e3) / (hbm / 48.0),
-                     "l2_kind": "measured here: qrt_read_bandwidth over a 64 MB buffer, 40 sweeps",
-                     "frame_algorithmic_gbs": frame_bytes / (ms * 1e-3) / 1e9},
-        "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
-        "staged_ms_per_step": staged_ms,
-        "e2e": {"value": world * rays / (e2e_ms * 1e-3) / 1e6, "unit": "Mrays/s",
-                "h2d_bytes_per_step": int(alb.nbytes), "d2h_bytes_per_step": int(img.numel() * 4),
-                "ms_per_step": e2e_ms,
+        "config": workload_config(args.workload, args.moana_scale),
+        "setup": {"parallelism": f"replicas{world}",
+                  "tlas_builder": "device linear BVH" if args.tlas_builder else "host binned SAH",
+                  "blas_builder": "device linear BVHs" if args.blas_builder else "host binned SAH",
+                  "device_bytes": scene.stats["device_bytes"],
+                  "view": [view.w, view.h, view.spp, params.max_depth]},
+        "path_samples_per_s": world * m["paths"] / (m["ms"] * 1e-3),
+        "rays_per_step": m["rays"], "paths_per_step": m["paths"],
+        "counters": m["counters"],
+        "roofline": roofline(m, args.workload, world, hbm, peak_kind, l2_gbs),
+        "stages_ms_per_step": {k: v[0] / args.steps for k, v in m["stages"].items()},
+        "staged_ms_per_step": m["staged_ms"],
+        "e2e": {"value": world * m["rays"] / (e2e_ms * 1e-3) / 1e6, "unit": "Mrays/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
                 "pipelining": "step k+1's albedo upload (pinned host -> device, copy stream) "
                               "overlaps step k's render; each image is read back after its render"},
-        "gpu_launches": int(sum(v[1] for v in stages.values())),
-        "clocks": clk,
+        "gpu_launches": int(round(m["launches_step"] * args.steps)),
+        "clocks": m["clocks"],
         "scene_build_s": build_s, "scene_gen_s": gen_s,
         "scene": {k: scene.stats[k] for k in ("n_quads", "n_instances", "blas_nodes", "tlas_nodes",
                                               "device_bytes", "max_blas_depth", "tlas_depth")},
@@ -607,30 +733,36 @@ def main():
                                   scene.stats["phase_seconds"])),
         "tuning": tuning, "tune_s": tune_s,
     }
-    extras = [] if args.extras == "none" else args.extras.split(",")
-    if args.workload != "mid":
-        extras = [e for e in extras if e in ("trace", "progressive", "costmap", "device_build")]
     if "trace" in extras:
-        line["trace"] = bench_trace(scene, sc, dev, tuning, eye=view.eye)
-    if "batched" in extras:
-        line["batched_vs_plain"] = bench_batched(api, scene, d_alb, dev, tuning)
-        # many small views (32-128 px, 1-4 spp): where one launch per view
-        # leaves the GPU idle between launches and in each launch's tail
-        line["batched_small_vs_plain"] = bench_batched(
-            api, scene, d_alb, dev, tuning,
-            views=I.batched_views(n_views=64, min_log2=5.0, max_log2=7.0, max_spp=4))
-    if "adjoint" in extras:
-        line["adjoint_vs_primal"] = bench_adjoint(api, scene, sc, dev, tuning)
+        line["trace"] = bench_trace(api, scene, view, d_alb, params, dev, tuning)
     if "costmap" in extras:
         line["cost_map"] = bench_cost_map(api, scene, view, d_alb, params, dev, tuning)
     if "progressive" in extras:
         line["progressive"] = bench_progressive(api, scene, view, d_alb, params, dev, tuning)
+    if args.workload == "mid":
+        if "batched" in extras:
+            line["batched_vs_plain"] = bench_batched(api, scene, d_alb, dev, tuning)
+            line["batched_small_vs_plain"] = bench_batched(
+                api, scene, d_alb, dev, tuning,
+                views=I.batched_views(n_views=64, min_log2=5.0, max_log2=7.0, max_spp=4))
+        if "adjoint" in extras:
+            line["adjoint_vs_primal"] = bench_adjoint(api, scene, sc, dev, tuning)
     if "device_build" in extras and not (args.tlas_builder or args.blas_builder):
         line["device_build"] = bench_device_build(api, scene, sc, view, d_alb, params, dev, tuning,
-                                                  rays=rays)
+                                                  rays=m["rays"])
+    scene.close()
+    del scene, d_alb
+    torch.cuda.empty_cache()
+    if "mid" in extras and args.workload != "mid":
+        line["mid"] = sub_measurement(api, I, args, dev, world, hbm, peak_kind, l2_gbs, extras)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = oracle_sample(sc, view, params, alb, budget_s=12.0,
-                                             frame=f"{view.w}x{view.h} {args.workload}")
+        import oracle as O
+        t0 = time.time()
+        osc = O.OracleScene(sc)
+        ob = time.time() - t0
+        line["cpu_baseline"] = oracle_sample(osc, view, params, alb, budget_s=12.0,
+                                             frame=f"{view.w}x{view.h} {args.workload}", build_s=ob)
+        del osc
     import resource
     line["host_peak_rss_gb"] = resource.getrusage(resource.RUSAGE_SELF).ru_maxrss / 1e6
     if rank == 0:
