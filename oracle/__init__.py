@@ -45,7 +45,9 @@ class _View(C.Structure):
 
 class _Params(C.Structure):
     _fields_ = [("max_depth", C.c_uint32), ("seed", C.c_uint64), ("env", C.c_float * 3),
-                ("sun_dir", C.c_float * 3), ("sun_E", C.c_float * 3)]
+                ("sun_dir", C.c_float * 3), ("sun_E", C.c_float * 3), ("tex_res", C.c_uint32),
+                ("tex", C.POINTER(C.c_float)), ("n_lights", C.c_uint32),
+                ("lights", C.POINTER(C.c_float))]
 
 
 def _p(a, ct):
@@ -78,7 +80,10 @@ def lib():
             L.ora_render.restype = C.c_int
             L.ora_render.argtypes = [C.c_void_p, C.POINTER(_View), f32p, C.POINTER(_Params),
                                      C.POINTER(C.c_int64), C.c_uint64, f64p, u32p, u32p, u32p,
-                                     f64p, u64p, u64p, C.c_int]
+                                     u32p, f64p, u64p, u64p, C.c_int]
+            L.ora_tex_lookup.argtypes = [f32p, C.c_uint32, C.c_uint64, C.c_double, C.c_double, f64p]
+            L.ora_light_sample.restype = C.c_int
+            L.ora_light_sample.argtypes = [f32p, C.c_uint32, f64p, f64p, f64p, f64p, f64p, f64p]
             L.ora_render_grad.restype = C.c_int
             L.ora_render_grad.argtypes = [C.c_void_p, C.POINTER(_View), f32p, C.POINTER(_Params),
                                           C.POINTER(C.c_int64), C.c_uint64, f64p, f64p, C.c_int]
@@ -123,14 +128,50 @@ def _view(v) -> _View:
     return cv
 
 
-def _params(p) -> _Params:
+def _params(p):
+    """(ctypes params, arrays to keep alive)."""
     cp = _Params()
     cp.max_depth = int(p.max_depth)
     cp.seed = int(p.seed)
     cp.env[:] = [float(x) for x in p.env]
     cp.sun_dir[:] = [float(x) for x in p.sun_dir]
     cp.sun_E[:] = [float(x) for x in p.sun_E]
-    return cp
+    keep = []
+    tex = getattr(p, "tex", None)
+    if tex is not None:
+        t = np.ascontiguousarray(tex, dtype=np.float32)
+        keep.append(t)
+        cp.tex_res = int(t.shape[1])
+        cp.tex = _p(t, C.c_float)
+    lights = getattr(p, "lights", None)
+    if lights is not None and len(lights):
+        lt = np.ascontiguousarray(lights, dtype=np.float32).reshape(-1, 12)
+        keep.append(lt)
+        cp.n_lights = int(lt.shape[0])
+        cp.lights = _p(lt, C.c_float)
+    return cp, keep
+
+
+def tex_lookup(tex, row, u, v) -> np.ndarray:
+    t = np.ascontiguousarray(tex, dtype=np.float32)
+    out = np.zeros(3)
+    lib().ora_tex_lookup(_p(t, C.c_float), int(t.shape[1]), int(row), float(u), float(v),
+                         _p(out, C.c_double))
+    return out
+
+
+def light_sample(lights, xi, x, nx):
+    """(hit, unit direction, distance, estimator [3]) of one key-light sample."""
+    lt = np.ascontiguousarray(lights, dtype=np.float32).reshape(-1, 12)
+    xi = np.ascontiguousarray(xi, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    nx = np.ascontiguousarray(nx, dtype=np.float64)
+    d = np.zeros(3)
+    w = np.zeros(3)
+    dist = C.c_double()
+    ok = lib().ora_light_sample(_p(lt, C.c_float), lt.shape[0], _p(xi, C.c_double), _p(x, C.c_double),
+                                _p(nx, C.c_double), _p(d, C.c_double), C.byref(dist), _p(w, C.c_double))
+    return bool(ok), d, dist.value, w
 
 
 def camera_ray(view, x, y, xi1, xi2):
@@ -198,9 +239,12 @@ class OracleScene:
                rays: bool = False):
         """Returns dict(rgb=[n_pix,3] f64, escaped, truncated[, inst, prim, shadow][, rays]).
         pixels: frame pixel indices y*w + x (None = the whole frame in order).
-        rays=True adds rays [n_paths, max_depth, 9]: per depth the origin and
-        direction of the closest-hit ray traced there and the origin of the
-        shadow ray traced from its hit (zeros where there was none)."""
+        rays=True adds rays [n_paths, max_depth, 13]: per depth the origin and
+        direction of the closest-hit ray traced there, the spawn point of its
+        hit (origin of its shadow rays) and the direction and distance of the
+        key-light shadow ray (zeros where there was none).  params may carry
+        tex (float [n_quads, R, R, 3] per-face textures) and lights (float
+        [n, 12] key lights)."""
         a = np.ascontiguousarray(albedo, dtype=np.float32).reshape(-1, 3)
         assert a.shape[0] == self.n_quads
         if pixels is None:
@@ -212,25 +256,29 @@ class OracleScene:
         rgb = np.zeros((n_pix, 3))
         D = int(params.max_depth)
         n_paths = n_pix * int(view.spp)
-        li = lp = ls = lr = None
+        li = lp = ls = ll = lr = None
         if rays:
-            lr = np.zeros((n_paths, D, 9))
+            lr = np.zeros((n_paths, D, 13))
         if log:
             li = np.zeros((n_paths, D), dtype=np.uint32)
             lp = np.zeros((n_paths, D), dtype=np.uint32)
             ls = np.zeros(n_paths, dtype=np.uint32)
+            ll = np.zeros(n_paths, dtype=np.uint32)
         esc = C.c_uint64()
         tr = C.c_uint64()
-        cv, cp = _view(view), _params(params)
+        cv = _view(view)
+        cp, keep = _params(params)
         rc = lib().ora_render(self._h, C.byref(cv), _p(a, C.c_float), C.byref(cp),
                               _p(px, C.c_int64), n_pix, _p(rgb, C.c_double),
                               _p(li, C.c_uint32), _p(lp, C.c_uint32), _p(ls, C.c_uint32),
-                              _p(lr, C.c_double), C.byref(esc), C.byref(tr), nthreads)
+                              _p(ll, C.c_uint32), _p(lr, C.c_double), C.byref(esc), C.byref(tr),
+                              nthreads)
+        del keep
         if rc != 0:
             raise ValueError(f"ora_render failed ({rc})")
         out = dict(rgb=rgb, escaped=esc.value, truncated=tr.value)
         if log:
-            out.update(inst=li, prim=lp, shadow=ls)
+            out.update(inst=li, prim=lp, shadow=ls, light=ll)
         if rays:
             out["rays"] = lr
         return out
@@ -242,10 +290,12 @@ class OracleScene:
         n_pix = int(view.w) * int(view.h) if px is None else px.shape[0]
         dimg = np.ascontiguousarray(dimage, dtype=np.float64).reshape(n_pix, 3)
         g = np.zeros((self.n_quads, 3))
-        cv, cp = _view(view), _params(params)
+        cv = _view(view)
+        cp, keep = _params(params)
         rc = lib().ora_render_grad(self._h, C.byref(cv), _p(a, C.c_float), C.byref(cp),
                                    _p(px, C.c_int64), n_pix, _p(dimg, C.c_double),
                                    _p(g, C.c_double), nthreads)
+        del keep
         if rc != 0:
             raise ValueError(f"ora_render_grad failed ({rc})")
         return g

@@ -538,8 +538,69 @@ V3 spawn_point(V3 p, V3 n) {
 
 struct PathVertex {
     uint64_t albedo_row;
-    double nee[3];  // E * cos / pi, zero if occluded or no sun
+    double tex[3];  // texture factor of the diffuse albedo at the hit (1 without textures)
+    double nee[3];  // light arriving by next-event estimation, over pi (sun and key light)
 };
+
+// Per-face texture (the stand-in for a Ptex texture: a texel grid baked on
+// each face, looked up by face id and the hit's position on the face): quad
+// row's R x R RGB texels (row-major in v, then u) cover quad-space
+// [i/R, (i+1)/R] x [j/R, (j+1)/R]; the value at (u, v) is bilinear between
+// texel centres, clamped to the face.
+void tex_lookup(const float* tex, uint32_t R, uint64_t row, double u, double v, double out[3]) {
+    const double s = std::min(std::max(u * R - 0.5, 0.0), (double)(R - 1));
+    const double t = std::min(std::max(v * R - 0.5, 0.0), (double)(R - 1));
+    const uint32_t i0 = (uint32_t)std::floor(s), j0 = (uint32_t)std::floor(t);
+    const uint32_t i1 = std::min(i0 + 1, R - 1), j1 = std::min(j0 + 1, R - 1);
+    const double fs = s - i0, ft = t - j0;
+    const float* T = tex + row * R * R * 3;
+    for (int c = 0; c < 3; ++c)
+        out[c] = (1.0 - fs) * (1.0 - ft) * T[3 * (j0 * R + i0) + c] + fs * (1.0 - ft) * T[3 * (j0 * R + i1) + c] +
+                 (1.0 - fs) * ft * T[3 * (j1 * R + i0) + c] + fs * ft * T[3 * (j1 * R + i1) + c];
+}
+
+// One sample of the key lights seen from x with unit normal nx.  Light k
+// (corner c, edges e1, e2, radiance Le; 12 floats) is a parallelogram
+// emitting on the side of e1 x e2.  xi picks a light uniformly and a point
+// uniformly on it; the estimator of the light arriving at x is
+// Le cos_x cos_l |e1 x e2| n / d^2 (n lights).  Writes the unit direction
+// toward the point, its distance and that estimator; false when the point
+// faces away from x or lies below x's horizon.
+bool light_sample(const float* lights, uint32_t n, const double xi[3], V3 x, V3 nx, V3* dir,
+                  double* dist, double w[3]) {
+    const uint32_t k = std::min((uint32_t)(xi[0] * n), n - 1);
+    const float* Lk = lights + 12 * (size_t)k;
+    const V3 c = mk(Lk[0], Lk[1], Lk[2]), e1 = mk(Lk[3], Lk[4], Lk[5]), e2 = mk(Lk[6], Lk[7], Lk[8]);
+    const V3 y = c + xi[1] * e1 + xi[2] * e2;
+    const V3 q = y - x;
+    const double d2 = dot(q, q);
+    if (!(d2 > 0.0)) return false;
+    const double d = std::sqrt(d2);
+    const V3 om = (1.0 / d) * q;
+    const V3 cr = cross(e1, e2);
+    const double A = std::sqrt(dot(cr, cr));
+    if (!(A > 0.0)) return false;
+    const double cx = dot(nx, om), cl = -dot(cr, om) / A;
+    if (!(cx > 0.0) || !(cl > 0.0)) return false;
+    const double g = cx * cl * A * (double)n / d2;
+    for (int ch = 0; ch < 3; ++ch) w[ch] = Lk[9 + ch] * g;
+    *dir = om;
+    *dist = d;
+    return true;
+}
+
+// Philox counter word of the key-light sample drawn at bounce i.
+const uint32_t kLightStream = 0x40000000u;
+
+// Optional per-path logs of trace_path.
+struct PathLogs {
+    uint32_t* inst = nullptr;   // max_depth hit instances
+    uint32_t* prim = nullptr;   // max_depth hit quads
+    uint32_t* shadow = nullptr; // sun shadow bits
+    uint32_t* light = nullptr;  // key-light shadow bits
+    double* rays = nullptr;     // max_depth records of kRayRec doubles
+};
+const int kRayRec = 13;  // ray origin, direction; spawn point; light direction, distance
 
 struct PathRecord {
     std::vector<PathVertex> verts;
@@ -550,8 +611,11 @@ struct PathRecord {
 // (with the given albedo) and its record.
 void trace_path(const ora_scene& s, const ora_view& view, const float* albedo,
                 const ora_params& p, uint32_t x, uint32_t y, uint32_t k, double L[3],
-                PathRecord* rec, uint32_t* log_inst, uint32_t* log_prim, uint32_t* log_shadow,
-                double* log_rays) {
+                PathRecord* rec, const PathLogs& lg) {
+    uint32_t* log_inst = lg.inst;
+    uint32_t* log_prim = lg.prim;
+    uint32_t* log_shadow = lg.shadow;
+    double* log_rays = lg.rays;
     const uint64_t pix = view.pixel_base + (uint64_t)y * view.w + x;
     const uint32_t smp = view.sample_base + k;  // Philox counter: (pixel, sample, bounce)
     double xi[4];
@@ -562,15 +626,16 @@ void trace_path(const ora_scene& s, const ora_view& view, const float* albedo,
     L[0] = L[1] = L[2] = 0.0;
     const bool sun = p.sun_E[0] != 0.0f || p.sun_E[1] != 0.0f || p.sun_E[2] != 0.0f;
     V3 l = normalize(mk(p.sun_dir[0], p.sun_dir[1], p.sun_dir[2]));
-    uint32_t shadow_bits = 0;
+    uint32_t shadow_bits = 0, light_bits = 0;
     if (rec) {
         rec->verts.clear();
         rec->escaped = false;
     }
     for (uint32_t i = 1; i <= p.max_depth; ++i) {
         if (log_rays) {
-            // the ray traced at depth i: origin, direction (shadow origin below)
-            double* r = log_rays + 9 * (i - 1);
+            // the ray traced at depth i: origin, direction (spawn point and
+            // key-light sample below)
+            double* r = log_rays + kRayRec * (i - 1);
             r[0] = o.x, r[1] = o.y, r[2] = o.z, r[3] = d.x, r[4] = d.y, r[5] = d.z;
         }
         HitRec h = closest(s, o, d, 0.0, kInf, 0);
@@ -585,20 +650,23 @@ void trace_path(const ora_scene& s, const ora_view& view, const float* albedo,
         }
         const Instance& I = s.inst[h.inst];
         uint64_t row = s.meshes[I.mesh].albedo_base + h.prim;
-        double a[3] = {albedo[3 * row], albedo[3 * row + 1], albedo[3 * row + 2]};
+        PathVertex pv{row, {1.0, 1.0, 1.0}, {0.0, 0.0, 0.0}};
+        if (p.tex_res > 0) tex_lookup(p.tex, p.tex_res, row, h.u, h.v, pv.tex);
+        // diffuse albedo: the quad's albedo modulated by its texture
+        double a[3];
+        for (int c = 0; c < 3; ++c) a[c] = albedo[3 * row + c] * pv.tex[c];
         V3 n = world_normal(s, h.inst, h.prim);
         if (dot(n, d) > 0.0) n = -1.0 * n;
         V3 hp = o + h.t * d;
         V3 sp = spawn_point(hp, n);
-        PathVertex pv{row, {0.0, 0.0, 0.0}};
+        if (log_rays) {
+            double* r = log_rays + kRayRec * (i - 1) + 6;
+            r[0] = sp.x, r[1] = sp.y, r[2] = sp.z;
+        }
         if (sun) {
             double cl = dot(n, l);
             if (cl > 0.0) {
                 if (i <= 16) shadow_bits |= 1u << (2 * (i - 1));
-                if (log_rays) {
-                    double* r = log_rays + 9 * (i - 1) + 6;
-                    r[0] = sp.x, r[1] = sp.y, r[2] = sp.z;
-                }
                 bool occ = any_hit(s, sp, l, 0.0, kInf, 0);
                 if (occ) {
                     if (i <= 16) shadow_bits |= 2u << (2 * (i - 1));
@@ -606,6 +674,26 @@ void trace_path(const ora_scene& s, const ora_view& view, const float* albedo,
                     for (int c = 0; c < 3; ++c) {
                         pv.nee[c] = p.sun_E[c] * cl / kPi;
                         L[c] += beta[c] * a[c] * pv.nee[c];
+                    }
+                }
+            }
+        }
+        if (p.n_lights > 0) {
+            double xl[4], w[3], dist;
+            V3 ld;
+            draw4(p.seed, pix, smp, kLightStream + i, xl);
+            if (light_sample(p.lights, p.n_lights, xl, sp, n, &ld, &dist, w)) {
+                if (i <= 16) light_bits |= 1u << (2 * (i - 1));
+                if (log_rays) {
+                    double* r = log_rays + kRayRec * (i - 1) + 9;
+                    r[0] = ld.x, r[1] = ld.y, r[2] = ld.z, r[3] = dist;
+                }
+                if (any_hit(s, sp, ld, 0.0, dist, 0)) {
+                    if (i <= 16) light_bits |= 2u << (2 * (i - 1));
+                } else {
+                    for (int c = 0; c < 3; ++c) {
+                        pv.nee[c] += w[c] / kPi;
+                        L[c] += beta[c] * a[c] * (w[c] / kPi);
                     }
                 }
             }
@@ -618,6 +706,7 @@ void trace_path(const ora_scene& s, const ora_view& view, const float* albedo,
         o = sp;
     }
     if (log_shadow) *log_shadow = shadow_bits;
+    if (lg.light) *lg.light = light_bits;
 }
 
 }  // namespace
@@ -733,6 +822,20 @@ void ora_camera_ray(const ora_view* v, uint32_t x, uint32_t y, double xi1, doubl
     d[2] = dd.z;
 }
 
+void ora_tex_lookup(const float* tex, uint32_t res, uint64_t row, double u, double v, double out[3]) {
+    tex_lookup(tex, res, row, u, v, out);
+}
+
+int ora_light_sample(const float* lights, uint32_t n, const double xi[3], const double x[3],
+                     const double nx[3], double dir[3], double* dist, double w[3]) {
+    V3 d;
+    if (!light_sample(lights, n, xi, mk(x[0], x[1], x[2]), mk(nx[0], nx[1], nx[2]), &d, dist, w)) return 0;
+    dir[0] = d.x;
+    dir[1] = d.y;
+    dir[2] = d.z;
+    return 1;
+}
+
 void ora_sample_cosine(const double n[3], double xi1, double xi2, double out[3]) {
     V3 r = sample_cosine(mk(n[0], n[1], n[2]), xi1, xi2);
     out[0] = r.x;
@@ -742,9 +845,10 @@ void ora_sample_cosine(const double n[3], double xi1, double xi2, double out[3])
 
 int ora_render(const ora_scene* s, const ora_view* view, const float* albedo,
                const ora_params* p, const int64_t* pixels, uint64_t n_pix, double* rgb,
-               uint32_t* log_inst, uint32_t* log_prim, uint32_t* log_shadow, double* log_rays,
-               uint64_t* n_escaped, uint64_t* n_truncated, int nthreads) {
+               uint32_t* log_inst, uint32_t* log_prim, uint32_t* log_shadow, uint32_t* log_light,
+               double* log_rays, uint64_t* n_escaped, uint64_t* n_truncated, int nthreads) {
     if (p->max_depth == 0 || p->max_depth > 256) return -1;
+    if ((p->tex_res > 0 && !p->tex) || (p->n_lights > 0 && !p->lights)) return -1;
     std::atomic<uint64_t> esc{0}, trunc{0};
     const uint32_t D = p->max_depth, spp = view->spp;
     parallel_for(n_pix, nthreads, [&](uint64_t k) {
@@ -755,11 +859,13 @@ int ora_render(const ora_scene* s, const ora_view* view, const float* albedo,
         for (uint32_t smp = 0; smp < spp; ++smp) {
             uint64_t path = k * spp + smp;
             double L[3];
-            trace_path(*s, *view, albedo, *p, x, y, smp, L, &rec,
-                       log_inst ? log_inst + path * D : nullptr,
-                       log_prim ? log_prim + path * D : nullptr,
-                       log_shadow ? log_shadow + path : nullptr,
-                       log_rays ? log_rays + path * D * 9 : nullptr);
+            PathLogs lg;
+            lg.inst = log_inst ? log_inst + path * D : nullptr;
+            lg.prim = log_prim ? log_prim + path * D : nullptr;
+            lg.shadow = log_shadow ? log_shadow + path : nullptr;
+            lg.light = log_light ? log_light + path : nullptr;
+            lg.rays = log_rays ? log_rays + path * D * kRayRec : nullptr;
+            trace_path(*s, *view, albedo, *p, x, y, smp, L, &rec, lg);
             if (log_inst) {
                 for (uint32_t i = (uint32_t)rec.verts.size() + (rec.escaped ? 1 : 0); i < D; ++i) {
                     log_inst[path * D + i] = kNone;
@@ -783,6 +889,7 @@ int ora_render_grad(const ora_scene* s, const ora_view* view, const float* albed
                     const ora_params* p, const int64_t* pixels, uint64_t n_pix,
                     const double* dimage, double* grad, int nthreads) {
     if (p->max_depth == 0 || p->max_depth > 256) return -1;
+    if ((p->tex_res > 0 && !p->tex) || (p->n_lights > 0 && !p->lights)) return -1;
     if (nthreads <= 0) nthreads = (int)std::max(1u, std::thread::hardware_concurrency());
     // Per-thread sparse (row, channel, value) lists, summed at the end.
     struct Entry {
@@ -799,23 +906,25 @@ int ora_render_grad(const ora_scene* s, const ora_view* view, const float* albed
         std::vector<Entry>& out = parts[k];
         for (uint32_t smp = 0; smp < spp; ++smp) {
             double L[3];
-            trace_path(*s, *view, albedo, *p, x, y, smp, L, &rec, nullptr, nullptr, nullptr, nullptr);
+            trace_path(*s, *view, albedo, *p, x, y, smp, L, &rec, PathLogs{});
             const size_t m = rec.verts.size();
             for (int c = 0; c < 3; ++c) {
                 double w = dimage[3 * k + c] / (double)spp;
                 if (w == 0.0) continue;
                 std::vector<double> a(m);
-                for (size_t j = 0; j < m; ++j) a[j] = albedo[3 * rec.verts[j].albedo_row + c];
+                for (size_t j = 0; j < m; ++j)
+                    a[j] = albedo[3 * rec.verts[j].albedo_row + c] * rec.verts[j].tex[c];
                 // Monomials: for each vertex k (1-based) the NEE term
-                // (prod_{j<=k} a_j) * nee_k; if the path escaped after its last
-                // vertex, the term (prod_{j<=m} a_j) * env.  Differentiate each
-                // monomial by each of its factors.
+                // (prod_{j<=k} a_j t_j) * nee_k, a_j the quad albedo and t_j its
+                // texture factor; if the path escaped after its last vertex,
+                // the term (prod_{j<=m} a_j t_j) * env.  Differentiate each
+                // monomial by each of its albedo factors (d(a_j t_j)/da_j = t_j).
                 for (size_t kk = 1; kk <= m; ++kk) {
                     double coef = rec.verts[kk - 1].nee[c];
                     if (kk == m && rec.escaped) coef += p->env[c];
                     if (coef == 0.0) continue;
                     for (size_t j = 0; j < kk; ++j) {
-                        double prod = coef;
+                        double prod = coef * rec.verts[j].tex[c];
                         for (size_t l = 0; l < kk; ++l)
                             if (l != j) prod *= a[l];
                         out.push_back(Entry{rec.verts[j].albedo_row, c, w * prod});

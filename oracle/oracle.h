@@ -32,6 +32,12 @@
  *   ora_render_grad       pinned: closed form on a flat plane, central
  *                         finite differences of ora_render.
  *   ora_camera_ray        pinned: centre and corner rays in closed form.
+ *   ora_tex_lookup        pinned: constant and linear texel grids reproduced
+ *                         exactly, clamping at the face's edges.
+ *   ora_light_sample      pinned: the mean over samples converges to the
+ *                         closed-form irradiance of a Lambertian polygon
+ *                         (Lambert's formula); lights facing away or below
+ *                         the horizon give nothing.
  */
 #ifndef QRT_ORACLE_H
 #define QRT_ORACLE_H
@@ -57,6 +63,10 @@ typedef struct {
     float env[3];
     float sun_dir[3];
     float sun_E[3];
+    uint32_t tex_res;     /* per-face textures: R x R texels per quad (0 = none) */
+    const float* tex;     /* n_quads x R x R x 3, per quad row-major in v then u */
+    uint32_t n_lights;    /* key lights (0 = none) */
+    const float* lights;  /* n_lights x 12: corner, edge1, edge2, radiance */
 } ora_params;
 
 /* Philox4x32-10: out = philox(ctr, key). */
@@ -95,18 +105,33 @@ void ora_sample_cosine(const double n[3], double xi1, double xi2, double out[3])
  * order).  rgb: n_pix x 3 doubles (mean over spp).  If log_inst/log_prim are
  * non-NULL they receive, per path (pixel-major, then sample), max_depth
  * entries of the hit instance / quad (0xFFFFFFFF = no hit); log_shadow gets
- * per path 2 bits per vertex for the first 16 vertices: bit 2i = shadow ray
- * traced at vertex i, bit 2i+1 = it was occluded.  max_depth is 1..256.
+ * per path 2 bits per vertex for the first 16 vertices: bit 2i = sun shadow
+ * ray traced at vertex i, bit 2i+1 = it was occluded; log_light the same
+ * for the key-light shadow ray.  max_depth is 1..256.
  * log_rays (nullable, zeroed by the caller) receives per path max_depth
- * records of 9 doubles: origin and direction of the closest-hit ray traced
- * at that depth, then the origin of the shadow ray traced from its hit
- * (records of rays not traced stay as given).  n_escaped/n_truncated
- * (nullable) count paths that left the scene / ran out of depth on a
- * surface. */
+ * records of 13 doubles: origin and direction of the closest-hit ray traced
+ * at that depth, the spawn point of its hit (origin of its shadow rays and
+ * of the next ray), and the unit direction and distance of the key-light
+ * shadow ray (records of rays not traced stay as given).
+ * n_escaped/n_truncated (nullable) count paths that left the scene / ran
+ * out of depth on a surface.  Returns -1 for a bad depth or a missing
+ * texture or light array. */
 int ora_render(const ora_scene* s, const ora_view* view, const float* albedo,
                const ora_params* p, const int64_t* pixels, uint64_t n_pix,
                double* rgb, uint32_t* log_inst, uint32_t* log_prim, uint32_t* log_shadow,
-               double* log_rays, uint64_t* n_escaped, uint64_t* n_truncated, int nthreads);
+               uint32_t* log_light, double* log_rays, uint64_t* n_escaped,
+               uint64_t* n_truncated, int nthreads);
+
+/* Per-face texture value of quad row at quad-space (u, v): bilinear between
+ * texel centres of its res x res grid, clamped to the face. */
+void ora_tex_lookup(const float* tex, uint32_t res, uint64_t row, double u, double v, double out[3]);
+
+/* One key-light sample seen from x (unit normal nx) for uniforms xi[3]:
+ * returns 1 and writes the unit direction toward the sampled point, its
+ * distance and the estimator Le cos_x cos_l area n / d^2, or returns 0 when
+ * the point faces away or lies below the horizon. */
+int ora_light_sample(const float* lights, uint32_t n, const double xi[3], const double x[3],
+                     const double nx[3], double dir[3], double* dist, double w[3]);
 
 /* Gradient of sum_p sum_c dimage[p,c] * I[p,c] with respect to the per-quad
  * albedo (n_quads x 3), accumulated into grad (doubles, zeroed by caller),

@@ -36,6 +36,8 @@ SEED_ALBEDO = 3
 SEED_RENDER = 4
 SEED_VIEWS = 5
 SEED_TARGET = 6
+SEED_TEXTURE = 7
+SEED_LIGHTS = 8
 
 
 @dataclass
@@ -97,6 +99,11 @@ class Params:
     env: tuple = (1.0, 1.0, 1.0)
     sun_dir: tuple = (0.0, 0.0, 1.0)
     sun_E: tuple = (0.0, 0.0, 0.0)
+    # per-face textures, float [n_quads, R, R, 3] (the renderer's copy lives
+    # on its device), and key lights, float [n, 12] (corner, edge1, edge2,
+    # radiance per parallelogram); None = off
+    tex: object = None
+    lights: object = None
 
     @property
     def sun_on(self) -> bool:
@@ -407,6 +414,44 @@ def adjoint_view() -> View:
 
 def adjoint_params() -> Params:
     return mid_params(max_depth=4)
+
+
+def face_textures(n_quads: int, res: int = 4, seed: int = SEED_TEXTURE, lo: float = 0.4,
+                  hi: float = 1.0) -> np.ndarray:
+    """Per-face texel grids standing in for Ptex textures (a texture baked on
+    each face, modulating the diffuse albedo): res x res RGB texels per quad,
+    U(lo, hi), float [n_quads, res, res, 3]."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(lo, hi, size=(n_quads, res, res, 3)).astype(np.float32)
+
+
+def key_lights(n: int, lo, hi, size, height: float, radiance, seed: int = SEED_LIGHTS) -> np.ndarray:
+    """n square key lights facing down (parallelograms emitting toward -z),
+    side `size`, centres uniform over the box [lo, hi] of xy at z = height,
+    spun about z; radiance RGB scaled by U(0.5, 1.5).  float [n, 12]:
+    corner, edge1, edge2, radiance."""
+    rng = np.random.default_rng(seed)
+    out = np.zeros((n, 12), dtype=np.float32)
+    for k in range(n):
+        cx, cy = rng.uniform(lo[0], hi[0]), rng.uniform(lo[1], hi[1])
+        phi = rng.uniform(0.0, 2.0 * math.pi)
+        e1 = size * np.array([math.cos(phi), math.sin(phi), 0.0])
+        e2 = size * np.array([math.sin(phi), -math.cos(phi), 0.0])   # e1 x e2 points down
+        c = np.array([cx, cy, height]) - 0.5 * (e1 + e2)
+        out[k, 0:3], out[k, 3:6], out[k, 6:9] = c, e1, e2
+        out[k, 9:12] = np.asarray(radiance, dtype=np.float64) * rng.uniform(0.5, 1.5)
+    return out
+
+
+def tiny_lights() -> np.ndarray:
+    """Four key lights above the tiny scene's 100^3 box."""
+    return key_lights(4, (10.0, 10.0), (90.0, 90.0), 15.0, 130.0, (30.0, 27.0, 22.0))
+
+
+def mid_lights() -> np.ndarray:
+    """The 23 key lights of the paper's Moana scene (Section 4.1), as squares
+    of side 120 at height 600 over the mid terrain."""
+    return key_lights(23, (300.0, 300.0), (3800.0, 3800.0), 120.0, 600.0, (60.0, 55.0, 45.0))
 
 
 def perturbed_albedo(a: np.ndarray, seed: int = SEED_TARGET, sigma: float = 0.05) -> np.ndarray:

@@ -3,6 +3,7 @@ itself (a closed form, an external implementation, brute force, or an
 invariant of the method) so that a dropped term, a wrong sign or index, or a
 transposed operand fails at least one of them.  CPU only.
 """
+import dataclasses
 import math
 import os
 import subprocess
@@ -428,9 +429,10 @@ def test_ray_log_follows_the_paths():
     """The oracle's ray log (used to explain divergent GPU paths) records the
     rays its paths trace: depth 1 is the camera ray from the eye; each
     logged hit lies on its logged ray (the quad's FP64 intersection); the
-    next ray starts at the spawn point of that hit, p + (1e-4 + 1e-5 max|p|) n
-    with n the quad's world normal faced against the ray, which is also the
-    origin of the hit's shadow ray; rays not traced are left zero."""
+    spawn point of that hit, p + (1e-4 + 1e-5 max|p|) n with n the quad's
+    world normal faced against the ray, is logged and starts the next ray;
+    a key-light shadow ray leaves it toward a point of one of the lights;
+    rays not traced are left zero."""
     import sys
     sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
     from parity import NONE, world_normal, world_quad
@@ -438,14 +440,16 @@ def test_ray_log_follows_the_paths():
     osc = O.OracleScene(sc)
     view = I.tiny_view()
     view.w, view.h, view.spp = 40, 30, 2
-    p = I.Params(max_depth=4, sun_dir=I.MID_SUN_DIR, sun_E=(3.0, 3.0, 3.0))
+    lights = I.tiny_lights()
+    p = I.Params(max_depth=4, sun_dir=I.MID_SUN_DIR, sun_E=(3.0, 3.0, 3.0), lights=lights)
     r = osc.render(view, I.albedo(sc.n_quads), p, log=True, rays=True)
     R = r["rays"]
-    assert R.shape == (40 * 30 * 2, 4, 9)
+    assert R.shape == (40 * 30 * 2, 4, 13)
     np.testing.assert_array_equal(R[:, 0, 0:3], np.broadcast_to(np.array(view.eye, float), (2400, 3)))
     np.testing.assert_allclose(np.linalg.norm(R[:, 0, 3:6], axis=1), 1.0, rtol=1e-14)
     l = np.array(I.MID_SUN_DIR, float) / np.linalg.norm(I.MID_SUN_DIR)
-    checked = shadows = 0
+    L64 = lights.astype(np.float64)
+    checked = shadows = lit = 0
     for k in range(2400):
         for i in range(4):
             inst, prim = r["inst"][k, i], r["prim"][k, i]
@@ -460,19 +464,223 @@ def test_ray_log_follows_the_paths():
                 n = -n
             hp = o + t * d
             sp = hp + (1e-4 + 1e-5 * np.abs(hp).max()) * n
-            traced = (r["shadow"][k] >> (2 * i)) & 1
-            if traced:
-                np.testing.assert_allclose(R[k, i, 6:9], sp, rtol=1e-12, atol=1e-12)
+            np.testing.assert_allclose(R[k, i, 6:9], sp, rtol=1e-12, atol=1e-12)
+            if (r["shadow"][k] >> (2 * i)) & 1:
                 assert n @ l > 0
                 shadows += 1
+            if (r["light"][k] >> (2 * i)) & 1:
+                ld, dist = R[k, i, 9:12], R[k, i, 12]
+                assert abs(np.linalg.norm(ld) - 1.0) < 1e-12 and dist > 0 and ld @ n > 0
+                y = sp + dist * ld
+                on = False
+                for L in L64:
+                    A = np.stack([L[3:6], L[6:9]], 1)
+                    st, res, _, _ = np.linalg.lstsq(A, y - L[0:3], rcond=None)
+                    if np.abs(A @ st - (y - L[0:3])).max() < 1e-9 and (st > -1e-9).all() and (st < 1 + 1e-9).all():
+                        on = True
+                assert on
+                lit += 1
             else:
-                assert (R[k, i, 6:9] == 0).all()
+                assert (R[k, i, 9:13] == 0).all()
             if i + 1 < 4:
                 np.testing.assert_allclose(R[k, i + 1, 0:3], sp, rtol=1e-12, atol=1e-12)
                 np.testing.assert_allclose(np.linalg.norm(R[k, i + 1, 3:6]), 1.0, rtol=1e-12)
                 assert R[k, i + 1, 3:6] @ n > 0  # leaves on the faced side
             checked += 1
-    assert checked > 200 and shadows > 20
+    assert checked > 200 and shadows > 20 and lit > 20
+
+
+# --------------------------------------------------------------------------
+# Per-face textures and key lights (the richer shading of the paper's scene:
+# Ptex textures modulating the diffuse albedo, Section 5.3; quad-shaped key
+# lights, Section 4.1)
+# --------------------------------------------------------------------------
+def test_tex_lookup_closed_forms():
+    """Bilinear lookup between texel centres, clamped to the face: constant
+    and linear texel grids are reproduced exactly; texel centres return the
+    texel; outside the centre square the value is the edge's."""
+    R = 4
+    rng = np.random.default_rng(61)
+    tex = rng.uniform(0.2, 1.0, size=(5, R, R, 3)).astype(np.float32)
+    # constant grid on quad 2
+    tex[2] = np.float32(0.625)
+    for u, v in rng.uniform(0.0, 1.0, size=(20, 2)):
+        np.testing.assert_allclose(O.tex_lookup(tex, 2, u, v), 0.625, rtol=1e-15)
+    # texel centres of quad 3
+    for j in range(R):
+        for i in range(R):
+            np.testing.assert_allclose(O.tex_lookup(tex, 3, (i + 0.5) / R, (j + 0.5) / R),
+                                       tex[3, j, i].astype(np.float64), rtol=1e-15)
+    # linear grid on quad 4: a + b u + c v at the texel centres
+    a, b, c = 0.25, 0.5, 0.125     # exact in FP32
+    cu = (np.arange(R) + 0.5) / R
+    tex[4] = (a + b * cu[None, :, None] + c * cu[:, None, None]).astype(np.float32)
+    for u, v in rng.uniform(0.5 / R, 1.0 - 0.5 / R, size=(20, 2)):
+        np.testing.assert_allclose(O.tex_lookup(tex, 4, u, v), a + b * u + c * v, rtol=1e-12)
+    # clamped outside the centres: the value at the nearest centre line
+    np.testing.assert_allclose(O.tex_lookup(tex, 4, 0.0, 0.5), a + b * 0.5 / R + c * 0.5, rtol=1e-12)
+    np.testing.assert_allclose(O.tex_lookup(tex, 4, 1.0, 1.0), a + (b + c) * (1 - 0.5 / R), rtol=1e-12)
+    # one texel per face: constant
+    np.testing.assert_allclose(O.tex_lookup(tex[:, :1, :1], 1, 0.3, 0.9), tex[1, 0, 0], rtol=1e-15)
+
+
+def _polygon_irradiance(x, n, verts, L):
+    """Irradiance at x (unit normal n) from a uniform Lambertian polygon of
+    radiance L lying above x's horizon (Lambert's polygon formula)."""
+    r = [(p - x) / np.linalg.norm(p - x) for p in verts]
+    tot = 0.0
+    for k in range(len(r)):
+        a, b = r[k], r[(k + 1) % len(r)]
+        g = np.cross(a, b)
+        tot += math.acos(np.clip(np.dot(a, b), -1.0, 1.0)) * np.dot(n, g / np.linalg.norm(g))
+    return 0.5 * abs(tot) * np.asarray(L, dtype=np.float64)
+
+
+def test_light_sample_mean_is_the_polygon_irradiance():
+    """The key-light estimator Le cos_x cos_l A n / d^2, sampled uniformly
+    over the lights, averages to the closed-form irradiance of the
+    parallelograms (Lambert's formula), for a light straight above a point,
+    a tilted one off to the side, and two lights together (n = 2)."""
+    x = np.array([0.3, -0.2, 0.1])
+    nx = np.array([0.0, 0.0, 1.0])
+    # light 1: square of side 2 at height 3, facing down
+    c1, e1, f1 = np.array([-0.7, -1.2, 3.1]), np.array([2.0, 0.0, 0.0]), np.array([0.0, 2.0, 0.0])
+    f1, e1 = e1, f1   # e1 x f1 points down
+    # light 2: a tilted parallelogram off to the side, facing x
+    c2 = np.array([2.0, 1.0, 1.5])
+    e2, f2 = np.array([0.0, 1.5, 0.0]), np.array([0.8, 0.0, 0.9])
+    if np.dot(np.cross(e2, f2), x - (c2 + 0.5 * e2 + 0.5 * f2)) < 0:
+        e2, f2 = f2, e2
+    L1, L2 = np.array([4.0, 2.0, 1.0]), np.array([1.0, 3.0, 2.0])
+    lights = np.array([np.concatenate([c1, e1, f1, L1]), np.concatenate([c2, e2, f2, L2])], dtype=np.float32)
+    l64 = lights.astype(np.float64)
+    quad = lambda l: [l[0:3], l[0:3] + l[3:6], l[0:3] + l[3:6] + l[6:9], l[0:3] + l[6:9]]
+    E1 = _polygon_irradiance(x, nx, quad(l64[0]), l64[0, 9:12])
+    E2 = _polygon_irradiance(x, nx, quad(l64[1]), l64[1, 9:12])
+    rng = np.random.default_rng(71)
+    xi = rng.uniform(size=(60000, 3))
+    for lt, expect in ((lights[:1], E1), (lights[1:], E2), (lights, E1 + E2)):
+        acc = np.zeros(3)
+        acc2 = np.zeros(3)
+        for z in xi:
+            ok, d, dist, w = O.light_sample(lt, z, x, nx)
+            acc += w
+            acc2 += w * w
+        m = acc / len(xi)
+        se = np.sqrt(np.maximum(acc2 / len(xi) - m * m, 0.0) / len(xi))
+        assert (np.abs(m - expect) <= 4 * se + 1e-12).all(), (m, expect, se)
+        assert (se < 0.02 * expect).all()
+
+
+def test_light_sample_facing_away_or_below_horizon_gives_nothing():
+    x, nx = np.zeros(3), np.array([0.0, 0.0, 1.0])
+    rng = np.random.default_rng(72)
+    up = np.array([[-1.0, -1.0, 2.0, 2.0, 0.0, 0.0, 0.0, 2.0, 0.0, 1.0, 1.0, 1.0]], dtype=np.float32)
+    below = np.array([[-1.0, -1.0, -2.0, 2.0, 0.0, 0.0, 0.0, 2.0, 0.0, 1.0, 1.0, 1.0]], dtype=np.float32)
+    for z in rng.uniform(size=(200, 3)):
+        assert not O.light_sample(up, z, x, nx)[0]      # emits upward, away from x
+        assert not O.light_sample(below, z, x, nx)[0]   # under x's horizon
+        ok, d, dist, w = O.light_sample(up[:, [0, 1, 2, 6, 7, 8, 3, 4, 5, 9, 10, 11]], z, x, nx)
+        assert ok and np.isclose(np.linalg.norm(d), 1.0) and dist > 0  # flipped: faces x
+
+
+def test_render_constant_face_textures_equal_scaled_albedo():
+    """A texture constant over each face multiplies that face's albedo:
+    rendering with it equals rendering with the product albedo (paths do not
+    depend on albedo), with the sun and several bounces."""
+    sc = I.tiny_scene()
+    osc = O.OracleScene(sc)
+    view = I.tiny_view()
+    view.w, view.h, view.spp = 48, 40, 2
+    alb = I.albedo(sc.n_quads)
+    k = np.random.default_rng(62).uniform(0.3, 1.0, size=(sc.n_quads, 3)).astype(np.float32)
+    tex = np.repeat(np.repeat(k[:, None, None, :], 4, axis=1), 4, axis=2)
+    p = I.Params(max_depth=3, sun_dir=I.MID_SUN_DIR, sun_E=(3.0, 3.0, 3.0))
+    r_tex = osc.render(view, alb, dataclasses.replace(p, tex=tex))["rgb"]
+    r_mul = osc.render(view, (alb.astype(np.float64) * k).astype(np.float32), p)["rgb"]
+    ok = r_mul > 0
+    assert ok.mean() > 0.2
+    np.testing.assert_allclose(r_tex, r_mul, rtol=2e-7)   # the FP32 rounding of the product
+
+
+def test_render_texture_follows_the_hit_position():
+    """A face texture bright on its u < 1/2 texels and dark on the others: on
+    the flat plane (env only, depth 2: the bounce always escapes) a pixel's
+    radiance is the albedo times the bilinear texture at the hit's
+    quad-space u, which the logged hit position reproduces."""
+    sc, view, n_w = _plane_scene()
+    osc = O.OracleScene(sc)
+    alb = np.ones((sc.n_quads, 3), dtype=np.float32)
+    tex = np.zeros((sc.n_quads, 2, 2, 3), dtype=np.float32)
+    tex[:, :, 0, :] = 1.0          # texels with i = 0 (u < 1/2)
+    p = I.Params(max_depth=2, env=(1.0, 1.0, 1.0), tex=tex)
+    r = osc.render(view, alb, p, log=True, rays=True)
+    assert (r["inst"][:, 1] == NONE).all()
+    vals = r["rgb"][:, 0]
+    assert (vals > 0.99).mean() > 0.15 and (vals < 0.01).mean() > 0.15   # both halves seen
+    # expected value from the hit position in the quad's own parameters
+    v, q = I.plane_mesh(128)
+    M = sc.xforms[0].reshape(3, 4).astype(np.float64)
+    for k in range(0, len(vals), 37):
+        o, d = r["rays"][k, 0, 0:3], r["rays"][k, 0, 3:6]
+        P = v[q[r["prim"][k, 0]]].astype(np.float64) @ M[:, :3].T + M[:, 3]
+        hit, t, u, w = O.intersect_quad(o, d, P)
+        assert hit
+        s_ = min(max(u * 2 - 0.5, 0.0), 1.0)
+        assert abs(vals[k] - (1.0 - s_)) < 1e-9
+
+
+def test_render_key_light_on_a_plane_is_the_polygon_irradiance():
+    """Depth 1 on a flat plane lit only by one key light above the pixel's
+    point (no environment, no sun): the radiance is a/pi times the light's
+    irradiance there (Lambert's polygon formula), to the Monte Carlo error
+    of its samples."""
+    v, q = I.plane_mesh(1)
+    xf = I.pack_xforms((np.eye(3) * 50.0)[None], np.zeros((1, 3)))
+    sc = I.Scene([(v, q)], xf, np.zeros(1, dtype=np.uint32))
+    osc = O.OracleScene(sc)
+    # a narrow camera straight down at the origin: every sample hits within
+    # 1e-3 of it
+    view = I.View(eye=(0.0, 0.0, 20.0), look=(0.0, 0.0, 0.0), up=(0.0, 1.0, 0.0), vfov_deg=0.005,
+                  w=1, h=1, spp=4096)
+    light = np.array([[-1.5, -1.0, 6.0, 0.0, 2.0, 0.0, 3.0, 0.0, 0.0, 8.0, 5.0, 3.0]], dtype=np.float32)
+    alb = np.full((1, 3), 0.5, dtype=np.float32)
+    p = I.Params(max_depth=1, env=(0.0, 0.0, 0.0), lights=light)
+    rgb = osc.render(view, alb, p)["rgb"][0]
+    l64 = light[0].astype(np.float64)
+    quad = [l64[0:3], l64[0:3] + l64[3:6], l64[0:3] + l64[3:6] + l64[6:9], l64[0:3] + l64[6:9]]
+    x = np.array([0.0, 0.0, 1e-4 + 0.0])   # the spawn point above the hit
+    E = _polygon_irradiance(x, np.array([0.0, 0.0, 1.0]), quad, l64[9:12])
+    np.testing.assert_allclose(rgb, 0.5 / math.pi * E, rtol=3e-3)
+
+
+def test_gradient_with_textures_and_key_lights_matches_central_differences():
+    sc = I.tiny_scene()
+    osc = O.OracleScene(sc)
+    view = I.tiny_view()
+    view.w = view.h = 48
+    view.spp = 2
+    alb = I.albedo(sc.n_quads).astype(np.float64)
+    p = I.Params(max_depth=3, sun_dir=I.MID_SUN_DIR, sun_E=(2.0, 2.0, 2.0),
+                 tex=I.face_textures(sc.n_quads), lights=I.tiny_lights())
+    dimg = np.random.default_rng(6).normal(size=(view.w * view.h, 3))
+    g = osc.grad(view, alb.astype(np.float32), p, dimg)
+    nz = np.argwhere(np.abs(g) > 1e-3 * np.abs(g).max())
+    assert nz.shape[0] > 20
+    pick = nz[np.random.default_rng(7).choice(nz.shape[0], 12, replace=False)]
+    h = 1.0 / 1024
+
+    def F(a):
+        return float((osc.render(view, a.astype(np.float32), p)["rgb"] * dimg).sum())
+
+    a32 = alb.astype(np.float32).astype(np.float64)
+    for qq, c in pick:
+        ap = a32.copy()
+        am = a32.copy()
+        ap[qq, c] = np.float32(a32[qq, c] + h)
+        am[qq, c] = np.float32(a32[qq, c] - h)
+        fd = (F(ap) - F(am)) / (ap[qq, c] - am[qq, c])
+        assert abs(fd - g[qq, c]) <= 1e-7 * max(1.0, abs(g[qq, c])), (qq, c, fd, g[qq, c])
 
 
 def test_progressive_samples_compose_to_one_render():
