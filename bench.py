@@ -226,12 +226,12 @@ def dumped_rays(api, scene, view, d_alb, params, n: int, tuning=None):
     rlog = torch.zeros(api.ray_log_floats([v], D), dtype=torch.float32, device=d_alb.device)
     scene.render([v], d_alb, params, ray_log=rlog, tuning=tuning)
     scene.check()
-    r = rlog.view(-1, D, 12)
+    r = rlog.view(-1, D, api.RAY_LOG_FLOATS)
     out = {}
     for name, k in (("primary", 0), ("diffuse", 1)):
         rk = r[:, k, 0:8]
         out[name] = rk[rk[:, 7] != 0][:n].contiguous()
-    so = r[:, :, 8:11].reshape(-1, 3)
+    so = r[:, :, 8:11].reshape(-1, 3)   # spawn points of the hits: the shadow rays' origins
     so = so[(so != 0).any(1)][:n]
     sun = torch.tensor(params.sun_dir, dtype=torch.float64)
     sh = torch.zeros((so.shape[0], 8), dtype=torch.float32, device=so.device)
@@ -397,6 +397,33 @@ def bench_adjoint(api, scene, sc, dev, tuning=None):
     scene.check()
     return {"primal_ms": tp * 1e3, "adjoint_ms": ta * 1e3, "ratio": ta / tp,
             "paths": view.w * view.h * view.spp, "n_params": int(a0.size)}
+
+
+def bench_shading(api, scene, sc, view, d_alb, params, dev, tuning=None):
+    """Richer shading on the same frame: per-face textures (4x4 RGB texels
+    per quad, the Ptex stand-in) modulating the albedo, and the 23 key
+    lights sampled at every vertex beside the sun (one more shadow ray per
+    vertex); rays and time against the plain frame."""
+    import dataclasses
+    import torch
+    from paper_2001_02620_gb300 import inputs as I
+    tex = torch.from_numpy(I.face_textures(sc.n_quads)).to(dev)
+    lit = dataclasses.replace(params, tex=tex, lights=I.mid_lights())
+    img = torch.empty((view.h, view.w, 3), device=dev)
+    out = {}
+    for name, p in (("plain", params), ("textures_and_key_lights", lit)):
+        t = _time(lambda: scene.render([view], d_alb, p, outs=[img], tuning=tuning), 5)
+        stats = torch.zeros(STAT_WORDS, dtype=torch.int64, device=dev)
+        scene.render([view], d_alb, p, outs=[img], stats=stats, tuning=tuning)
+        st = stats.cpu().numpy()
+        rays = int(st[0] + st[6])
+        out[name] = {"ms": t * 1e3, "rays": rays, "mrays_s": rays / t / 1e6,
+                     "path_samples_per_s": view.w * view.h * view.spp / t}
+    scene.check()
+    out["texture"] = "4x4 RGB texels per quad, bilinear in quad (u, v), times the quad albedo"
+    out["lights"] = "23 square key lights (side 120, height 600), one sample per vertex"
+    del tex
+    return out
 
 
 def run_reference(args):
@@ -624,6 +651,8 @@ def sub_measurement(api, I, args, dev, world, hbm, peak_kind, l2_gbs, extras):
         out["adjoint_vs_primal"] = bench_adjoint(api, scene, sc, dev, tuning)
     if "progressive" in extras:
         out["progressive"] = bench_progressive(api, scene, view, d_alb, params, dev, tuning)
+    if "shading" in extras:
+        out["richer_shading"] = bench_shading(api, scene, sc, view, d_alb, params, dev, tuning)
     scene.close()
     return out
 
@@ -640,7 +669,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--extras", default="trace,batched,adjoint,progressive,costmap,device_build,mid",
+    ap.add_argument("--extras", default="trace,batched,adjoint,progressive,costmap,device_build,shading,mid",
                     help="comma list of sub-measurements to add (or 'none')")
     ap.add_argument("--res", type=int, default=0,
                     help="override the view side (small profiling captures only)")
@@ -747,6 +776,8 @@ def main():
                 views=I.batched_views(n_views=64, min_log2=5.0, max_log2=7.0, max_spp=4))
         if "adjoint" in extras:
             line["adjoint_vs_primal"] = bench_adjoint(api, scene, sc, dev, tuning)
+        if "shading" in extras:
+            line["richer_shading"] = bench_shading(api, scene, sc, view, d_alb, params, dev, tuning)
     if "device_build" in extras and not (args.tlas_builder or args.blas_builder):
         line["device_build"] = bench_device_build(api, scene, sc, view, d_alb, params, dev, tuning,
                                                   rays=m["rays"])

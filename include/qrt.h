@@ -44,6 +44,11 @@ extern "C" {
 /* qrt_params.flags */
 #define QRT_FLAG_STAGE_TIMES 1u /* record GPU time of each wavefront stage (qrt_stage_times) */
 
+/* Most key lights one render takes (qrt_params.n_lights). */
+#define QRT_MAX_LIGHTS 32
+/* Largest per-face texture resolution (qrt_params.tex_res). */
+#define QRT_MAX_TEX_RES 16
+
 enum {
     QRT_OK = 0,
     QRT_ERR_INVALID_ARG = -1,    /* bad handle, NULL pointer, size or value */
@@ -162,25 +167,43 @@ typedef struct {
  *               shadow rays
  *   d_path_log  optional DEVICE buffer for diagnostics (NULL = off): per path
  *               max_depth pairs (inst, prim) of the hits, 0xFFFFFFFF where the
- *               path had no such ray, then one word of shadow bits (bit 2i: a
- *               shadow ray was traced at vertex i, bit 2i+1: it was occluded;
- *               first 16 vertices).  Path p of view v sits at
+ *               path had no such ray, then one word of sun shadow bits (bit
+ *               2i: a shadow ray was traced at vertex i, bit 2i+1: it was
+ *               occluded; first 16 vertices) and one word of key-light shadow
+ *               bits (the same layout).  Path p of view v sits at
  *               sum_{u<v}(rw*rh*spp)_u + (y'*rw + x')*spp + sample, (x', y')
  *               the pixel within the view's rendered region, each path taking
- *               2*max_depth + 1 words.
+ *               2*max_depth + 2 words.
  *   max_steps   traversal step limit per ray (0 = 2^20); exceeding it stops
  *               that ray and raises QRT_ERR_STEP_LIMIT.
  *   tuning      launch tuning (zeros = defaults).
  *   d_ray_log   optional DEVICE float buffer for diagnostics (NULL = off),
  *               16-byte aligned, indexed by path like d_path_log: per path
- *               max_depth records of 12 floats, one per depth i = 1..max_depth:
+ *               max_depth records of 16 floats, one per depth i = 1..max_depth:
  *               the closest-hit ray traced at depth i as a qrt_ray (o, tmin,
  *               d, tmax; the camera ray at depth 1, then each bounce ray as
- *               spawned), then the origin of the shadow ray traced from the hit
- *               of depth i (3 floats; its direction is the sun's) and one
- *               unused float.  Records of rays a path did not trace are zero.
- *               The exact FP32 rays let a test re-trace, in FP64, the ray on
- *               which a path first left the oracle's path. */
+ *               spawned), the spawn point of the hit of depth i (3 floats and
+ *               one unused: the origin of its shadow rays and of the next
+ *               ray), and the direction and distance of its key-light shadow
+ *               ray (4 floats).  Records of rays a path did not trace are
+ *               zero.  The exact FP32 rays let a test re-trace, in FP64, the
+ *               ray on which a path first left the oracle's path.
+ *   d_tex, tex_res  optional per-face textures (Section 5.3: a Ptex texture,
+ *               baked on each face, modulates the diffuse albedo): DEVICE
+ *               float [n_quads * tex_res^2 * 3], quad row q's texels row-major
+ *               in v then u; texel (i, j) covers quad-space [i/R, (i+1)/R] x
+ *               [j/R, (j+1)/R] and a hit at (u, v) takes the bilinear value
+ *               between texel centres, clamped to the face.  The diffuse
+ *               albedo is d_albedo[q] times that value.  NULL / 0 = none;
+ *               tex_res at most QRT_MAX_TEX_RES.
+ *   n_lights, lights  key lights (Section 4.1: quad-shaped key lights):
+ *               HOST float [n_lights * 12], per light a parallelogram (corner,
+ *               edge1, edge2) emitting radiance (RGB, 3 floats) on the side of
+ *               edge1 x edge2; copied during the call.  Reached only by
+ *               next-event estimation: at each path vertex one light is
+ *               picked uniformly and a point uniformly on it, from the random
+ *               stream (pixel, sample, 2^30 + depth), and a shadow ray is
+ *               traced toward that point.  At most QRT_MAX_LIGHTS. */
 typedef struct {
     uint32_t max_depth;
     uint32_t flags;
@@ -192,6 +215,10 @@ typedef struct {
     uint32_t* d_path_log;
     qrt_tuning tuning;
     float* d_ray_log;
+    const float* d_tex;
+    uint32_t tex_res;
+    uint32_t n_lights;
+    const float* lights;
 } qrt_params;
 
 /* BVH build options (NULL = defaults).

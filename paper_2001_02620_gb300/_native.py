@@ -55,7 +55,8 @@ class qrt_params(C.Structure):
     _fields_ = [("max_depth", C.c_uint32), ("flags", C.c_uint32), ("seed", C.c_uint64),
                 ("env", C.c_float * 3), ("sun_dir", C.c_float * 3), ("sun_E", C.c_float * 3),
                 ("max_steps", C.c_uint32), ("d_path_log", C.c_void_p), ("tuning", qrt_tuning),
-                ("d_ray_log", C.c_void_p)]
+                ("d_ray_log", C.c_void_p), ("d_tex", C.c_void_p), ("tex_res", C.c_uint32),
+                ("n_lights", C.c_uint32), ("lights", C.POINTER(C.c_float))]
 
 
 class qrt_build_opts(C.Structure):

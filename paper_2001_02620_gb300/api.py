@@ -42,6 +42,19 @@ def make_params(p: Params, tuning: dict | None = None, path_log: torch.Tensor | 
     cp.d_path_log = _ptr(path_log)
     cp.d_ray_log = _ptr(ray_log)
     cp.tuning = make_tuning(tuning)
+    tex = getattr(p, "tex", None)
+    if tex is not None:
+        if not (isinstance(tex, torch.Tensor) and tex.is_cuda and tex.dtype == torch.float32
+                and tex.is_contiguous() and tex.dim() == 4):
+            raise TypeError("Params.tex must be a contiguous float32 CUDA tensor [n_quads, R, R, 3]")
+        cp.d_tex = _ptr(tex)
+        cp.tex_res = int(tex.shape[1])
+    lights = getattr(p, "lights", None)
+    if lights is not None and len(lights):
+        lt = np.ascontiguousarray(lights, dtype=np.float32).reshape(-1, 12)
+        cp.n_lights = int(lt.shape[0])
+        cp.lights = lt.ctypes.data_as(C.POINTER(C.c_float))
+        cp._keep = lt   # the library copies the lights during the call
     return cp
 
 
@@ -73,10 +86,13 @@ def n_paths(views) -> int:
 
 
 def path_log_words(views, max_depth: int) -> int:
-    return n_paths(views) * (2 * int(max_depth) + 1)
+    """Words of a path log: per path (inst, prim) per depth, sun and key-light shadow bits."""
+    return n_paths(views) * (2 * int(max_depth) + 2)
 
 
-RAY_LOG_FLOATS = 12  # per path and depth: closest-hit ray (8), shadow-ray origin (3), unused (1)
+# per path and depth: closest-hit ray (8), spawn point (3) and one unused,
+# key-light shadow direction and distance (4)
+RAY_LOG_FLOATS = 16
 
 
 def ray_log_floats(views, max_depth: int) -> int:

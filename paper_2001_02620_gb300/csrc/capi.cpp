@@ -787,6 +787,19 @@ int make_params(const qrt_params* p, ParamsDev& P) {
     if (P.path_log && !aligned(P.path_log, 4)) return fail(QRT_ERR_ALIGN, "d_path_log must be 4-byte aligned");
     P.ray_log = p->d_ray_log;
     if (P.ray_log && !aligned(P.ray_log, 16)) return fail(QRT_ERR_ALIGN, "d_ray_log must be 16-byte aligned");
+    P.tex = p->tex_res ? p->d_tex : nullptr;
+    P.tex_res = p->d_tex ? p->tex_res : 0;
+    if (P.tex_res > kMaxTexRes) return fail(QRT_ERR_INVALID_ARG, "tex_res exceeds QRT_MAX_TEX_RES");
+    if (P.tex && !aligned(P.tex, 4)) return fail(QRT_ERR_ALIGN, "d_tex must be 4-byte aligned");
+    if (p->n_lights > (uint32_t)kMaxLights) return fail(QRT_ERR_INVALID_ARG, "n_lights exceeds QRT_MAX_LIGHTS");
+    if (p->n_lights && !p->lights) return fail(QRT_ERR_INVALID_ARG, "lights is NULL");
+    P.n_lights = p->n_lights;
+    for (uint32_t k = 0; k < p->n_lights; ++k)
+        for (int c = 0; c < 12; ++c) {
+            const float v = p->lights[12 * k + c];
+            if (!std::isfinite(v)) return fail(QRT_ERR_INVALID_ARG, "light " + std::to_string(k) + " is not finite");
+            P.lights[k][c] = v;
+        }
     return QRT_OK;
 }
 

@@ -77,6 +77,8 @@ struct ViewDev {
 };
 
 constexpr int kMaxViewsPerLaunch = 64;
+constexpr int kMaxLights = 32;
+constexpr uint32_t kMaxTexRes = 16;
 
 struct ParamsDev {
     uint32_t max_depth;
@@ -87,12 +89,22 @@ struct ParamsDev {
     float sun_E[3];
     uint32_t sun_on;
     uint32_t* path_log;
-    float* ray_log;  // diagnostics: 12 floats per path and depth (see qrt_params)
+    float* ray_log;     // diagnostics: kRayLogFloats per path and depth (see qrt_params)
+    const float* tex;   // per-face textures, tex_res^2 RGB texels per quad (or null)
+    uint32_t tex_res;
+    uint32_t n_lights;  // key lights: corner, edge1, edge2, radiance
+    float lights[kMaxLights][12];
 };
 
-// Floats per path and depth in the ray log: closest-hit ray (8), shadow-ray
-// origin (3), unused (1).
-constexpr int kRayLogFloats = 12;
+// Floats per path and depth in the ray log: closest-hit ray (8), spawn
+// point (3) and one unused, key-light shadow direction and distance (4).
+constexpr int kRayLogFloats = 16;
+// Words per path in the path log: (inst, prim) per depth, sun shadow bits,
+// key-light shadow bits.
+__host__ __device__ constexpr uint64_t path_log_words(uint32_t max_depth) { return 2ull * max_depth + 2; }
+// Random stream (fourth Philox counter word) of the key-light sample drawn
+// at a path's vertex of depth i: kLightStream + i.
+constexpr uint32_t kLightStream = 0x40000000u;
 
 struct RenderArgs {
     DevScene S;

@@ -44,13 +44,11 @@ __device__ __forceinline__ uint32_t path_sample(const RenderArgs& A, const ViewD
     F3 o = f3(V.eye[0], V.eye[1], V.eye[2]);
     float b0 = 1.f, b1 = 1.f, b2 = 1.f;     // throughput
     float l0 = 0.f, l1 = 0.f, l2 = 0.f;     // radiance
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f;     // sun terms so far (replay)
-    uint32_t shadow_bits = 0;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;     // next-event terms so far (replay)
+    uint32_t shadow_bits = 0, light_bits = 0;
     const uint32_t D = P.max_depth;
     uint32_t i = 1;
-    if (rlog)
-        for (uint32_t k = 0; k < 3 * D; ++k)
-            reinterpret_cast<float4*>(rlog)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (rlog) clear_ray_log(rlog, D);
     for (; i <= D; ++i) {
         Hit h;
         if (rlog) log_ray(rlog + (i - 1) * kRayLogFloats, o, d);
@@ -71,16 +69,23 @@ __device__ __forceinline__ uint32_t path_sample(const RenderArgs& A, const ViewD
         uint32_t qbase;
         const F3 n = hit_normal(S, h.inst, h.slot, d, &qbase);
         const uint32_t row = qbase + h.prim;
-        const float a0 = __ldg(A.albedo + 3 * (size_t)row);
-        const float a1 = __ldg(A.albedo + 3 * (size_t)row + 1);
-        const float a2 = __ldg(A.albedo + 3 * (size_t)row + 2);
+        const float q0 = __ldg(A.albedo + 3 * (size_t)row);
+        const float q1 = __ldg(A.albedo + 3 * (size_t)row + 1);
+        const float q2 = __ldg(A.albedo + 3 * (size_t)row + 2);
+        float a0 = q0, a1 = q1, a2 = q2;  // diffuse albedo: the quad's, times its texture
+        if (P.tex_res) {
+            const F3 tx = tex_lookup(P.tex, P.tex_res, row, h.u, h.v);
+            a0 = __fmul_rn(q0, tx.x);
+            a1 = __fmul_rn(q1, tx.y);
+            a2 = __fmul_rn(q2, tx.z);
+        }
         const F3 sp = spawn_point(o, d, h.t, n);
+        if (rlog) log_spawn(rlog + (i - 1) * kRayLogFloats, sp);
         float n0 = 0.f, n1 = 0.f, n2 = 0.f;  // this vertex's sun term
         if (P.sun_on) {
             const float cl = dot3(n, f3(P.sun_l[0], P.sun_l[1], P.sun_l[2]));
             if (cl > 0.f) {
                 if (i <= 16) shadow_bits |= 1u << (2 * (i - 1));
-                if (rlog) log_shadow_origin(rlog + (i - 1) * kRayLogFloats, sp);
                 Hit hs;
                 err |= trace_ray<true, STACK, FETCH>(S, sp.x, sp.y, sp.z, P.sun_l[0], P.sun_l[1],
                                                       P.sun_l[2], 0.0f, kInfF, P.max_steps, hs, ls);
@@ -95,10 +100,11 @@ __device__ __forceinline__ uint32_t path_sample(const RenderArgs& A, const ViewD
             }
         }
         if (mode == 1) {
-            // d L / d a_i = (radiance leaving vertex i) / a_i
-            const float g0 = a0 != 0.f ? __fdiv_rn(__fmul_rn(w[0], __fsub_rn(Ltot[0], s0)), a0) : 0.f;
-            const float g1 = a1 != 0.f ? __fdiv_rn(__fmul_rn(w[1], __fsub_rn(Ltot[1], s1)), a1) : 0.f;
-            const float g2 = a2 != 0.f ? __fdiv_rn(__fmul_rn(w[2], __fsub_rn(Ltot[2], s2)), a2) : 0.f;
+            // d L / d q_i = (radiance leaving vertex i) / q_i, q_i the quad's
+            // albedo (the texture factor is a constant of the path)
+            const float g0 = q0 != 0.f ? __fdiv_rn(__fmul_rn(w[0], __fsub_rn(Ltot[0], s0)), q0) : 0.f;
+            const float g1 = q1 != 0.f ? __fdiv_rn(__fmul_rn(w[1], __fsub_rn(Ltot[1], s1)), q1) : 0.f;
+            const float g2 = q2 != 0.f ? __fdiv_rn(__fmul_rn(w[2], __fsub_rn(Ltot[2], s2)), q2) : 0.f;
             grad_add(A.grad, row, g0, g1, g2);
             s0 = __fadd_rn(s0, n0);
             s1 = __fadd_rn(s1, n1);
@@ -107,6 +113,37 @@ __device__ __forceinline__ uint32_t path_sample(const RenderArgs& A, const ViewD
         l0 = __fadd_rn(l0, n0);
         l1 = __fadd_rn(l1, n1);
         l2 = __fadd_rn(l2, n2);
+        // key light: one sample, its shadow ray traced toward the sampled
+        // point; added after the sun term, as the wavefront shadow stage
+        // adds it after the sun's
+        if (P.n_lights) {
+            const uint4 xl = draw(P.seed, gpix, smp, kLightStream + i);
+            F3 ld, wl;
+            float dist;
+            if (light_sample(P, u01(xl.x), u01(xl.y), u01(xl.z), sp, n, &ld, &dist, &wl)) {
+                if (i <= 16) light_bits |= 1u << (2 * (i - 1));
+                if (rlog) log_light_ray(rlog + (i - 1) * kRayLogFloats, ld, dist);
+                Hit hl;
+                err |= trace_ray<true, STACK, FETCH>(S, sp.x, sp.y, sp.z, ld.x, ld.y, ld.z, 0.0f, dist,
+                                                      P.max_steps, hl, ls);
+                if (hl.inst != 0xFFFFFFFFu) {
+                    if (i <= 16) light_bits |= 2u << (2 * (i - 1));
+                } else {
+                    const float ip = 0.318309886183790671538f;  // 1 / pi
+                    const float m0 = __fmul_rn(__fmul_rn(b0, a0), __fmul_rn(wl.x, ip));
+                    const float m1 = __fmul_rn(__fmul_rn(b1, a1), __fmul_rn(wl.y, ip));
+                    const float m2 = __fmul_rn(__fmul_rn(b2, a2), __fmul_rn(wl.z, ip));
+                    l0 = __fadd_rn(l0, m0);
+                    l1 = __fadd_rn(l1, m1);
+                    l2 = __fadd_rn(l2, m2);
+                    if (mode == 1) {
+                        s0 = __fadd_rn(s0, m0);
+                        s1 = __fadd_rn(s1, m1);
+                        s2 = __fadd_rn(s2, m2);
+                    }
+                }
+            }
+        }
         b0 = __fmul_rn(b0, a0);
         b1 = __fmul_rn(b1, a1);
         b2 = __fmul_rn(b2, a2);
@@ -124,6 +161,7 @@ __device__ __forceinline__ uint32_t path_sample(const RenderArgs& A, const ViewD
             log[2 * k + 1] = 0xFFFFFFFFu;
         }
         log[2 * D] = shadow_bits;
+        log[2 * D + 1] = light_bits;
     }
     L[0] = l0;
     L[1] = l1;
@@ -174,7 +212,7 @@ __global__ void __launch_bounds__(256) render_kernel(const __grid_constant__ Ren
                 for (uint32_t s = 0; s < V.spp; ++s) {
                     float L[3];
                     const uint64_t g = V.path_begin + pix * V.spp + s;
-                    uint32_t* log = A.P.path_log ? A.P.path_log + g * (2ull * D + 1) : nullptr;
+                    uint32_t* log = A.P.path_log ? A.P.path_log + g * path_log_words(D) : nullptr;
                     float* rlog = A.P.ray_log ? ray_log_rec(A.P, g, 1) : nullptr;
                     const uint32_t e = path_sample<STACK, FETCH>(A, V, x, y, gpix, V.sample_base + s, 0, L, nullptr,
                                                                  nullptr, log, rlog, &st);

@@ -57,7 +57,8 @@ __device__ __forceinline__ uint64_t view_pixel(const ViewDev& V, uint64_t k, uin
 }
 
 // Ray-log record of depth i (1-based) of path g: the closest-hit ray as
-// (o, 0, d, inf), then the shadow-ray origin (diagnostics only).
+// (o, 0, d, inf), the spawn point of its hit, the key-light shadow ray's
+// direction and distance (diagnostics only).
 __device__ __forceinline__ float* ray_log_rec(const ParamsDev& P, uint64_t g, uint32_t i) {
     return P.ray_log + (g * P.max_depth + (i - 1)) * (uint64_t)kRayLogFloats;
 }
@@ -66,8 +67,72 @@ __device__ __forceinline__ void log_ray(float* rec, F3 o, F3 d) {
     r[0] = make_float4(o.x, o.y, o.z, 0.f);
     r[1] = make_float4(d.x, d.y, d.z, __int_as_float(0x7f800000));
 }
-__device__ __forceinline__ void log_shadow_origin(float* rec, F3 o) {
+__device__ __forceinline__ void log_spawn(float* rec, F3 o) {
     reinterpret_cast<float4*>(rec)[2] = make_float4(o.x, o.y, o.z, 0.f);
+}
+__device__ __forceinline__ void log_light_ray(float* rec, F3 d, float dist) {
+    reinterpret_cast<float4*>(rec)[3] = make_float4(d.x, d.y, d.z, dist);
+}
+__device__ __forceinline__ void clear_ray_log(float* rec0, uint32_t depth) {
+    float4* r = reinterpret_cast<float4*>(rec0);
+    for (uint32_t k = 0; k < (kRayLogFloats / 4) * depth; ++k) r[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Per-face texture value of quad row at quad-space (u, v) (qrt_params:
+// bilinear between texel centres, clamped to the face), FP32.
+__device__ __forceinline__ F3 tex_lookup(const float* tex, uint32_t R, uint32_t row, float u, float v) {
+    const float fr = (float)R;
+    const float s = fminf(fmaxf(__fmaf_rn(u, fr, -0.5f), 0.f), fr - 1.f);
+    const float t = fminf(fmaxf(__fmaf_rn(v, fr, -0.5f), 0.f), fr - 1.f);
+    const uint32_t i0 = (uint32_t)s, j0 = (uint32_t)t;
+    const uint32_t i1 = min(i0 + 1u, R - 1u), j1 = min(j0 + 1u, R - 1u);
+    const float fs = __fsub_rn(s, (float)i0), ft = __fsub_rn(t, (float)j0);
+    const float* T = tex + (size_t)row * R * R * 3;
+    const float* a = T + 3 * (j0 * R + i0);
+    const float* b = T + 3 * (j0 * R + i1);
+    const float* c = T + 3 * (j1 * R + i0);
+    const float* d = T + 3 * (j1 * R + i1);
+    float o[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float lo = __fmaf_rn(fs, __fsub_rn(__ldg(b + k), __ldg(a + k)), __ldg(a + k));
+        const float hi = __fmaf_rn(fs, __fsub_rn(__ldg(d + k), __ldg(c + k)), __ldg(c + k));
+        o[k] = __fmaf_rn(ft, __fsub_rn(hi, lo), lo);
+    }
+    return f3(o[0], o[1], o[2]);
+}
+
+// One key-light sample seen from x with unit normal nx (qrt_params): light
+// floor(xi0 n), point corner + xi1 edge1 + xi2 edge2; writes the unit
+// direction toward it, its distance and the estimator Le cos_x cos_l
+// |edge1 x edge2| n / d^2.  False when the point faces away from x or lies
+// below its horizon.  FP32.
+__device__ __forceinline__ bool light_sample(const ParamsDev& P, float xi0, float xi1, float xi2, F3 x,
+                                             F3 nx, F3* dir, float* dist, F3* w) {
+    const uint32_t k = min((uint32_t)__fmul_rn(xi0, (float)P.n_lights), P.n_lights - 1u);
+    const float* L = P.lights[k];
+    const F3 y = f3(__fmaf_rn(xi2, L[6], __fmaf_rn(xi1, L[3], L[0])),
+                    __fmaf_rn(xi2, L[7], __fmaf_rn(xi1, L[4], L[1])),
+                    __fmaf_rn(xi2, L[8], __fmaf_rn(xi1, L[5], L[2])));
+    const F3 q = f3(__fsub_rn(y.x, x.x), __fsub_rn(y.y, x.y), __fsub_rn(y.z, x.z));
+    const float d2 = dot3(q, q);
+    if (!(d2 > 0.f)) return false;
+    const float d = __fsqrt_rn(d2);
+    const float inv = __frcp_rn(d);
+    const F3 om = f3(__fmul_rn(q.x, inv), __fmul_rn(q.y, inv), __fmul_rn(q.z, inv));
+    const F3 cr = f3(__fsub_rn(__fmul_rn(L[4], L[8]), __fmul_rn(L[5], L[7])),
+                     __fsub_rn(__fmul_rn(L[5], L[6]), __fmul_rn(L[3], L[8])),
+                     __fsub_rn(__fmul_rn(L[3], L[7]), __fmul_rn(L[4], L[6])));
+    const float A = __fsqrt_rn(dot3(cr, cr));
+    if (!(A > 0.f)) return false;
+    const float cx = dot3(nx, om);
+    const float cl = -__fdiv_rn(dot3(cr, om), A);
+    if (!(cx > 0.f) || !(cl > 0.f)) return false;
+    const float g = __fdiv_rn(__fmul_rn(__fmul_rn(__fmul_rn(cx, cl), A), (float)P.n_lights), d2);
+    *w = f3(__fmul_rn(L[9], g), __fmul_rn(L[10], g), __fmul_rn(L[11], g));
+    *dir = om;
+    *dist = d;
+    return true;
 }
 
 // Pinhole ray through (x + xi1, y + xi2) of view V (unit direction).

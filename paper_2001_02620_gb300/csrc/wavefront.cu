@@ -87,17 +87,19 @@ __global__ void __launch_bounds__(256) wave_gen(const __grid_constant__ WaveArgs
     A.B.ray_d[j] = make_float4(d.x, d.y, d.z, kInfF);
     A.B.beta[j] = make_float4(1.f, 1.f, 1.f, 0.f);
     A.B.L[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (A.P.n_lights) A.B.lpend[j].w = 0.f;
     A.B.meta[j] = make_uint2((uint32_t)(V.item_begin + pix), smp);
     A.B.q[1][j] = j;  // depth 1 uses queue 1 & 1
     if (A.cost_on) A.B.cost[j] = 0;
     if (A.P.path_log) {
-        uint32_t* log = A.P.path_log + g * (2ull * A.P.max_depth + 1);
-        for (uint32_t k = 0; k < 2 * A.P.max_depth + 1; ++k) log[k] = k == 2 * A.P.max_depth ? 0u : 0xFFFFFFFFu;
+        uint32_t* log = A.P.path_log + g * path_log_words(A.P.max_depth);
+        for (uint32_t k = 0; k < 2 * A.P.max_depth; ++k) log[k] = 0xFFFFFFFFu;
+        log[2 * A.P.max_depth] = log[2 * A.P.max_depth + 1] = 0u;
     }
     if (A.P.ray_log) {
-        float4* rl = reinterpret_cast<float4*>(ray_log_rec(A.P, g, 1));
-        for (uint32_t k = 0; k < 3 * A.P.max_depth; ++k) rl[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        log_ray(reinterpret_cast<float*>(rl), f3(V.eye[0], V.eye[1], V.eye[2]), d);
+        float* rl = ray_log_rec(A.P, g, 1);
+        clear_ray_log(rl, A.P.max_depth);
+        log_ray(rl, f3(V.eye[0], V.eye[1], V.eye[2]), d);
     }
 }
 
@@ -118,12 +120,18 @@ __global__ void __maxnreg__(occupancy_regs(OCC)) wave_trace(const __grid_constan
     Traversal<ANY, kMaxStack, FETCH> T;
     T.err = 0;  // accumulated over this thread's rays
     uint32_t j = 0;
+    // any-hit entries of key-light shadow rays carry kLightRay
     auto start_ray = [&](uint32_t k) {
         j = queue[k];
         if (ANY) {
-            const float4 o = A.B.sray_o[j];
-            T.init(A.S, o.x, o.y, o.z, A.P.sun_l[0], A.P.sun_l[1], A.P.sun_l[2], 0.f, kInfF,
-                   A.P.max_steps, st);
+            const float4 o = A.B.sray_o[j & ~kLightRay];
+            if (j & kLightRay) {
+                const float4 ld = A.B.lray_d[j & ~kLightRay];
+                T.init(A.S, o.x, o.y, o.z, ld.x, ld.y, ld.z, 0.f, ld.w, A.P.max_steps, st);
+            } else {
+                T.init(A.S, o.x, o.y, o.z, A.P.sun_l[0], A.P.sun_l[1], A.P.sun_l[2], 0.f, kInfF,
+                       A.P.max_steps, st);
+            }
         } else {
             // path rays span (0, inf) (the spawn point is offset off the
             // surface): constant bounds fold into the traversal instead of
@@ -133,32 +141,45 @@ __global__ void __maxnreg__(occupancy_regs(OCC)) wave_trace(const __grid_constan
         }
     };
     auto finish_ray = [&]() {
+        const uint32_t jj = j & ~kLightRay;
         if constexpr (STATS) {
-            if (A.cost_on) atomicAdd(A.B.cost + j, A.P.max_steps - T.budget);
+            if (A.cost_on) atomicAdd(A.B.cost + jj, A.P.max_steps - T.budget);
         }
         if (ANY) {
+            const bool light = j & kLightRay;
             if (T.h.inst == 0xFFFFFFFFu) {
-                const float4 p = A.B.pend[j];
-                float4 l = A.B.L[j];
-                l.x = __fadd_rn(l.x, p.x);
-                l.y = __fadd_rn(l.y, p.y);
-                l.z = __fadd_rn(l.z, p.z);
-                if (depth <= kVisDepths) l.w = __uint_as_float(__float_as_uint(l.w) | (1u << (depth - 1)));
-                A.B.L[j] = l;
+                if (light) {
+                    // the sun's shadow ray of the same vertex may add into L
+                    // in this launch: flag the term, fold_light adds it later
+                    A.B.lpend[jj].w = 1.f;
+                } else {
+                    const float4 p = A.B.pend[jj];
+                    float4 l = A.B.L[jj];
+                    l.x = __fadd_rn(l.x, p.x);
+                    l.y = __fadd_rn(l.y, p.y);
+                    l.z = __fadd_rn(l.z, p.z);
+                    if (depth <= kVisDepths) l.w = __uint_as_float(__float_as_uint(l.w) | (1u << (depth - 1)));
+                    A.B.L[jj] = l;
+                }
             } else if (A.P.path_log && depth <= 16) {
-                const uint64_t g = A.P0 + j;
-                A.P.path_log[g * (2ull * A.P.max_depth + 1) + 2 * A.P.max_depth] |=
+                const uint64_t g = A.P0 + jj;
+                A.P.path_log[g * path_log_words(A.P.max_depth) + 2 * A.P.max_depth + (light ? 1 : 0)] |=
                     2u << (2 * (depth - 1));
             }
         } else {
             A.B.hit[j] = make_uint4(__float_as_uint(T.h.t), T.h.inst, T.h.prim, T.h.slot);
+            if (A.P.tex_res) A.B.hit_uv[j] = make_float2(T.h.u, T.h.v);
         }
     };
     // the world ray is read back from the queue buffers where the traversal
     // needs it, not kept live per lane
     auto world_ray = [&]() {
         if (ANY) {
-            const float4 o = __ldg(A.B.sray_o + j);
+            const float4 o = __ldg(A.B.sray_o + (j & ~kLightRay));
+            if (j & kLightRay) {
+                const float4 ld = __ldg(A.B.lray_d + (j & ~kLightRay));
+                return WRay{o.x, o.y, o.z, ld.x, ld.y, ld.z};
+            }
             return WRay{o.x, o.y, o.z, A.P.sun_l[0], A.P.sun_l[1], A.P.sun_l[2]};
         }
         const float4 o = __ldg(A.B.ray_o + j), d = __ldg(A.B.ray_d + j);
@@ -170,9 +191,32 @@ __global__ void __maxnreg__(occupancy_regs(OCC)) wave_trace(const __grid_constan
     if constexpr (STATS) add_stats(A.stats + (ANY ? 6 : 0), st);
 }
 
+// Adds path j's key-light term of the previous vertex into its radiance if
+// its shadow ray found the light (flag in lpend.w): after the sun's term of
+// that vertex, as the single-kernel renderer adds them.
+__device__ __forceinline__ void fold_light(const WaveBufs& B, uint32_t j) {
+    const float4 p = B.lpend[j];
+    if (p.w != 0.f) {
+        float4 l = B.L[j];
+        l.x = __fadd_rn(l.x, p.x);
+        l.y = __fadd_rn(l.y, p.y);
+        l.z = __fadd_rn(l.z, p.z);
+        B.L[j] = l;
+        B.lpend[j].w = 0.f;
+    }
+}
+
+__global__ void __launch_bounds__(256) wave_fold(const __grid_constant__ WaveArgs A, uint32_t n) {
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) fold_light(A.B, j);
+}
+
 // Shade stage of depth i (1-based).  replay = false: primal; true: replay
-// pass of the adjoint (gradient into A.grad, no env term, L holds the sun
-// terms gathered so far).
+// pass of the adjoint (gradient into A.grad, no env term, L holds the
+// next-event terms gathered so far).  The diffuse albedo is the quad's
+// albedo times its per-face texture at the hit (when textures are given);
+// next-event estimation queues the sun's shadow ray and one key-light
+// shadow ray (tagged kLightRay) with their pending terms.
 __global__ void __launch_bounds__(256) wave_shade(const __grid_constant__ WaveArgs A, int depth,
                                                   int replay) {
     const uint32_t* ctr = A.B.ctr + kCtrStride * depth;
@@ -180,12 +224,13 @@ __global__ void __launch_bounds__(256) wave_shade(const __grid_constant__ WaveAr
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const uint32_t j = A.B.q[depth & 1][k];
+    if (A.P.n_lights && depth > 1) fold_light(A.B, j);
     const uint4 hb = A.B.hit[j];
     const float t = __uint_as_float(hb.x);
     const uint32_t inst = hb.y, prim = hb.z, slot = hb.w;
     const uint32_t D = A.P.max_depth;
     const uint64_t g = A.P0 + j;
-    uint32_t* log = A.P.path_log ? A.P.path_log + g * (2ull * D + 1) : nullptr;
+    uint32_t* log = A.P.path_log ? A.P.path_log + g * path_log_words(D) : nullptr;
     if (log) {
         log[2 * (depth - 1)] = inst;
         log[2 * (depth - 1) + 1] = prim;
@@ -206,29 +251,41 @@ __global__ void __launch_bounds__(256) wave_shade(const __grid_constant__ WaveAr
     uint32_t qbase;
     const F3 nrm = hit_normal(A.S, inst, slot, d, &qbase);
     const uint32_t row = qbase + prim;
-    const float a0 = __ldg(A.albedo + 3 * (size_t)row);
-    const float a1 = __ldg(A.albedo + 3 * (size_t)row + 1);
-    const float a2 = __ldg(A.albedo + 3 * (size_t)row + 2);
+    const float q0 = __ldg(A.albedo + 3 * (size_t)row);
+    const float q1 = __ldg(A.albedo + 3 * (size_t)row + 1);
+    const float q2 = __ldg(A.albedo + 3 * (size_t)row + 2);
+    float a0 = q0, a1 = q1, a2 = q2;  // diffuse albedo at the hit
+    if (A.P.tex_res) {
+        const float2 uv = A.B.hit_uv[j];
+        const F3 tx = tex_lookup(A.P.tex, A.P.tex_res, row, uv.x, uv.y);
+        a0 = __fmul_rn(q0, tx.x);
+        a1 = __fmul_rn(q1, tx.y);
+        a2 = __fmul_rn(q2, tx.z);
+    }
     const F3 sp = spawn_point(o, d, t, nrm);
+    float* rlog = A.P.ray_log ? ray_log_rec(A.P, g, depth) : nullptr;
+    if (rlog) log_spawn(rlog, sp);
+    const uint2 mt = A.B.meta[j];
+    const ViewDev& V = A.views[find_view_by_item(A, mt.x)];
+    uint32_t px, py;
+    const uint64_t gpix = view_pixel(V, mt.x - V.item_begin, &px, &py);
     if (replay) {
-        // d L / d a_i = (radiance leaving vertex i) / a_i, per channel
-        const uint2 mt = A.B.meta[j];
-        const ViewDev& V = A.views[find_view_by_item(A, mt.x)];
+        // d L / d q_i = (radiance leaving vertex i) / q_i per channel, q_i the
+        // quad's albedo (the texture factor is a constant of the path)
         const float* di = V.dimage + 3 * (mt.x - V.item_begin);
         const float inv_spp = __frcp_rn((float)V.spp);
         const float w0 = __fmul_rn(__ldg(di), inv_spp), w1 = __fmul_rn(__ldg(di + 1), inv_spp),
                     w2 = __fmul_rn(__ldg(di + 2), inv_spp);
         const float4 lt = A.B.Ltot[j], s = A.B.L[j];
-        const float g0 = a0 != 0.f ? __fdiv_rn(__fmul_rn(w0, __fsub_rn(lt.x, s.x)), a0) : 0.f;
-        const float g1 = a1 != 0.f ? __fdiv_rn(__fmul_rn(w1, __fsub_rn(lt.y, s.y)), a1) : 0.f;
-        const float g2 = a2 != 0.f ? __fdiv_rn(__fmul_rn(w2, __fsub_rn(lt.z, s.z)), a2) : 0.f;
+        const float g0 = q0 != 0.f ? __fdiv_rn(__fmul_rn(w0, __fsub_rn(lt.x, s.x)), q0) : 0.f;
+        const float g1 = q1 != 0.f ? __fdiv_rn(__fmul_rn(w1, __fsub_rn(lt.y, s.y)), q1) : 0.f;
+        const float g2 = q2 != 0.f ? __fdiv_rn(__fmul_rn(w2, __fsub_rn(lt.z, s.z)), q2) : 0.f;
         if (g0 != 0.f || g1 != 0.f || g2 != 0.f) grad_add(A.grad, row, g0, g1, g2);
     }
     if (A.P.sun_on) {
         const float cl = dot3(nrm, f3(A.P.sun_l[0], A.P.sun_l[1], A.P.sun_l[2]));
         if (cl > 0.f) {
             if (log && depth <= 16) log[2 * D] |= 1u << (2 * (depth - 1));
-            if (A.P.ray_log) log_shadow_origin(ray_log_rec(A.P, g, depth), sp);
             const float kk = __fmul_rn(cl, 0.318309886183790671538f);  // cos / pi
             const float4 p = make_float4(__fmul_rn(__fmul_rn(b.x, a0), __fmul_rn(A.P.sun_E[0], kk)),
                                          __fmul_rn(__fmul_rn(b.y, a1), __fmul_rn(A.P.sun_E[1], kk)),
@@ -246,9 +303,24 @@ __global__ void __launch_bounds__(256) wave_shade(const __grid_constant__ WaveAr
                 }
             } else {
                 A.B.pend[j] = p;
-                A.B.sray_o[j] = make_float4(sp.x, sp.y, sp.z, 0.f);
                 push(A.B.qs, A.B.ctr + kCtrStride * depth + kCtrShadow, j);
             }
+        }
+    }
+    if (A.P.sun_on || A.P.n_lights) A.B.sray_o[j] = make_float4(sp.x, sp.y, sp.z, 0.f);
+    if (A.P.n_lights) {
+        const uint4 xl = draw(A.P.seed, gpix, mt.y, kLightStream + (uint32_t)depth);
+        F3 ld, w;
+        float dist;
+        if (light_sample(A.P, u01(xl.x), u01(xl.y), u01(xl.z), sp, nrm, &ld, &dist, &w)) {
+            if (log && depth <= 16) log[2 * D + 1] |= 1u << (2 * (depth - 1));
+            if (rlog) log_light_ray(rlog, ld, dist);
+            const float ip = 0.318309886183790671538f;  // 1 / pi
+            A.B.lpend[j] = make_float4(__fmul_rn(__fmul_rn(b.x, a0), __fmul_rn(w.x, ip)),
+                                       __fmul_rn(__fmul_rn(b.y, a1), __fmul_rn(w.y, ip)),
+                                       __fmul_rn(__fmul_rn(b.z, a2), __fmul_rn(w.z, ip)), 0.f);
+            A.B.lray_d[j] = make_float4(ld.x, ld.y, ld.z, dist);
+            push(A.B.qs, A.B.ctr + kCtrStride * depth + kCtrShadow, j | kLightRay);
         }
     }
     b.x = __fmul_rn(b.x, a0);
@@ -256,10 +328,6 @@ __global__ void __launch_bounds__(256) wave_shade(const __grid_constant__ WaveAr
     b.z = __fmul_rn(b.z, a2);
     A.B.beta[j] = b;
     if ((uint32_t)depth < D) {
-        const uint2 mt = A.B.meta[j];
-        const ViewDev& V = A.views[find_view_by_item(A, mt.x)];
-        uint32_t px, py;
-        const uint64_t gpix = view_pixel(V, mt.x - V.item_begin, &px, &py);
         const uint4 xi = draw(A.P.seed, gpix, mt.y, (uint32_t)depth);
         const F3 nd = sample_cosine(nrm, u01(xi.x), u01(xi.y));
         if (A.P.ray_log) log_ray(ray_log_rec(A.P, g, depth + 1), sp, nd);
@@ -340,7 +408,10 @@ void wave_carve(void* base, uint64_t C, bool adjoint, WaveBufs& B) {
     B.L = reinterpret_cast<float4*>(take(16 * C));
     B.pend = reinterpret_cast<float4*>(take(16 * C));
     B.sray_o = reinterpret_cast<float4*>(take(16 * C));
+    B.lray_d = reinterpret_cast<float4*>(take(16 * C));
+    B.lpend = reinterpret_cast<float4*>(take(16 * C));
     B.hit = reinterpret_cast<uint4*>(take(16 * C));
+    B.hit_uv = reinterpret_cast<float2*>(take(8 * C));
     B.meta = reinterpret_cast<uint2*>(take(8 * C));
     B.q[0] = reinterpret_cast<uint32_t*>(take(4 * C));
     B.q[1] = reinterpret_cast<uint32_t*>(take(4 * C));
@@ -416,7 +487,7 @@ cudaError_t static_workspace(void** ptr) {
 // One pass over paths [P0, P0 + n) of the launch.
 static cudaError_t wave_pass(WaveArgs& A, uint64_t P0, uint32_t n, int replay, const Tune& t,
                              int sm_count, cudaStream_t s, StageHook* hook, const WaveStreams* ov) {
-    const bool overlap = ov && ov->aux && A.P.sun_on;
+    const bool overlap = ov && ov->aux && (A.P.sun_on || A.P.n_lights);
     A.P0 = P0;
     cudaError_t e = cudaMemsetAsync(A.B.ctr, 0, sizeof(uint32_t) * kCtrStride * (A.P.max_depth + 2), s);
     if (e != cudaSuccess) return e;
@@ -437,9 +508,9 @@ static cudaError_t wave_pass(WaveArgs& A, uint64_t P0, uint32_t n, int replay, c
         wave_shade<<<(n + 255) / 256, 256, 0, s>>>(A, (int)i, replay);
         if (hook) hook->end(kStageShade, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        // the replay traces shadow rays only beyond the depths whose
-        // visibility the primal recorded
-        if (A.P.sun_on && !(replay && i <= (uint32_t)kVisDepths)) {
+        // the replay traces sun shadow rays only beyond the depths whose
+        // visibility the primal recorded; key-light shadow rays every time
+        if ((A.P.sun_on && !(replay && i <= (uint32_t)kVisDepths)) || A.P.n_lights) {
             cudaStream_t ss = s;
             if (overlap) {
                 if ((e = cudaEventRecord(ov->fork, s)) != cudaSuccess) return e;
@@ -457,6 +528,11 @@ static cudaError_t wave_pass(WaveArgs& A, uint64_t P0, uint32_t n, int replay, c
         }
     }
     if (shadow_pending && (e = cudaStreamWaitEvent(s, ov->join, 0)) != cudaSuccess) return e;
+    if (A.P.n_lights) {
+        // key-light terms of the last vertices (no shade stage follows them)
+        wave_fold<<<(n + 255) / 256, 256, 0, s>>>(A, n);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     return cudaSuccess;
 }
 

@@ -16,9 +16,12 @@ constexpr int kCtrShadow = 1;       // shadow-ray queue length of this depth
 constexpr int kCtrFetchClosest = 2;
 constexpr int kCtrFetchShadow = 3;
 
-// Depths whose shadow-ray visibility the primal pass of the adjoint records
-// (one bit each), so that the replay need not trace those shadow rays.
+// Depths whose sun shadow-ray visibility the primal pass of the adjoint
+// records (one bit each), so that the replay need not trace those shadow
+// rays (key-light shadow rays are traced again).
 constexpr int kVisDepths = 32;
+// Shadow-queue entries of key-light shadow rays carry this bit.
+constexpr uint32_t kLightRay = 0x80000000u;
 
 struct WaveBufs {
     float4* ray_o;   // origin.xyz, tmin (0: path rays span (0, inf))
@@ -28,7 +31,10 @@ struct WaveBufs {
                      // of the path's unoccluded shadow rays, depths 1..32
     float4* pend;    // sun term waiting for its shadow ray
     float4* sray_o;  // shadow-ray origin
+    float4* lray_d;  // key-light shadow ray: direction, distance
+    float4* lpend;   // key-light term waiting for its shadow ray
     uint4* hit;      // t bits, instance, quad, slot
+    float2* hit_uv;  // quad-space (u, v) of the hit (per-face textures)
     uint2* meta;     // (pixel item, sample)
     uint32_t* q[2];  // closest-ray queues, ping-pong by depth parity
     uint32_t* qs;    // shadow-ray queue
@@ -73,7 +79,7 @@ struct WaveArgs {
 
 // Bytes wave_carve() takes for `capacity` paths (each piece 256-B aligned).
 constexpr size_t wave_workspace_bytes(uint64_t capacity, bool adjoint) {
-    return 7 * (((16 * capacity) + 255) & ~uint64_t(255)) + (((8 * capacity) + 255) & ~uint64_t(255)) +
+    return 9 * (((16 * capacity) + 255) & ~uint64_t(255)) + 2 * (((8 * capacity) + 255) & ~uint64_t(255)) +
            4 * (((4 * capacity) + 255) & ~uint64_t(255)) +
            ((sizeof(uint32_t) * kCtrStride * 258 + 255) & ~uint64_t(255)) +
            (adjoint ? (((16 * capacity) + 255) & ~uint64_t(255)) : 0);

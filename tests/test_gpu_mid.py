@@ -56,6 +56,25 @@ def test_mid_render_sampled_pixels(api, mid):
     assert len(rep["depths"]) >= 2
 
 
+def test_mid_render_textures_and_key_lights(api, mid):
+    """The mid frame with per-face textures (4x4 texels per quad) and the
+    23 key lights beside the sun, on 8192 sampled pixels: every divergent
+    path explained, agreeing paths within 1e-4 of the oracle."""
+    sc, gs, osc = mid
+    view = I.mid_view()
+    params = I.mid_params()
+    params.tex = I.face_textures(sc.n_quads)
+    params.lights = I.mid_lights()
+    alb = I.albedo(sc.n_quads)
+    px = np.sort(np.random.default_rng(19).choice(view.w * view.h, size=8192, replace=False))
+    pix_ok, err, r, rep = render_parity(api, gs, osc, sc, view, alb, params, pixels=px)
+    print(report_line("mid textures + 23 key lights", rep))
+    assert not rep["unexplained"], rep["unexplained"][:8]
+    assert rep["near_tie"] <= max(1, 1e-5 * rep["rays"]), report_line("mid lit", rep)
+    assert rep["divergent_path_frac"] < 5e-3, report_line("mid lit", rep)
+    assert (err <= 1e-4 * np.abs(r) + 1e-6).all(), err.max()
+
+
 def _mid_rays(sc):
     lo = np.array([0.0, 0.0, -150.0])
     hi = np.array([4096.0, 4096.0, 250.0])

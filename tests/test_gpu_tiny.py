@@ -1,6 +1,8 @@
 """GPU parity on the tiny instanced scene (one 64x64-quad mesh, 256
 instances): ray queries, path tracing, batching, graphs, the adjoint, and the
 device error paths, all through the C ABI against the FP64 oracle."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -162,16 +164,41 @@ def test_render_tiny_sun_and_depth(api, tiny):
     assert (err <= 1e-4 * np.abs(r) + 1e-6).all(), err.max()
 
 
-@pytest.mark.parametrize("chunk_log2", [10, 13, 21])
-def test_wavefront_equals_single_kernel(api, tiny, chunk_log2):
+@pytest.mark.parametrize("mode", [2, 1])
+def test_render_tiny_textures_and_key_lights(api, tiny, mode):
+    """Per-face textures (the Ptex stand-in) and four key lights beside the
+    sun: every divergent path explained, agreeing paths within 1e-4 of the
+    oracle's radiance, and the key lights visibly contributing."""
+    sc, gs, osc = tiny
+    view = I.tiny_view()
+    view.w, view.h, view.spp = 160, 120, 2
+    params = I.Params(max_depth=4, sun_dir=I.MID_SUN_DIR, sun_E=(2.0, 2.0, 2.0),
+                      env=(0.6, 0.7, 0.8), tex=I.face_textures(sc.n_quads), lights=I.tiny_lights())
+    alb = I.albedo(sc.n_quads)
+    pix_ok, err, r, rep = render_parity(api, gs, osc, sc, view, alb, params, tuning=dict(mode=mode))
+    _check_paths(f"tiny textures + key lights, mode {mode}", rep, 3e-3)
+    assert (err <= 1e-4 * np.abs(r) + 1e-6).all(), err.max()
+    # the lights matter: the image without them is darker somewhere
+    r0 = osc.render(view, alb, dataclasses.replace(params, lights=None))["rgb"]
+    assert (osc.render(view, alb, params)["rgb"] - r0).max() > 0.05
+
+
+@pytest.mark.parametrize("chunk_log2,shading", [(10, False), (13, False), (21, False), (10, True),
+                                                 (21, True)])
+def test_wavefront_equals_single_kernel(api, tiny, chunk_log2, shading):
     """The two renderers compute the same paths with the same arithmetic; a
-    tiny chunk size cuts chunks inside views and pixels' sample runs."""
+    tiny chunk size cuts chunks inside views and pixels' sample runs.  With
+    per-face textures and key lights too (the wavefront adds a vertex's
+    key-light term after its sun term, as the single kernel does)."""
     sc, gs, osc = tiny
     views = I.batched_views(n_views=5, min_log2=5.0, max_log2=7.0, max_spp=5)
     for v in views:
         v.eye = (50.0 + (v.eye[0] - 2048.0) / 40, -120.0, 50.0)
         v.look = (50.0, 50.0, 50.0)
     params = I.Params(max_depth=4, sun_dir=I.MID_SUN_DIR, sun_E=(3.0, 3.0, 3.0))
+    if shading:
+        params.tex = torch.from_numpy(I.face_textures(sc.n_quads)).cuda()
+        params.lights = I.tiny_lights()
     alb = torch.from_numpy(I.albedo(sc.n_quads)).cuda()
     D = params.max_depth
     words = api.path_log_words(views, D)
@@ -335,7 +362,7 @@ def test_adjoint_beyond_recorded_shadow_depths(api):
     alb = torch.from_numpy(I.albedo(sc.n_quads, lo=0.85, hi=0.95)).cuda()
     log = torch.zeros(api.path_log_words([view], D), dtype=torch.int32, device="cuda")
     gs.render([view], alb, params, path_log=log)
-    gl = log.cpu().numpy().view(np.uint32).reshape(-1, 2 * D + 1)
+    gl = log.cpu().numpy().view(np.uint32).reshape(-1, 2 * D + 2)
     assert (gl[:, 2 * 32] != NONE).sum() > 50          # hits at depth 33 exist
     dimg = torch.from_numpy(np.random.default_rng(5).normal(size=(view.h, view.w, 3))
                             .astype(np.float32)).cuda()
@@ -524,16 +551,16 @@ def test_crops_equal_whole_frame(api, tiny, mode):
     crl = torch.zeros(api.ray_log_floats(crops, D), dtype=torch.float32, device="cuda")
     outs = gs.render(crops, alb, params, path_log=clog, ray_log=crl, tuning=dict(mode=mode))
     gs.check()
-    flog = log.view(view.h, view.w, view.spp, 2 * D + 1)
-    frl = rlog.view(view.h, view.w, view.spp, D, 12)
+    flog = log.view(view.h, view.w, view.spp, 2 * D + 2)
+    frl = rlog.view(view.h, view.w, view.spp, D, 16)
     p0 = 0
     for (x, y, w, h), out in zip(tiles, outs):
         assert out.shape == (h, w, 3)
         assert torch.equal(out, full[y:y + h, x:x + w])
         n = w * h * view.spp
-        assert torch.equal(clog.view(-1, 2 * D + 1)[p0:p0 + n].view(h, w, view.spp, -1),
+        assert torch.equal(clog.view(-1, 2 * D + 2)[p0:p0 + n].view(h, w, view.spp, -1),
                            flog[y:y + h, x:x + w])
-        assert torch.equal(crl.view(-1, D, 12)[p0:p0 + n].view(h, w, view.spp, D, 12),
+        assert torch.equal(crl.view(-1, D, 16)[p0:p0 + n].view(h, w, view.spp, D, 16),
                            frl[y:y + h, x:x + w])
         p0 += n
 
@@ -612,7 +639,7 @@ def test_adjoint_matches_oracle_gradient(api, tiny):
     og = osc.grad(view, alb, params, dimg.reshape(-1, 3).astype(np.float64))
     agree = path_agreement(log.cpu().numpy().view(np.uint32), ref, D)
     # quads touched by a divergent path (either side) are excluded and counted
-    gl = log.cpu().numpy().view(np.uint32).reshape(-1, 2 * D + 1)
+    gl = log.cpu().numpy().view(np.uint32).reshape(-1, 2 * D + 2)
     offs = sc.quad_offsets
     touched = set()
     for k in np.nonzero(~agree)[0]:
@@ -671,7 +698,7 @@ def test_render_fn_autograd(api, tiny):
     gs.render([view], alb.detach(), params, path_log=log)
     ref = osc.render(view, a0, params, log=True)
     og = osc.grad(view, a0, params, dimg.double().cpu().numpy().reshape(-1, 3))
-    glog = log.cpu().numpy().view(np.uint32).reshape(-1, 2 * D + 1)
+    glog = log.cpu().numpy().view(np.uint32).reshape(-1, 2 * D + 2)
     agree = path_agreement(glog, ref, D)
     mask = np.ones(sc.n_quads, dtype=bool)
     mask[list(_touched_quads(sc, glog, ref, agree, D))] = False
@@ -680,6 +707,52 @@ def test_render_fn_autograd(api, tiny):
     assert sel.sum() > 1000
     rel = np.abs(g[sel] - og[sel]) / np.abs(og[sel])
     assert rel.max() < 1e-4, rel.max()
+
+
+def test_adjoint_with_textures_and_key_lights_matches_oracle_gradient(api, tiny):
+    """The replay adjoint with per-face textures and key lights (light
+    shadow rays traced again in the replay) against the oracle's stored-path
+    gradient, on quads whose paths agree, for both renderers.  The textures
+    are constant over each face (a random factor per face): the gradient
+    then does not depend on where a ray hits a face, which FP32 rays fix
+    only to within their rounding (the render tests bound that effect)."""
+    sc, gs, osc = tiny
+    view = I.tiny_view()
+    view.w, view.h, view.spp = 128, 96, 2
+    k = np.random.default_rng(63).uniform(0.4, 1.0, size=(sc.n_quads, 1, 1, 3)).astype(np.float32)
+    tex = np.ascontiguousarray(np.broadcast_to(k, (sc.n_quads, 4, 4, 3)))
+    params = I.Params(max_depth=3, sun_dir=I.MID_SUN_DIR, sun_E=(2, 2, 2), tex=tex, lights=I.tiny_lights())
+    gparams = dataclasses.replace(params, tex=torch.from_numpy(tex).cuda())
+    alb = I.albedo(sc.n_quads)
+    D = params.max_depth
+    dimg = np.random.default_rng(9).normal(size=(view.h, view.w, 3)).astype(np.float32)
+    d_alb = torch.from_numpy(alb).cuda()
+    log = torch.zeros(api.path_log_words([view], D), dtype=torch.int32, device="cuda")
+    gs.render([view], d_alb, gparams, path_log=log)
+    ref = osc.render(view, alb, params, log=True)
+    og = osc.grad(view, alb, params, dimg.reshape(-1, 3).astype(np.float64))
+    glog = log.cpu().numpy().view(np.uint32).reshape(-1, 2 * D + 2)
+    agree = path_agreement(glog, ref, D)
+    mask = np.ones(sc.n_quads, dtype=bool)
+    mask[list(_touched_quads(sc, glog, ref, agree, D))] = False
+    sel = mask[:, None] & (np.abs(og) > 1e-6 * np.abs(og).max())
+    assert sel.sum() > 1000
+    # every path term of the gradient is positive times the pixel's dimage
+    # entry, so the oracle gradient of |dimage| is the sum of the terms'
+    # magnitudes: FP32 rounding of each term bounds the error by a multiple
+    # of it, however much the signed terms cancel
+    mag = osc.grad(view, alb, params, np.abs(dimg).reshape(-1, 3).astype(np.float64))
+    for mode in (2, 1):
+        grad = torch.zeros_like(d_alb)
+        gs.adjoint([view], d_alb, [torch.from_numpy(dimg).cuda()], grad, gparams, tuning=dict(mode=mode))
+        gs.check()
+        g = grad.double().cpu().numpy()
+        rel = np.abs(g[sel] - og[sel]) / mag[sel]
+        assert rel.max() < 1e-4, (mode, rel.max())
+        # and against the signed value where the terms do not cancel much
+        keep = np.abs(og[sel]) > 0.1 * mag[sel]
+        assert keep.sum() > 500
+        assert (np.abs(g[sel] - og[sel])[keep] / np.abs(og[sel])[keep]).max() < 1e-4
 
 
 def test_l2_loss(api):
