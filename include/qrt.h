@@ -134,9 +134,9 @@ typedef struct {
  *   fetch          node fetch width in bytes (16: 4x128-bit, 32: 2x256-bit
  *                  loads, default)
  *   occupancy      trace kernels' register budget as resident warps per SM:
- *                  16 (up to 128 registers a thread), 24 (80) or 32 (64,
- *                  default; more warps hide the latency of the dependent
- *                  node loads better than the spills they cost)
+ *                  16 (up to 128 registers a thread), 24 (80), 32 (64,
+ *                  default), 40 (48) or 48 (40); more warps hide the latency
+ *                  of the dependent node loads, at the price of spills
  *   mode           renderer: 0 = default (wavefront), 1 = single persistent
  *                  kernel (a lane renders whole pixels), 2 = wavefront (stages
  *                  gen / trace / shade / shadow / accumulate over queues; a
@@ -445,6 +445,18 @@ int qrt_blases_build_check(const qrt_mesh* meshes, uint32_t n_mesh, const qrt_bu
  * INVALID_ARG (bad boxes, failed check), CUDA. */
 int qrt_tlas_build_check(const float* boxes, uint64_t n, const qrt_build_opts* opts,
                          uint64_t* n_nodes, uint32_t* depth);
+
+/* Test aid: sorts n (key, value) pairs by bits [0, end_bit) of the 64-bit
+ * key, stably (pairs whose sorting bits are equal keep their input order),
+ * with the device radix sort that the linear BVH builds use to order items
+ * along their Morton curve (Karras, HPG 2012).  keys / vals: host
+ * arrays of n entries, read; keys_out / vals_out: host arrays of n entries,
+ * written with the sorted pairs (whole keys, including bits at and above
+ * end_bit).  Allocates and frees device memory on the current device.
+ * n <= 2^32 - 2049, end_bit <= 64.  Errors: INVALID_ARG (NULL array, n or
+ * end_bit out of range), CUDA. */
+int qrt_test_sort_pairs(const uint64_t* keys, const uint32_t* vals, uint64_t n, uint32_t end_bit,
+                        uint64_t* keys_out, uint32_t* vals_out);
 
 #ifdef __cplusplus
 }

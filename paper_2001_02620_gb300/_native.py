@@ -112,6 +112,7 @@ SIGNATURES = {
                                   C.POINTER(C.c_uint32)]),
     "qrt_blases_build_check": (_i, [_vp, _u32, C.POINTER(qrt_build_opts), C.POINTER(C.c_uint64),
                                     C.POINTER(C.c_uint32)]),
+    "qrt_test_sort_pairs": (_i, [_vp, _vp, _u64, _u32, _vp, _vp]),
 }
 
 _lock = threading.Lock()

@@ -18,10 +18,10 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["trace.cu", "render.cu", "wavefront.cu", "lbvh.cu"]
+CU_SOURCES = ["trace.cu", "render.cu", "wavefront.cu", "lbvh.cu", "radix_sort.cu"]
 CPP_SOURCES = ["capi.cpp", "bvh_build.cpp"]
 HEADERS = ["qrt_layout.h", "launch.h", "traverse.cuh", "shading.cuh", "wavefront.h", "bvh_build.h",
-           "lbvh.h"]
+           "lbvh.h", "radix_sort.h"]
 
 
 def _inputs():

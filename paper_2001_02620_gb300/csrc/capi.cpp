@@ -21,6 +21,7 @@
 #include "bvh_build.h"
 #include "lbvh.h"
 #include "launch.h"
+#include "radix_sort.h"
 #include "wavefront.h"
 
 using namespace qrt;
@@ -257,8 +258,9 @@ int validate_tuning(const Tune& t) {
     if (t.batch < 1 || t.batch > 64) return fail(QRT_ERR_INVALID_ARG, "tuning.batch must be 1..64");
     if (t.blocks_per_sm < 0 || t.blocks_per_sm > 32)
         return fail(QRT_ERR_INVALID_ARG, "tuning.blocks_per_sm must be 0..32");
-    if (t.occupancy != 16 && t.occupancy != 24 && t.occupancy != 32)
-        return fail(QRT_ERR_INVALID_ARG, "tuning.occupancy must be 0, 16, 24 or 32");
+    if (t.occupancy != 16 && t.occupancy != 24 && t.occupancy != 32 && t.occupancy != 40 &&
+        t.occupancy != 48)
+        return fail(QRT_ERR_INVALID_ARG, "tuning.occupancy must be 0, 16, 24, 32, 40 or 48");
     if (t.mode < 1 || t.mode > 2) return fail(QRT_ERR_INVALID_ARG, "tuning.mode must be 0, 1 or 2");
     if (t.chunk_log2 != 0 && (t.chunk_log2 < 10 || t.chunk_log2 > 26))
         return fail(QRT_ERR_INVALID_ARG, "tuning.chunk_log2 must be 0 or 10..26");
@@ -1379,6 +1381,31 @@ int qrt_blas_build_check(const qrt_mesh* mesh, const qrt_build_opts* opts, uint6
     if (!check_wide(r.nodes, items, err, &d)) return fail(QRT_ERR_INVALID_ARG, err);
     if (n_nodes) *n_nodes = r.nodes.size();
     if (depth) *depth = d;
+    return QRT_OK;
+}
+
+int qrt_test_sort_pairs(const uint64_t* keys, const uint32_t* vals, uint64_t n, uint32_t end_bit,
+                        uint64_t* keys_out, uint32_t* vals_out) {
+    if (n && (!keys || !vals || !keys_out || !vals_out)) return fail(QRT_ERR_INVALID_ARG, "NULL array");
+    if (n > 0xFFFFFFFFull - 2048) return fail(QRT_ERR_INVALID_ARG, "n above 2^32 - 2049");
+    if (end_bit > 64) return fail(QRT_ERR_INVALID_ARG, "end_bit above 64");
+    if (n == 0) return QRT_OK;
+    const size_t sizes[5] = {(size_t)n * 8, (size_t)n * 4, (size_t)n * 8, (size_t)n * 4,
+                             sort_pairs_scratch_bytes((uint32_t)n)};
+    void* bufs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < 5 && e == cudaSuccess; ++b) e = cudaMalloc(&bufs[b], sizes[b]);
+    if (e == cudaSuccess) e = cudaMemcpy(bufs[0], keys, sizes[0], cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(bufs[1], vals, sizes[1], cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = sort_pairs(static_cast<uint64_t*>(bufs[0]), static_cast<uint32_t*>(bufs[1]),
+                       static_cast<uint64_t*>(bufs[2]), static_cast<uint32_t*>(bufs[3]), (uint32_t)n,
+                       (int)end_bit, bufs[4], 0);
+    if (e == cudaSuccess) e = cudaMemcpy(keys_out, bufs[2], sizes[0], cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(vals_out, bufs[3], sizes[1], cudaMemcpyDeviceToHost);
+    for (void* p : bufs)
+        if (p) cudaFree(p);
+    if (e != cudaSuccess) return fail(QRT_ERR_CUDA, std::string("CUDA: ") + cudaGetErrorString(e));
     return QRT_OK;
 }
 

@@ -13,9 +13,8 @@
 #include <thread>
 #include <vector>
 
-#include <cub/device/device_radix_sort.cuh>
-
 #include "lbvh.h"
+#include "radix_sort.h"
 
 namespace qrt {
 namespace {
@@ -509,13 +508,9 @@ bool build_on_device(const std::vector<FBox>& boxes, const Grid& g, TlasResult& 
     k_morton<<<blocks, B>>>(d_boxes, n, g.cmin[0], g.cmin[1], g.cmin[2], g.scale[0], g.scale[1],
                             g.scale[2], d_keys, d_ids);
     QRT_LBVH_TRY(cudaGetLastError());
-    size_t tmp_bytes = 0;
-    QRT_LBVH_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, d_keys, d_keys_sorted, d_ids,
-                                                 d_ids_sorted, (int)n, 0, 63));
-    void* d_tmp = nullptr;
-    QRT_LBVH_TRY(buf.alloc(reinterpret_cast<char**>(&d_tmp), tmp_bytes));
-    QRT_LBVH_TRY(cub::DeviceRadixSort::SortPairs(d_tmp, tmp_bytes, d_keys, d_keys_sorted, d_ids,
-                                                 d_ids_sorted, (int)n, 0, 63));
+    char* d_tmp = nullptr;
+    QRT_LBVH_TRY(buf.alloc(&d_tmp, sort_pairs_scratch_bytes(n)));
+    QRT_LBVH_TRY(sort_pairs(d_keys, d_ids, d_keys_sorted, d_ids_sorted, n, 63, d_tmp, 0));
     QRT_LBVH_TRY(cudaMemset(d_pint, 0xFF, (n - 1) * sizeof(uint32_t)));
     QRT_LBVH_TRY(cudaMemset(d_pleaf, 0xFF, n * sizeof(uint32_t)));
     QRT_LBVH_TRY(cudaMemset(d_arrivals, 0, (n - 1) * sizeof(uint32_t)));
@@ -1119,13 +1114,9 @@ bool blases_on_device(const std::vector<MeshView>& meshes, const std::vector<Mes
 
     k_quad_keys<<<blocks, B>>>(d_verts, d_quads, d_md, n_mesh, n, d_keys, d_ids);
     QRT_LBVH_TRY(cudaGetLastError());
-    size_t tmp_bytes = 0;
-    QRT_LBVH_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, d_keys, d_keys_sorted, d_ids,
-                                                 d_ids_sorted, (int)n, 0, 63));
     char* d_tmp = nullptr;
-    QRT_LBVH_TRY(buf.alloc(&d_tmp, tmp_bytes));
-    QRT_LBVH_TRY(cub::DeviceRadixSort::SortPairs(d_tmp, tmp_bytes, d_keys, d_keys_sorted, d_ids,
-                                                 d_ids_sorted, (int)n, 0, 63));
+    QRT_LBVH_TRY(buf.alloc(&d_tmp, sort_pairs_scratch_bytes(n)));
+    QRT_LBVH_TRY(sort_pairs(d_keys, d_ids, d_keys_sorted, d_ids_sorted, n, 63, d_tmp, 0));
     k_quad_gather<<<blocks, B>>>(d_verts, d_quads, d_md, n_mesh, d_ids_sorted, n, d_lbox, d_oq, d_prim);
     QRT_LBVH_TRY(cudaGetLastError());
     std::vector<uint32_t> roots(n_mesh, kNone);
