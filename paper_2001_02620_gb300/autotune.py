@@ -37,7 +37,7 @@ DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__f
 SPACE = {
     "block": [64, 128, 256],
     "fetch": [16, 32],
-    "occupancy": [16, 24, 32],
+    "occupancy": [24, 32, 40, 48],
     "batch": [1, 2, 4, 8],
 }
 STACK_DEPTHS = (32, 64)   # the library's choices; 64 is its maximum

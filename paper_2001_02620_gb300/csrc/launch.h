@@ -52,7 +52,7 @@ struct Tune {
     int batch = 1;          // single kernel: 32-pixel groups a warp claims; trace kernels: rays a lane claims
     int stack = 64;         // 32 or 64
     int fetch = 32;         // node fetch bytes per load: 16 or 32
-    int occupancy = 32;     // trace kernels: target resident warps per SM (16, 24 or 32)
+    int occupancy = 32;     // trace kernels: target resident warps per SM (16, 24, 32, 40 or 48)
     int mode = 2;           // 1 = single persistent kernel, 2 = wavefront
     int chunk_log2 = 0;     // wavefront paths per chunk = 2^chunk_log2; 0 = fit the call
 };

@@ -84,6 +84,8 @@ static cudaError_t launch_any_variant(const DevScene& S, const void* rays, uint6
         QRT_TV(16, OC, false);                                  \
     }
     QRT_TV_OCC(32)
+    QRT_TV_OCC(40)
+    QRT_TV_OCC(48)
     QRT_TV_OCC(24)
     QRT_TV_OCC(16)
 #undef QRT_TV_OCC

@@ -388,6 +388,8 @@ static cudaError_t launch_wave_trace(const WaveArgs& A, int depth, const Tune& t
         QRT_WT(16, OC, false);                                  \
     }
     QRT_WT_OCC(32)
+    QRT_WT_OCC(40)
+    QRT_WT_OCC(48)
     QRT_WT_OCC(24)
     QRT_WT_OCC(16)
 #undef QRT_WT_OCC

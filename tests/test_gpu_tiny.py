@@ -470,7 +470,7 @@ def test_autotuner_choice_is_valid_and_changes_no_pixel(api, tiny, tmp_path):
     view = I.tiny_view()
     params = I.Params(max_depth=3, sun_dir=I.MID_SUN_DIR, sun_E=(3.0, 3.0, 3.0))
     alb = torch.from_numpy(I.albedo(sc.n_quads)).cuda()
-    space = {"block": [64, 128], "stack": [32, 64], "occupancy": [16, 24], "batch": [1, 4]}
+    space = {"block": [64, 128], "stack": [32, 64], "occupancy": [24, 40], "batch": [1, 4]}
     cache = str(tmp_path / "tune.json")
     best = autotune.tune(gs, view, alb, params, space=space, reps=1, cache_path=cache,
                          scene_name="tiny")

@@ -136,8 +136,8 @@ def test_pack_and_unpack_without_a_process_group():
 
 def test_autotune_candidates_and_cache(tmp_path):
     c = autotune.candidates()
-    assert len(c) == 72 and all(set(x) == {"block", "fetch", "occupancy", "batch"} for x in c)
-    assert len({tuple(sorted(x.items())) for x in c}) == 72
+    assert len(c) == 96 and all(set(x) == {"block", "fetch", "occupancy", "batch"} for x in c)
+    assert len({tuple(sorted(x.items())) for x in c}) == 96
     # stack depths proven for a scene: 3 entries per wide-node level of a
     # TLAS path plus a BLAS path
     assert autotune.proven_stack_depths(4, 6) == [32, 64]
