@@ -100,3 +100,37 @@ def test_moana_dumped_rays_parity(moana):
         diff = np.nonzero(occ != o_occ)[0]
         # an any-hit disagreement must be a closest-hit near-tie as well
         assert all(k in set(np.nonzero((h[:, 1] != o_i) | (h[:, 2] != o_p))[0]) for k in diff), name
+
+
+@pytest.fixture(scope="module")
+def moana_full():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2001_02620_gb300 import api
+    sc = I.moana_scene(1.0)
+    return api, sc
+
+
+def test_moana_full_scale_sampled_pixels(moana_full):
+    """The benchmark's own workload and launch configuration at full size
+    (261.1 M unique quads, 39.3 M instances, 1920x1080, 16 spp, depth 8,
+    library defaults) on 1024 sampled pixels against the full-scale oracle:
+    every divergent path explained, agreeing paths within 1e-4."""
+    import gc
+    api, sc = moana_full
+    gs = api.Scene(sc)
+    osc = O.OracleScene(sc)
+    view, params = I.moana_view(sc.meta["extent"]), I.moana_params()
+    alb = I.albedo(sc.n_quads)
+    px = np.sort(np.random.default_rng(31).choice(view.w * view.h, size=1024, replace=False))
+    pix_ok, err, r, rep = render_parity(api, gs, osc, sc, view, alb, params, pixels=px)
+    print(report_line("moana x1.0 1920x1080 16 spp depth 8", rep))
+    print(f"moana x1.0: TLAS depth {gs.stats['tlas_depth']}, deepest BLAS {gs.stats['max_blas_depth']}")
+    assert gs.stats["n_quads"] == sc.n_quads and gs.stats["n_instances"] == len(sc.xforms)
+    assert not rep["unexplained"], rep["unexplained"][:8]
+    assert rep["near_tie"] <= max(1, 1e-5 * rep["rays"]), report_line("moana full", rep)
+    assert rep["divergent_path_frac"] < 5e-3, report_line("moana full", rep)
+    assert (err <= 1e-4 * np.abs(r) + 1e-6).all(), err.max()
+    gs.close()
+    del osc, gs
+    gc.collect()
