@@ -107,10 +107,34 @@ def proxy_view(view, max_paths: int = 1 << 22):
     return dataclasses.replace(view, w=max(32, int(view.w * s)), h=max(32, int(view.h * s)))
 
 
+def _time_render(scene, view, albedo, params, out, cand, reps: int) -> float:
+    """Best of `reps` timed renders (after one untimed) with CUDA events."""
+    import torch
+    scene.render([view], albedo, params, outs=[out], tuning=cand)
+    scene.check()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        scene.render([view], albedo, params, outs=[out], tuning=cand)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) * 1e-3)
+    scene.check()
+    return min(ts)
+
+
 def tune(scene, view, albedo, params, space: dict | None = None, reps: int = 3,
          cache_path: str | None = DEFAULT_CACHE, scene_name: str | None = None,
-         force: bool = False, log=None) -> dict:
-    """Returns the best tuning dict for rendering `view` of `scene` (api.Scene)."""
+         force: bool = False, log=None, finalists: int = 4, proxy_paths: int = 1 << 22) -> dict:
+    """Returns the best tuning dict for rendering `view` of `scene` (api.Scene).
+
+    Every candidate is timed on a proxy view of at most proxy_paths paths; when the
+    view is larger, the `finalists` fastest are timed again on the view
+    itself and the fastest there wins.  (A proxy renders from a warm L2 and
+    a smaller working set: on a scene of tens of GB the full frame preferred
+    40 resident warps per SM, 2.6 % faster, where the proxy chose 32.)"""
     import torch
 
     from . import _native as N
@@ -122,7 +146,7 @@ def tune(scene, view, albedo, params, space: dict | None = None, reps: int = 3,
         hit = load_cache(cache_path).get(key)
         if hit:
             return hit["tuning"]
-    pv = proxy_view(view)
+    pv = proxy_view(view, proxy_paths)
     out = torch.empty((pv.h, pv.w, 3), device=albedo.device)
     timings = {}
     space = dict(space or SPACE)
@@ -131,26 +155,28 @@ def tune(scene, view, albedo, params, space: dict | None = None, reps: int = 3,
     for cand in candidates(space):
         ck = json.dumps(cand, sort_keys=True)
         try:
-            scene.render([pv], albedo, params, outs=[out], tuning=cand)
-            scene.check()
-            ts = []
-            for _ in range(reps):
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record()
-                scene.render([pv], albedo, params, outs=[out], tuning=cand)
-                e1.record()
-                e1.synchronize()
-                ts.append(e0.elapsed_time(e1) * 1e-3)
-            scene.check()
-            timings[ck] = min(ts)
+            timings[ck] = _time_render(scene, pv, albedo, params, out, cand, reps)
         except N.QrtError:
             timings[ck] = None
         if log:
             log(f"tune {ck}: {timings[ck]}")
     best, t = pick_best(timings)
+    final = {}
+    if finalists > 1 and (pv.w, pv.h) != (view.w, view.h):
+        ranked = sorted((v, k) for k, v in timings.items() if v is not None)[:finalists]
+        full = torch.empty((view.h, view.w, 3), device=albedo.device)
+        for _, ck in ranked:
+            try:
+                final[ck] = _time_render(scene, view, albedo, params, full, json.loads(ck), 2)
+            except N.QrtError:
+                final[ck] = None
+            if log:
+                log(f"tune (whole view) {ck}: {final[ck]}")
+        del full
+        best, t = pick_best(final)
     result = json.loads(best)
     if cache_path:
         store_cache(key, {"tuning": result, "seconds": t, "proxy": [pv.w, pv.h, pv.spp],
+                          "whole_view_finalists": final,
                           "when": time.strftime("%Y-%m-%dT%H:%M:%S")}, cache_path)
     return result

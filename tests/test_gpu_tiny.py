@@ -483,6 +483,28 @@ def test_autotuner_choice_is_valid_and_changes_no_pixel(api, tiny, tmp_path):
     gs.check()
 
 
+def test_autotuner_times_finalists_on_the_whole_view(api, tiny, tmp_path):
+    """With a proxy smaller than the view, the fastest proxy candidates are
+    timed again on the view itself and the winner is one of them."""
+    import json
+
+    from paper_2001_02620_gb300 import autotune
+    sc, gs, osc = tiny
+    view = I.tiny_view()
+    alb = torch.from_numpy(I.albedo(sc.n_quads)).cuda()
+    space = {"block": [64, 128, 256], "stack": [64], "occupancy": [32, 40], "batch": [1]}
+    cache = str(tmp_path / "tune.json")
+    best = autotune.tune(gs, view, alb, I.tiny_params(), space=space, reps=1, cache_path=cache,
+                         scene_name="tiny", finalists=3, proxy_paths=1 << 12)
+    (entry,) = autotune.load_cache(cache).values()
+    finals = entry["whole_view_finalists"]
+    assert len(finals) == 3 and all(v is not None for v in finals.values())
+    assert json.dumps(best, sort_keys=True) in finals
+    assert finals[json.dumps(best, sort_keys=True)] == min(finals.values())
+    assert entry["proxy"][0] * entry["proxy"][1] * view.spp <= 1 << 12
+    gs.check()
+
+
 def test_white_furnace_gpu(api):
     v, q = I.sphere_mesh(24, 48, 5.0)
     sc = I.Scene([(v, q)], I.IDENTITY_XFORM[None].copy(), np.zeros(1, dtype=np.uint32))
