@@ -124,7 +124,7 @@ typedef struct {
 } qrt_view;
 
 /* Launch tuning; 0 in any field selects the library default.
- *   block          threads per block: 64, 128 (default), 192 or 256
+ *   block          threads per block: 64, 128, 192 or 256 (default)
  *   blocks_per_sm  resident blocks per SM for persistent kernels (default:
  *                  as many as the register budget allows)
  *   batch          single kernel: pixels a warp claims per fetch, in units
@@ -134,8 +134,8 @@ typedef struct {
  *   fetch          node fetch width in bytes (16: 4x128-bit, 32: 2x256-bit
  *                  loads, default)
  *   occupancy      trace kernels' register budget as resident warps per SM:
- *                  16 (up to 128 registers a thread), 24 (80), 32 (64,
- *                  default), 40 (48) or 48 (40); more warps hide the latency
+ *                  16 (up to 128 registers a thread), 24 (80), 32 (64),
+ *                  40 (48, default) or 48 (40); more warps hide the latency
  *                  of the dependent node loads, at the price of spills
  *   mode           renderer: 0 = default (wavefront), 1 = single persistent
  *                  kernel (a lane renders whole pixels), 2 = wavefront (stages

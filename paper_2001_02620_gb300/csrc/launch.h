@@ -47,12 +47,12 @@ constexpr int occupancy_regs(int warps) { return (65536 / (32 * warps)) & ~7; }
 
 // Resolved launch configuration.
 struct Tune {
-    int block = 128;
+    int block = 256;
     int blocks_per_sm = 0;  // 0 = occupancy maximum
     int batch = 1;          // single kernel: 32-pixel groups a warp claims; trace kernels: rays a lane claims
     int stack = 64;         // 32 or 64
     int fetch = 32;         // node fetch bytes per load: 16 or 32
-    int occupancy = 32;     // trace kernels: target resident warps per SM (16, 24, 32, 40 or 48)
+    int occupancy = 40;     // trace kernels: target resident warps per SM (16, 24, 32, 40 or 48)
     int mode = 2;           // 1 = single persistent kernel, 2 = wavefront
     int chunk_log2 = 0;     // wavefront paths per chunk = 2^chunk_log2; 0 = fit the call
 };
