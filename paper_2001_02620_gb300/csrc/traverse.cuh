@@ -477,7 +477,10 @@ __device__ __forceinline__ void add_stats(unsigned long long* stats, const Trace
 // drive the warp-synchronous phase methods below from persistent_trace and
 // refill finished lanes, so no lane waits for the slowest ray of its warp.
 // The world ray itself is not kept: the callers' world() functors supply it.
-template <bool ANY, int STACK, int FETCH>
+// UV = false drops the hit's quad-space (u, v) (left 0): closest-hit rays
+// whose consumer needs no (u, v) do not carry two more values through the
+// traversal nor divide for them at every closer hit.
+template <bool ANY, int STACK, int FETCH, bool UV = true>
 struct Traversal {
     float tmin, tmax;
     float te;  // object-space parameter offset: t = s + te
@@ -833,8 +836,10 @@ struct Traversal {
                 if (better && tc < (double)tmax) {
                     h.t = (float)tc;
                     h.inst = cur_inst;
-                    h.u = uu;
-                    h.v = vv;
+                    if constexpr (UV) {
+                        h.u = uu;
+                        h.v = vv;
+                    }
                     h.slot = slot;
                     h_eps = sh.eps_t;
                 }
@@ -843,16 +848,20 @@ struct Traversal {
             if (tt < h.t) {
                 h.t = tt;
                 h.inst = cur_inst;
-                h.u = uu;
-                h.v = vv;
+                if constexpr (UV) {
+                    h.u = uu;
+                    h.v = vv;
+                }
                 h.slot = slot;
                 h_eps = ex64 ? 0.f : sh.eps_t;
             } else if (tt == h.t) {
                 if (cur_inst < h.inst ||
                     (cur_inst == h.inst && __ldg(S.prim + slot) < __ldg(S.prim + h.slot))) {
                     h.inst = cur_inst;
-                    h.u = uu;
-                    h.v = vv;
+                    if constexpr (UV) {
+                        h.u = uu;
+                        h.v = vv;
+                    }
                     h.slot = slot;
                     h_eps = ex64 ? 0.f : sh.eps_t;
                 }
@@ -876,8 +885,8 @@ struct Traversal {
 // groups) until few lanes are left with an inner node, then lanes enter
 // instances or test one leaf each.  Finished lanes refill
 // immediately, so no lane waits for the slowest ray of its warp.
-template <bool ANY, int STACK, int FETCH, class Idx, class Start, class Done, class World>
-__device__ __forceinline__ void persistent_trace(const DevScene& S, Traversal<ANY, STACK, FETCH>& T,
+template <bool ANY, int STACK, int FETCH, bool UV, class Idx, class Start, class Done, class World>
+__device__ __forceinline__ void persistent_trace(const DevScene& S, Traversal<ANY, STACK, FETCH, UV>& T,
                                                  TraceStats& st, Idx* cursor, Idx count,
                                                  uint32_t batch, int cap, Start start, Done done,
                                                  World world) {

@@ -108,7 +108,8 @@ __global__ void __launch_bounds__(256) wave_gen(const __grid_constant__ WaveArgs
 // sun; an unoccluded ray adds pend[] into L[].  Rays use at most stack_cap
 // stack entries.  Work counters are kept only in the STATS variant: in the
 // others they are dead code, which saves a dozen registers per thread.
-template <bool ANY, int FETCH, int OCC, bool STATS>
+// UV: closest-hit rays keep the hit's (u, v) (per-face textures need them)
+template <bool ANY, int FETCH, int OCC, bool STATS, bool UV>
 __global__ void __maxnreg__(occupancy_regs(OCC)) wave_trace(const __grid_constant__ WaveArgs A, int depth,
                                                         int stack_cap) {
     const uint32_t* ctr = A.B.ctr + kCtrStride * depth;
@@ -117,7 +118,7 @@ __global__ void __maxnreg__(occupancy_regs(OCC)) wave_trace(const __grid_constan
     const uint32_t* queue = ANY ? A.B.qs : A.B.q[depth & 1];
     const uint32_t batch = A.batch;
     TraceStats st{0, 0, 0, 0, 0, 0};
-    Traversal<ANY, kMaxStack, FETCH> T;
+    Traversal<ANY, kMaxStack, FETCH, UV> T;
     T.err = 0;  // accumulated over this thread's rays
     uint32_t j = 0;
     // any-hit entries of key-light shadow rays carry kLightRay
@@ -168,7 +169,7 @@ __global__ void __maxnreg__(occupancy_regs(OCC)) wave_trace(const __grid_constan
             }
         } else {
             A.B.hit[j] = make_uint4(__float_as_uint(T.h.t), T.h.inst, T.h.prim, T.h.slot);
-            if (A.P.tex_res) A.B.hit_uv[j] = make_float2(T.h.u, T.h.v);
+            if constexpr (UV) A.B.hit_uv[j] = make_float2(T.h.u, T.h.v);
         }
     };
     // the world ray is read back from the queue buffers where the traversal
@@ -365,22 +366,22 @@ __global__ void __launch_bounds__(256) wave_accumulate(const __grid_constant__ W
     }
 }
 
-template <bool ANY, int FETCH, int OCC, bool STATS>
+template <bool ANY, int FETCH, int OCC, bool STATS, bool UV>
 static cudaError_t launch_wave_trace_v(const WaveArgs& A, int depth, const Tune& t, int sm_count,
                                        cudaStream_t s) {
     static ResidentBlocks resident;
     const int per_sm = t.blocks_per_sm > 0 ? t.blocks_per_sm
-                                           : resident.get(wave_trace<ANY, FETCH, OCC, STATS>, t.block);
-    wave_trace<ANY, FETCH, OCC, STATS><<<(unsigned)(sm_count * per_sm), t.block, 0, s>>>(A, depth,
-                                                                                         t.stack);
+                                           : resident.get(wave_trace<ANY, FETCH, OCC, STATS, UV>, t.block);
+    wave_trace<ANY, FETCH, OCC, STATS, UV><<<(unsigned)(sm_count * per_sm), t.block, 0, s>>>(
+        A, depth, t.stack);
     return cudaGetLastError();
 }
 
-template <bool ANY>
-static cudaError_t launch_wave_trace(const WaveArgs& A, int depth, const Tune& t, int sm_count,
-                                     cudaStream_t s) {
+template <bool ANY, bool UV>
+static cudaError_t launch_wave_trace_uv(const WaveArgs& A, int depth, const Tune& t, int sm_count,
+                                        cudaStream_t s) {
     const bool st = A.stats != nullptr, f32 = t.fetch == 32;
-#define QRT_WT(FE, OC, ST) return launch_wave_trace_v<ANY, FE, OC, ST>(A, depth, t, sm_count, s)
+#define QRT_WT(FE, OC, ST) return launch_wave_trace_v<ANY, FE, OC, ST, UV>(A, depth, t, sm_count, s)
 #define QRT_WT_OCC(OC)                                          \
     if (t.occupancy == OC) {                                    \
         if (st) { if (f32) QRT_WT(32, OC, true); QRT_WT(16, OC, true); } \
@@ -395,6 +396,16 @@ static cudaError_t launch_wave_trace(const WaveArgs& A, int depth, const Tune& t
 #undef QRT_WT_OCC
 #undef QRT_WT
     return cudaErrorInvalidValue;
+}
+
+// Closest-hit rays carry (u, v) only when the shading reads them.
+template <bool ANY>
+static cudaError_t launch_wave_trace(const WaveArgs& A, int depth, const Tune& t, int sm_count,
+                                     cudaStream_t s) {
+    if constexpr (!ANY) {
+        if (A.P.tex_res) return launch_wave_trace_uv<false, true>(A, depth, t, sm_count, s);
+    }
+    return launch_wave_trace_uv<ANY, false>(A, depth, t, sm_count, s);
 }
 
 void wave_carve(void* base, uint64_t C, bool adjoint, WaveBufs& B) {
