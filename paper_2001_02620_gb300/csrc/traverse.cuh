@@ -187,8 +187,9 @@ __device__ __forceinline__ float byte_f(uint32_t w, int i) {
 __device__ __forceinline__ float exp2i(int e) { return __int_as_float((e + 127) << 23); }
 
 // Tests the four children of a node; writes entry distances (inf = culled)
-// and references, sorted nearest first.  Returns the number of hits.
-template <int FETCH>
+// and references, sorted nearest first (SORT) or in slot order (any-hit
+// rays, which need no order).  Returns the number of hits.
+template <int FETCH, bool SORT = true>
 __device__ __forceinline__ int node_children(const QNode* node, const RaySetup& r, float tmin,
                                              float tmax, float t[4], uint32_t ref[4]) {
     uint4 A, B, C, D;
@@ -233,6 +234,8 @@ __device__ __forceinline__ int node_children(const QNode* node, const RaySetup& 
         t[i] = hit ? tn : kInfF;
         ref[i] = (m == kMetaInner) ? child[i] : (kRefLeaf | ((m - 1u) << 27) | child[i]);
     }
+    if constexpr (!SORT)
+        return (t[0] < kInfF) + (t[1] < kInfF) + (t[2] < kInfF) + (t[3] < kInfF);
     // sorting network on (t, ref); strict comparisons keep equal keys in order
 #define QRT_CSWAP(i, j)                             \
     if (t[j] < t[i]) {                              \
@@ -499,6 +502,28 @@ struct Traversal {
     uint32_t pleaf;  // postponed BLAS leaf reference (0 = none)
     Hit h;
 
+    // Pushes the hit children other than the one visited next and makes that
+    // one current (nh > 0).  Closest hit: children sorted nearest first, the
+    // nearest visited next, the others pushed farthest first with their entry
+    // distances.  Any hit: children in slot order (the answer does not
+    // depend on the order, and an unoccluded ray visits every child anyway),
+    // the first hit visited next.
+    __device__ __forceinline__ void push_children(int nh, const float t[4], const uint32_t ref[4]) {
+        if constexpr (ANY) {
+            const bool h0 = t[0] < kInfF, h1 = t[1] < kInfF, h2 = t[2] < kInfF;
+            const int first = h0 ? 0 : (h1 ? 1 : (h2 ? 2 : 3));
+#pragma unroll
+            for (int k = 3; k >= 0; --k)
+                if (t[k] < kInfF && k != first) stack[sp++] = ref[k];
+            cur = h0 ? ref[0] : (h1 ? ref[1] : (h2 ? ref[2] : ref[3]));
+        } else {
+#pragma unroll
+            for (int k = 3; k >= 1; --k)
+                if (k < nh) stack[sp++] = ((uint64_t)__float_as_uint(t[k]) << 32) | ref[k];
+            cur = ref[0];
+        }
+    }
+
     __device__ __forceinline__ void init(const DevScene& S, float ox, float oy, float oz, float dx,
                                          float dy, float dz, float t0, float t1, uint32_t msteps,
                                          TraceStats& st) {
@@ -553,7 +578,7 @@ struct Traversal {
                 float t[4];
                 uint32_t ref[4];
                 const float lo = top() ? tmin : __fsub_rn(tmin, te);
-                const int nh = node_children<FETCH>(S.nodes + node_base + cur, r, lo, limit(), t, ref);
+                const int nh = node_children<FETCH, !ANY>(S.nodes + node_base + cur, r, lo, limit(), t, ref);
                 if (nh == 0) {
                     have = false;
                 } else {
@@ -561,10 +586,7 @@ struct Traversal {
                         err |= kErrStackOverflow;
                         return false;
                     }
-#pragma unroll
-                    for (int k = 3; k >= 1; --k)
-                        if (k < nh) stack[sp++] = ANY ? ref[k] : (((uint64_t)__float_as_uint(t[k]) << 32) | ref[k]);
-                    cur = ref[0];
+                    push_children(nh, t, ref);
                     return true;
                 }
             } else if (top()) {
@@ -656,7 +678,7 @@ struct Traversal {
         float t[4];
         uint32_t ref[4];
         const float lo = top() ? tmin : __fsub_rn(tmin, te);
-        const int nh = node_children<FETCH>(S.nodes + node_base + cur, r, lo, limit(), t, ref);
+        const int nh = node_children<FETCH, !ANY>(S.nodes + node_base + cur, r, lo, limit(), t, ref);
         if (nh == 0) {
             have = false;
         } else {
@@ -664,10 +686,7 @@ struct Traversal {
                 stop(kErrStackOverflow);
                 return;
             }
-#pragma unroll
-            for (int k = 3; k >= 1; --k)
-                if (k < nh) stack[sp++] = ANY ? ref[k] : (((uint64_t)__float_as_uint(t[k]) << 32) | ref[k]);
-            cur = ref[0];
+            push_children(nh, t, ref);
         }
         advance(S, world);
     }
