@@ -34,3 +34,27 @@ def test_reference_arm_prints_one_json_line():
     import bench
     assert d["config"] == bench.workload_config("mid", 1.0)
     assert set(bench.workload_config("moana", 1.0)) == {"workload", "l2"}
+
+
+def test_recorded_traffic_needs_current_sources_and_launch_parameters(tmp_path, monkeypatch):
+    """A committed DRAM figure is reported only for the kernel sources and the
+    launch parameters it was captured with."""
+    sys.path.insert(0, ROOT)
+    import bench
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    rec = {"moana": {"kernel": "k", "dram_bytes_per_launch": 123, "source": "s",
+                     "kernel_source_hash": bench.kernel_source_hash(),
+                     "launch": {"block": 256, "fetch": 32, "occupancy": 40}},
+           "mid": {"kernel": "k", "dram_bytes_per_launch": 5, "source": "s",
+                   "kernel_source_hash": "0000000000000000"}}
+    (prof / "roofline_traffic.json").write_text(json.dumps(rec))
+    h = bench.kernel_source_hash()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: h)
+    assert bench.recorded_traffic("moana")[0] == 123.0          # library defaults
+    assert bench.recorded_traffic("moana", {"block": 256, "fetch": 32, "occupancy": 40,
+                                            "batch": 1, "stack": 64})[0] == 123.0
+    assert bench.recorded_traffic("moana", {"block": 256, "occupancy": 32})[0] is None
+    assert bench.recorded_traffic("mid")[0] is None               # other kernel sources
+    assert bench.recorded_traffic("tiny")[0] is None
