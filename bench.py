@@ -37,7 +37,8 @@ STAT_WORDS = 12
 # the closest-hit kernel's code and the scene build that shapes its traffic
 KERNEL_SOURCES = ["paper_2001_02620_gb300/csrc/traverse.cuh", "paper_2001_02620_gb300/csrc/wavefront.cu",
                   "paper_2001_02620_gb300/csrc/qrt_layout.h", "paper_2001_02620_gb300/csrc/shading.cuh",
-                  "paper_2001_02620_gb300/csrc/bvh_build.cpp", "paper_2001_02620_gb300/csrc/capi.cpp"]
+                  "paper_2001_02620_gb300/csrc/bvh_build.cpp", "paper_2001_02620_gb300/csrc/bvh_build.h",
+                  "paper_2001_02620_gb300/csrc/capi.cpp"]
 
 
 def kernel_source_hash() -> str:

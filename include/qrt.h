@@ -222,7 +222,7 @@ typedef struct {
 } qrt_params;
 
 /* BVH build options (NULL = defaults).
- *   max_leaf   quads per BLAS leaf (1..8, default 4)
+ *   max_leaf   quads per BLAS leaf (1..8, default 2)
  *   sah_bins   binned-SAH bins (4..64, default 16)
  *   threads    host threads for the build (0 = all cores)
  *   degenerate 1 = build a deliberately deep chain-shaped BLAS (test aid for
