@@ -152,8 +152,8 @@ WORKLOADS = {
 }
 # what stands between timed steps and the L2 (the same words on both arms)
 L2_NOTE = {
-    "mid": "no flush: scene (0.36 GB) and per-path state (0.7 GB) exceed the 129 MB L2",
-    "moana": "no flush: scene (23 GB) and per-path state (5.5 GB) exceed the 129 MB L2",
+    "mid": "no flush: scene (0.4 GB) and per-path state (0.7 GB) exceed the 129 MB L2",
+    "moana": "no flush: scene (25 GB) and per-path state (5.5 GB) exceed the 129 MB L2",
 }
 
 
