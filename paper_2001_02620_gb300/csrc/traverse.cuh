@@ -137,9 +137,10 @@ __device__ __forceinline__ float maxabs3(float a, float b, float c) {
 
 // --------------------------------------------------------------------------
 // Node fetch: 64 bytes as four 128-bit or two 256-bit read-only loads.  The
-// loads do not allocate in L1: at 32 warps per SM the per-ray local memory
-// (spilled values and traversal stacks) needs L1, and node lines, which are
-// seldom reused by the same SM soon enough, would only evict it (the mid
+// loads do not allocate in L1: with 32 or more warps per SM the per-ray
+// local memory (spilled values and traversal stacks) needs L1, and node
+// lines, which are seldom reused by the same SM soon enough, would only
+// evict it (the mid
 // frame measured 657 -> 674 Mrays/s with the hint, 678 with quads read the
 // same way; L2 still caches both).
 // --------------------------------------------------------------------------
