@@ -140,9 +140,8 @@ __device__ __forceinline__ float maxabs3(float a, float b, float c) {
 // loads do not allocate in L1: with 32 or more warps per SM the per-ray
 // local memory (spilled values and traversal stacks) needs L1, and node
 // lines, which are seldom reused by the same SM soon enough, would only
-// evict it (the mid
-// frame measured 657 -> 674 Mrays/s with the hint, 678 with quads read the
-// same way; L2 still caches both).
+// evict it (the mid frame measured 657 -> 674 Mrays/s with the hint, 678
+// with quads read the same way; L2 still caches both).
 // --------------------------------------------------------------------------
 __device__ __forceinline__ uint4 ld_nc_na(const void* p) {
     uint4 v;
